@@ -1,0 +1,128 @@
+/*
+ * Sequential CPU oracle for the deterministic multilevel partitioner of
+ * "Tera-Scale Multilevel Graph Partitioning" (TeraPart).
+ *
+ * TEST INFRASTRUCTURE ONLY. This code is the plain, slow, obviously correct
+ * statement of what the GPU path computes. Only the test-suite, the smoke check
+ * and the CPU-baseline leg of the benchmark may load it. The GPU library shares
+ * no code, header, table or constant with it.
+ *
+ * Every function cites the passage of the paper it restates (section, equation
+ * or algorithm). Where the paper is silent the reading taken is stated at the
+ * function.
+ *
+ * Parity status per function:
+ *   orc_varint_*, orc_encode, orc_decode  pinned (hand-computed bytes, round trip)
+ *   orc_lp_*                              pinned (brute-force argmax, cap invariant,
+ *                                                  approval vs subset enumeration)
+ *   orc_two_hop                           pinned (cap + grouping invariants, hand cases)
+ *   orc_contract                          pinned (weight sums, identity, all-in-one)
+ *   orc_initial_partition, orc_refine,
+ *   orc_rebalance, orc_partition          pinned by invariants only (balance, cut
+ *                                          bounds, projection preserves cut);
+ *                                          the heuristic itself has no closed form
+ */
+#ifndef TERAPART_ORACLE_H
+#define TERAPART_ORACLE_H
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Undirected graph in CSR form (Section "Graph Representation"): the
+ * neighbours of u are adj[xadj[u] .. xadj[u+1]), sorted ascending, no
+ * self-loops, no duplicates, every edge stored in both directions.
+ * vw = node weights c(u) (> 0), ew = edge weights w(u,v) (> 0). */
+typedef struct {
+  int64_t n;
+  int64_t m2; /* adjacency entries = 2m */
+  int64_t *xadj;
+  int32_t *adj;
+  int64_t *vw;
+  int64_t *ew;
+} orc_graph;
+
+/* Semantic parameters: they change results. */
+typedef struct {
+  uint64_t seed;
+  int32_t cluster_rounds; /* LP rounds per coarsening level (5, Section "Label Propagation Clustering") */
+  int32_t refine_rounds;  /* LP rounds per refinement level (5) */
+  int32_t sub_rounds;     /* synchronous sub-rounds per round, S (8) */
+  int32_t c_lim;          /* coarsening stops once n <= c_lim * k (160) */
+  int32_t ip_attempts;    /* bisection attempts per tree node, T (8) */
+  int32_t two_hop;        /* 1: pack leftover singletons after clustering */
+  int32_t max_levels;     /* at most this many graphs in the hierarchy (64) */
+} orc_params;
+
+typedef struct {
+  int64_t cut;
+  int64_t max_block_weight;
+  int64_t l_max;
+  int64_t u_max; /* cluster weight cap U */
+  double imbalance;
+  int32_t levels;
+  int32_t balanced; /* 1 iff every block <= l_max */
+  int64_t level_n[64];
+  int64_t level_m2[64];
+} orc_stats;
+
+/* ---- hashing (counter-based, used for sub-round assignment and ties) ---- */
+uint64_t orc_mix64(uint64_t z);
+uint64_t orc_step(uint64_t h, uint64_t x);
+uint64_t orc_round_key(uint64_t seed, uint64_t tag, uint64_t a, uint64_t b);
+uint64_t orc_tag(int which); /* 0 cluster, 1 refine, 2 two-hop, 3 ip-seed, 4 ip-lp, 5 tie */
+
+/* ---- compressed adjacency (Section "Compression Scheme") ---- */
+int orc_varint_len(uint64_t x);
+int orc_varint_put(uint8_t *out, uint64_t x);                 /* returns bytes written */
+int orc_varint_get(const uint8_t *in, int64_t avail, uint64_t *x); /* returns bytes read, 0 on error */
+int64_t orc_encoded_size(int64_t n, const int64_t *xadj, const int32_t *adj);
+int64_t orc_encode(int64_t n, const int64_t *xadj, const int32_t *adj, uint8_t *bytes, uint64_t *off);
+/* Returns 0 on success, -1 on a corrupt stream. xadj_out has n+1 entries,
+ * adj_out has m2 entries (m2 taken from the terminal header). */
+int orc_decode(int64_t n, const uint8_t *bytes, int64_t nbytes, const uint64_t *off,
+               int64_t *xadj_out, int32_t *adj_out, int64_t adj_cap);
+
+/* ---- label propagation (Algorithm 1, made synchronous and deterministic) ---- */
+/* Decision for one vertex against a state snapshot. Returns 1 if u moves. */
+int orc_rate_vertex(const orc_graph *g, int64_t u, const int32_t *label, const int64_t *lw,
+                    int64_t cap_uniform, const int64_t *cap, int ignore_cap, uint64_t hv,
+                    int32_t *target, int64_t *gain);
+/* One sub-round s of round key rk. Returns the number of applied moves.
+ */
+int64_t orc_lp_subround(const orc_graph *g, int32_t *label, int64_t *lw, int64_t nlabels,
+                        int64_t cap_uniform, const int64_t *cap, uint64_t rk, int32_t S, int32_t s);
+int64_t orc_lp_rounds(const orc_graph *g, int32_t *label, int64_t *lw, int64_t nlabels,
+                      int64_t cap_uniform, const int64_t *cap, uint64_t seed, uint64_t tag,
+                      uint64_t a, uint64_t b0, int32_t rounds, int32_t S);
+void orc_two_hop(const orc_graph *g, int32_t *C, const int64_t *Wc, int64_t U, uint64_t seed,
+                 int64_t level);
+/* Full clustering of one coarsening level: singletons, LP rounds, two-hop. */
+void orc_cluster(const orc_graph *g, int64_t U, const orc_params *p, int64_t level, int32_t *C);
+
+/* ---- contraction (Section "Contraction") ---- */
+/* Fills *out (arrays malloc'ed, release with orc_graph_free) and map[n].
+ * Returns n'. */
+int64_t orc_contract(const orc_graph *g, const int32_t *C, orc_graph *out, int32_t *map);
+void orc_graph_free(orc_graph *g);
+
+/* ---- initial partitioning, refinement, balance, metrics ---- */
+void orc_initial_partition(const orc_graph *g, int32_t k, int64_t l_max, const orc_params *p,
+                           int32_t *part);
+void orc_block_weights(const orc_graph *g, const int32_t *part, int32_t k, int64_t *B);
+int64_t orc_cut(const orc_graph *g, const int32_t *part);
+int orc_rebalance(const orc_graph *g, int32_t *part, int64_t *B, int32_t k, int64_t l_max);
+int64_t orc_refine(const orc_graph *g, int32_t *part, int64_t *B, int32_t k, int64_t l_max,
+                   const orc_params *p, int64_t level);
+int64_t orc_cluster_cap(int64_t W, int32_t k, int64_t eps_ppm);
+int64_t orc_block_cap(int64_t W, int32_t k, int64_t eps_ppm);
+int orc_validate(const orc_graph *g);
+int orc_partition(const orc_graph *g, int32_t k, int64_t eps_ppm, const orc_params *p,
+                  int32_t *part, orc_stats *st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

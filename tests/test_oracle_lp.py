@@ -1,0 +1,157 @@
+"""Pins for the oracle's hashing and label propagation (Algorithm 1 made
+synchronous; size constraint; two-hop packing)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import _brute as bf
+
+# splitmix64 started from state 0 (published reference outputs of the
+# generator of Steele, Lea and Flood): outputs are mix64(i * gamma), i = 1, 2, 3.
+SPLITMIX64_FROM_ZERO = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_mix64_published_vectors():
+    g = bf.GAMMA
+    for i, want in enumerate(SPLITMIX64_FROM_ZERO, start=1):
+        assert oracle.mix64((i * g) & bf.M64) == want
+    # step(h, x) absorbs x + gamma: from h = 0 it is the first output
+    assert oracle.step(0, 0) == SPLITMIX64_FROM_ZERO[0]
+    assert oracle.step(0, g) == SPLITMIX64_FROM_ZERO[1]
+
+
+def test_hash_agrees_with_bruteforce():
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        a, b, c, d = (int(x) for x in rng.integers(0, 2**63, 4))
+        assert oracle.round_key(a, b, c, d) == bf.round_key(a, b, c, d)
+    tags = {oracle.tag(i) for i in range(6)}
+    assert len(tags) == 6 and 0 not in tags
+
+
+def _tiny(seed, n=10, p=0.35, max_w=3):
+    rng = np.random.default_rng(seed)
+    xadj, adj, ew, vw = bf.random_graph(rng, n, p, max_w)
+    return rng, xadj, adj, ew, vw
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_rating_argmax_by_enumeration(seed):
+    rng, xadj, adj, ew, vw = _tiny(seed)
+    n = len(xadj) - 1
+    g = oracle.Graph(xadj, adj, vw, ew)
+    nlabels = n
+    label = rng.integers(0, nlabels, size=n).astype(np.int32)
+    lw = np.zeros(nlabels, np.int64)
+    np.add.at(lw, label, vw)
+    cap = rng.integers(1, 12, size=nlabels).astype(np.int64)
+    for u in range(n):
+        for ignore in (False, True):
+            hv = int(rng.integers(0, 2**63))
+            got = oracle.rate_vertex(g, u, label, lw, 0, cap, ignore, hv)
+            want = bf.rate(xadj, adj, ew, vw, u, label, lw, nlabels, cap, ignore, hv)
+            assert got[0] == want[0], (u, got, want)
+            if want[0]:
+                assert got[1:] == want[1:], (u, got, want)
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_subround_by_enumeration(seed):
+    rng, xadj, adj, ew, vw = _tiny(100 + seed, n=12, p=0.4, max_w=4)
+    n = len(xadj) - 1
+    g = oracle.Graph(xadj, adj, vw, ew)
+    S = int(rng.integers(1, 4))
+    nlabels = n
+    label = np.arange(n, dtype=np.int32)
+    lw = vw.copy()
+    capv = int(rng.integers(1, 10))
+    cap = np.full(nlabels, capv, np.int64)
+    for r in range(3):
+        rk = int(rng.integers(0, 2**63))
+        for s in range(S):
+            want_l, want_w = bf.subround(xadj, adj, ew, vw, label, lw, nlabels, cap, rk, S, s,
+                                         oracle.tag(oracle.TAG_TIE))
+            oracle.lp_subround(g, label, lw, nlabels, capv, None, rk, S, s)
+            assert np.array_equal(label, want_l) and np.array_equal(lw, want_w)
+
+
+@pytest.mark.parametrize("kind", ["gnm", "rgg", "rmat"])
+def test_cluster_cap_invariant(kind):
+    if kind == "gnm":
+        xadj, adj = synth.gnm(4000, 30000, 1)
+    elif kind == "rgg":
+        xadj, adj = synth.rgg2d(4000, 16.0, 1)
+    else:
+        xadj, adj = synth.rmat(12, 16, seed=1)
+    g = oracle.Graph(xadj, adj)
+    n = g.n
+    U = 25
+    p = oracle.Params(two_hop=0)
+    label = np.arange(n, dtype=np.int32)
+    lw = np.ones(n, np.int64)
+    for r in range(5):
+        rk = oracle.round_key(1, oracle.tag(oracle.TAG_CLUSTER), 0, r)
+        for s in range(8):
+            oracle.lp_subround(g, label, lw, n, U, None, rk, 8, s)
+            recount = np.bincount(label, minlength=n)
+            assert np.array_equal(recount, lw)
+            assert lw.max() <= U and lw.sum() == n
+    C = oracle.cluster(g, U, oracle.Params(), 0)
+    sizes = np.bincount(C, minlength=n)
+    assert sizes.max() <= U and sizes.sum() == n
+
+
+def test_first_round_moves_every_nonisolated_vertex_possible():
+    # a path 0-1-2-3: in round 0 every active vertex sees only singletons with
+    # rating 1 > 0 = R[own], so it moves unless its target is full
+    xadj = np.array([0, 1, 3, 5, 6], np.int64)
+    adj = np.array([1, 0, 2, 1, 3, 2], np.int32)
+    g = oracle.Graph(xadj, adj)
+    label = np.arange(4, dtype=np.int32)
+    lw = np.ones(4, np.int64)
+    moved = oracle.lp_subround(g, label, lw, 4, 10, None, 12345, 1, 0)
+    assert moved == 4  # S = 1: all active, all move (to a neighbour's label)
+    assert all(label[u] in (u - 1, u + 1) for u in range(4))
+
+
+def test_two_hop_isolated_packing():
+    # 10 isolated vertices, U = 4: bins of P//4 -> {0..3}, {4..7}, {8, 9}
+    n = 10
+    g = oracle.Graph(np.zeros(n + 1, np.int64), np.zeros(0, np.int32))
+    C = np.arange(n, dtype=np.int32)
+    Wc = np.ones(n, np.int64)
+    oracle.two_hop(g, C, Wc, 4, 1, 0)
+    assert list(C) == [0, 0, 0, 0, 4, 4, 4, 4, 8, 8]
+
+
+def test_two_hop_straddler_stays_alone():
+    # isolated vertices of weights 3,3,3,3 and U = 7: prefixes 0,3,6,9 ->
+    # bins 0,0,0(straddles 6+3>7),1 -> groups {0,1}, {2} alone, {3}
+    n = 4
+    g = oracle.Graph(np.zeros(n + 1, np.int64), np.zeros(0, np.int32), vw=np.full(n, 3))
+    C = np.arange(n, dtype=np.int32)
+    Wc = np.full(n, 3, np.int64)
+    oracle.two_hop(g, C, Wc, 7, 1, 0)
+    assert list(C) == [0, 0, 2, 3]
+
+
+def test_two_hop_shared_favourite():
+    # star: centre 0 with leaves 1..9. The centre's cluster {0,1,2} is full
+    # (U = 3); leaves 3..9 are singletons whose favourite is cluster 0 and get
+    # packed three by three in id order.
+    n = 10
+    xadj = np.zeros(n + 1, np.int64)
+    adj = []
+    nb = {0: list(range(1, n))}
+    for v in range(1, n):
+        nb[v] = [0]
+    for u in range(n):
+        adj += nb[u]
+        xadj[u + 1] = len(adj)
+    g = oracle.Graph(xadj, np.array(adj, np.int32))
+    C = np.array([0, 0, 0, 3, 4, 5, 6, 7, 8, 9], np.int32)
+    Wc = np.zeros(n, np.int64)
+    np.add.at(Wc, C, 1)
+    oracle.two_hop(g, C, Wc, 3, 1, 0)
+    assert list(C) == [0, 0, 0, 3, 3, 3, 6, 6, 6, 9]

@@ -1,0 +1,145 @@
+"""Pins for the oracle's balance caps, cut, projection, initial partitioning,
+rebalancing, refinement and the multilevel driver (problem statement of the
+paper's introduction; Sections "The Multilevel Scheme" and "KaMinPar")."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import _brute as bf
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_caps_golden():
+    with open(os.path.join(GOLD, "caps.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    for W, k, eps_ppm, l_max, U in (map(int, r) for r in rows):
+        assert oracle.block_cap(W, k, eps_ppm) == l_max
+        assert oracle.cluster_cap(W, k, eps_ppm) == U
+    assert oracle.eps_to_ppm(0.03) == 30000
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_cut_and_weights_bruteforce(seed):
+    rng = np.random.default_rng(seed)
+    xadj, adj, ew, vw = bf.random_graph(rng, 20, 0.3, 7)
+    g = oracle.Graph(xadj, adj, vw, ew)
+    part = rng.integers(0, 4, size=20).astype(np.int32)
+    assert oracle.cut(g, part) == bf.cut(xadj, adj, ew, part)
+    assert np.array_equal(oracle.block_weights(g, part, 4), np.bincount(part, weights=vw, minlength=4))
+
+
+def test_projection_preserves_cut_and_weights():
+    xadj, adj = synth.rgg2d(6000, 16.0, 9)
+    g = oracle.Graph(xadj, adj)
+    C = oracle.cluster(g, 30, oracle.Params(), 0)
+    cg, mp = oracle.contract(g, C)
+    rng = np.random.default_rng(1)
+    coarse_part = rng.integers(0, 8, size=cg.n).astype(np.int32)
+    fine_part = coarse_part[mp]
+    assert oracle.cut(g, fine_part) == oracle.cut(cg, coarse_part)
+    assert np.array_equal(oracle.block_weights(g, fine_part, 8), oracle.block_weights(cg, coarse_part, 8))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_bisection_not_below_optimum(seed):
+    rng = np.random.default_rng(50 + seed)
+    xadj, adj, ew, vw = bf.random_graph(rng, 12, 0.35, 3)
+    g = oracle.Graph(xadj, adj, vw, ew)
+    W = int(vw.sum())
+    l_max = oracle.block_cap(W, 2, 30000)
+    part = oracle.initial_partition(g, 2, l_max, oracle.Params(seed=seed))
+    B = oracle.block_weights(g, part, 2)
+    assert set(np.unique(part)) <= {0, 1}
+    opt = bf.min_bisection_cut(xadj, adj, ew, vw, l_max, l_max)
+    if B.max() <= l_max and opt is not None:
+        assert oracle.cut(g, part) >= opt
+
+
+def test_two_disjoint_cliques_cut_zero():
+    n = 40
+    edges = [(u, v) for base in (0, 20) for u in range(base, base + 20) for v in range(u + 1, base + 20)]
+    nb = [[] for _ in range(n)]
+    for u, v in edges:
+        nb[u].append(v)
+        nb[v].append(u)
+    xadj = np.zeros(n + 1, np.int64)
+    adj = []
+    for u in range(n):
+        adj += sorted(nb[u])
+        xadj[u + 1] = len(adj)
+    g = oracle.Graph(xadj, np.array(adj, np.int32))
+    part, st = oracle.partition(g, 2, 0.03, oracle.Params())
+    assert st["cut"] == 0 and st["balanced"]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_rebalance_by_enumeration(seed):
+    rng = np.random.default_rng(200 + seed)
+    xadj, adj, ew, vw = bf.random_graph(rng, 14, 0.3, 4)
+    g = oracle.Graph(xadj, adj, vw, ew)
+    k = 3
+    part = np.zeros(14, np.int32)
+    part[rng.random(14) < 0.2] = 1
+    B = oracle.block_weights(g, part, k)
+    l_max = int(vw.sum()) // k + 2
+    want_part, want_B, want_r = bf.rebalance(xadj, adj, ew, vw, part, B, k, l_max)
+    got_part, got_B = part.copy(), B.copy()
+    r = oracle.rebalance(g, got_part, got_B, k, l_max)
+    assert r == want_r
+    assert list(got_part) == want_part and list(got_B) == want_B
+    if r == 0:
+        assert got_B.max() <= l_max
+
+
+def test_refine_keeps_caps_and_does_not_raise_cut():
+    xadj, adj = synth.rgg2d(8000, 16.0, 4)
+    g = oracle.Graph(xadj, adj)
+    k = 8
+    rng = np.random.default_rng(3)
+    part = (np.arange(g.n) * k // g.n).astype(np.int32)  # contiguous id ranges
+    B = oracle.block_weights(g, part, k)
+    l_max = oracle.block_cap(g.n, k, 30000)
+    before = oracle.cut(g, part)
+    oracle.refine(g, part, B, k, l_max, oracle.Params(), 0)
+    assert np.array_equal(B, oracle.block_weights(g, part, k))
+    assert B.max() <= l_max
+    # refinement improves this deliberately poor start (contiguous id ranges)
+    assert oracle.cut(g, part) <= before
+
+
+@pytest.mark.parametrize("kind,k", [("gnm", 8), ("rgg", 16), ("rmat", 32)])
+def test_partition_balanced_deterministic(kind, k):
+    if kind == "gnm":
+        xadj, adj = synth.gnm(1 << 13, 1 << 16, 1)
+    elif kind == "rgg":
+        xadj, adj = synth.rgg2d(1 << 14, 16.0, 1)
+    else:
+        xadj, adj = synth.rmat(13, 16, seed=1)
+    g = oracle.Graph(xadj, adj)
+    p = oracle.Params()
+    part, st = oracle.partition(g, k, 0.03, p)
+    assert part.min() >= 0 and part.max() < k
+    assert st["balanced"] and st["max_block_weight"] <= st["l_max"]
+    assert st["cut"] == oracle.cut(g, part)
+    part2, st2 = oracle.partition(g, k, 0.03, p)
+    assert np.array_equal(part, part2) and st == st2
+    # the hierarchy shrinks by at least 5% per level
+    ln = st["level_n"]
+    assert all(20 * b <= 19 * a for a, b in zip(ln, ln[1:]))
+    # a random partition of the same graph cuts more
+    rnd = np.random.default_rng(0).integers(0, k, size=g.n).astype(np.int32)
+    assert st["cut"] < oracle.cut(g, rnd)
+
+
+def test_partition_k1_and_empty():
+    xadj, adj = synth.gnm(100, 300, 1)
+    g = oracle.Graph(xadj, adj)
+    part, st = oracle.partition(g, 1, 0.03, oracle.Params())
+    assert not part.any() and st["cut"] == 0
+    g0 = oracle.Graph(np.zeros(1, np.int64), np.zeros(0, np.int32))
+    part, st = oracle.partition(g0, 4, 0.03, oracle.Params())
+    assert len(part) == 0 and st["cut"] == 0
