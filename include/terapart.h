@@ -1,0 +1,227 @@
+/*
+ * terapart.h — C-ABI of the GB300 (sm_103a) multilevel graph partitioner.
+ *
+ * The library computes the deterministic variant of the multilevel k-way
+ * partitioner of "Tera-Scale Multilevel Graph Partitioning" (TeraPart):
+ * size-constrained label propagation (LP) clustering (Algorithm 1, with the
+ * two-phase idea of Algorithm 2 recast as GPU degree tiers), over either a
+ * plain CSR graph or the paper's gap + VarInt compressed adjacency (Section
+ * "Compression Scheme"), cluster contraction (Section "Contraction"), initial
+ * bisection on the coarsest graph and LP refinement during uncoarsening
+ * (Section "KaMinPar"). Every step runs in the library's CUDA kernels; there is
+ * no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named d_* are device pointers; pointers named h_* are host
+ *    pointers. Graph handles (tp_graph) are opaque, device-resident and own
+ *    their memory until tp_graph_destroy.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is stream-ordered: an entry point may return before its kernels
+ *    finish, except where it says it synchronises.
+ *  - Errors are status codes; nothing throws or aborts across the ABI.
+ *    Errors that kernels detect (a corrupt compressed stream, an exhausted
+ *    spin limit) are latched in the graph's error word and returned by
+ *    tp_graph_check or by the next entry point that synchronises.
+ *  - Vertex ids are int32 (n < 2^31); edge offsets, node and edge weights are
+ *    int64. Graphs are undirected: each edge stored in both directions,
+ *    neighbour lists sorted ascending, no self-loops or duplicates, weights
+ *    positive; tp_graph_from_csr rejects anything else with TP_ERR_INVALID.
+ *  - A handle is not thread-safe; distinct handles may be used concurrently
+ *    on distinct streams.
+ *
+ * Determinism: results depend only on the graph, k, eps and the semantic
+ * fields of tp_params. The performance fields never change a single output
+ * bit; tests run with randomised performance fields to check that.
+ */
+#ifndef TERAPART_H
+#define TERAPART_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TP_OK = 0,
+  TP_ERR_INVALID = 1, /* bad argument or malformed graph */
+  TP_ERR_OOM = 2,     /* device allocation failed (nothing leaked) */
+  TP_ERR_CUDA = 3,    /* a CUDA runtime call failed */
+  TP_ERR_CORRUPT = 4, /* compressed stream failed validation in a kernel */
+  TP_ERR_TIMEOUT = 5, /* a bounded device-side wait ran out */
+  TP_ERR_BUDGET = 6   /* request exceeds a memory budget */
+} tp_status;
+
+typedef struct tp_graph tp_graph;
+
+/* Parameters. The first block is semantic (changes results; the defaults are
+ * the paper's five LP rounds per level and this library's readings of what
+ * the paper leaves open). The second block only steers performance. */
+typedef struct {
+  uint64_t seed;          /* hashing seed (sub-rounds, ties, bisection seeds) */
+  int32_t cluster_rounds; /* LP rounds per coarsening level (5) */
+  int32_t refine_rounds;  /* LP rounds per uncoarsening level and bisection (5) */
+  int32_t sub_rounds;     /* synchronous sub-rounds per round, S (8) */
+  int32_t c_lim;          /* stop coarsening once n <= c_lim * k (160) */
+  int32_t ip_attempts;    /* bisection attempts per tree node, T (8) */
+  int32_t two_hop;        /* pack leftover singletons after clustering (1) */
+  int32_t max_levels;     /* hierarchy depth limit, <= 64 (64) */
+  /* performance only */
+  int32_t tier_small;    /* max degree rated with the small shared table (64) */
+  int32_t tier_mid;      /* max degree rated with the large shared table (1000) */
+  int32_t warps_per_block; /* warps per block in the small tier (8) */
+  int32_t use_graphs;    /* capture LP levels below graph_n into CUDA graphs (1) */
+  int32_t graph_n;       /* see use_graphs (1 << 16) */
+} tp_params;
+
+typedef struct {
+  int64_t cut;              /* edge cut of the final partition */
+  int64_t max_block_weight; /* heaviest block */
+  int64_t l_max;            /* block cap floor((1e6+eps_ppm) ceil(W/k) / 1e6) */
+  int64_t u_max;            /* cluster cap max(1, floor(eps_ppm W / (1e6 k))) */
+  double imbalance;         /* max_block_weight / ceil(W/k) - 1 */
+  int32_t levels;           /* graphs in the hierarchy, input included */
+  int32_t balanced;         /* 1 iff max_block_weight <= l_max */
+  int64_t level_n[64];      /* vertices per level */
+  int64_t level_m2[64];     /* adjacency entries (2m) per level */
+  double ms_coarsen, ms_initial, ms_uncoarsen; /* device time per phase */
+  double ms_lp_level0;      /* device time of the level-0 clustering rounds */
+} tp_stats;
+
+/* Fills p with the defaults listed above. */
+void tp_params_default(tp_params *p);
+
+/* Human-readable name of a status code (static string). */
+const char *tp_status_string(tp_status s);
+
+/* Device memory hook. alloc(bytes, stream, ctx) must return stream-ordered
+ * device memory or NULL; free(ptr, bytes, stream, ctx) releases it. Passing
+ * NULL functions restores the default (cudaMallocAsync / cudaFreeAsync). The
+ * hook is process-wide; set it before creating graphs. */
+tp_status tp_set_allocator(void *(*alloc)(size_t, void *, void *),
+                           void (*free_fn)(void *, size_t, void *, void *), void *ctx);
+
+/* Makes a graph from CSR arrays (Section "Graph Representation": the
+ * neighbours of u are adj[xadj[u] .. xadj[u+1])). host_ptrs = 1: the arrays
+ * are host memory and are copied in; 0: device memory, also copied (the
+ * caller keeps ownership of its arrays either way). vwgt / ewgt may be NULL
+ * for unit weights (kept implicit, no array is stored). The graph is
+ * validated on the device; violations return TP_ERR_INVALID. Synchronises. */
+tp_status tp_graph_from_csr(int64_t n, const int64_t *xadj, const int32_t *adj,
+                            const int64_t *vwgt, const int64_t *ewgt, int host_ptrs,
+                            void *stream, tp_graph **out);
+
+/* Compresses a unit-weight CSR graph into the gap + VarInt format of Section
+ * "Compression Scheme": per vertex a VarInt header holding its first edge id,
+ * then (degree > 10 000) a table of nchunks-1 little-endian u32 chunk offsets
+ * relative to the neighbourhood start and chunks of 1 000 neighbours, each
+ * chunk starting with VarInt(2|v0-u| + [v0<u]) followed by VarInt gaps; a
+ * terminal header holding 2m sits at off[n]. Offsets are u32 when the stream
+ * is below 4 GiB, else u64. TP_ERR_INVALID for weighted graphs or an already
+ * compressed input. Synchronises (to size the output). */
+tp_status tp_graph_compress(const tp_graph *csr, void *stream, tp_graph **out);
+
+/* Makes a compressed graph from a stream in the format above: nbytes bytes
+ * and n+1 u64 offsets (host_ptrs as for tp_graph_from_csr; copied in). Every
+ * neighbourhood is decoded once on the device to validate it; a malformed
+ * stream (bad header, truncated VarInt, id out of range, wrong chunk table,
+ * unsorted ids) gives TP_ERR_CORRUPT. Synchronises. */
+tp_status tp_graph_from_compressed(int64_t n, uint64_t nbytes, const uint8_t *bytes,
+                                   const uint64_t *off, int host_ptrs, void *stream,
+                                   tp_graph **out);
+
+/* Decodes a compressed graph back to CSR (round-trip check); corrupt streams
+ * give TP_ERR_CORRUPT. Synchronises. */
+tp_status tp_graph_decompress(const tp_graph *g, void *stream, tp_graph **out_csr);
+
+/* Sizes of a graph: n, adjacency entries 2m, whether it is compressed, the
+ * bytes its arrays occupy on the device, and (compressed graphs) the length
+ * of the byte stream alone. Any output pointer may be NULL. */
+tp_status tp_graph_info(const tp_graph *g, int64_t *n, int64_t *m2, int *compressed,
+                        size_t *bytes, size_t *stream_bytes);
+
+/* Copies a CSR graph out to caller device buffers (xadj n+1, adj 2m, vw n,
+ * ew 2m; any may be NULL; unit weights are written as ones). */
+tp_status tp_graph_export_csr(const tp_graph *g, int64_t *d_xadj, int32_t *d_adj, int64_t *d_vw,
+                              int64_t *d_ew, void *stream);
+
+/* Copies a compressed graph out: d_bytes gets the stream (size from
+ * tp_graph_info), d_off gets n+1 offsets widened to u64. */
+tp_status tp_graph_export_compressed(const tp_graph *g, uint8_t *d_bytes, uint64_t *d_off,
+                                     void *stream);
+
+/* Returns (and clears) the error latched by kernels working on g. Synchronises. */
+tp_status tp_graph_check(const tp_graph *g, void *stream);
+
+void tp_graph_destroy(tp_graph *g);
+
+/* One synchronous LP sub-round (Algorithm 1 restricted to the vertices u with
+ * hash(round_key, u) mod S == s) on caller state: d_label[n] in [0, nlabels),
+ * d_lw[nlabels] the label weights (sum of node weights per label). A vertex
+ * moves to the admissible label with the largest rating (ties: 32-bit tie
+ * hash, then label) if that rating exceeds the rating of its own label;
+ * admissible means lw + c(u) <= cap. Movers into a label whose weight would
+ * overflow are approved in (gain desc, vertex asc) order while the inclusive
+ * prefix fits. round_key = hash(seed, phase tag, a, b) as documented in the
+ * library's determinism notes. In place on d_label and d_lw. */
+tp_status tp_lp_subround(const tp_graph *g, int32_t *d_label, int64_t *d_lw, int64_t nlabels,
+                         int64_t cap, uint64_t round_key, int32_t S, int32_t s, void *stream);
+
+/* Size-constrained LP clustering of one coarsening level (Algorithm 1;
+ * Algorithm 2's split into low-degree and high-degree work becomes the
+ * library's degree tiers and never changes the result): singleton start,
+ * p->cluster_rounds rounds of p->sub_rounds sub-rounds with cluster cap
+ * max_cluster_weight, then (p->two_hop) packing of leftover singletons that
+ * share a favourite cluster. d_cluster[n] receives the cluster label of
+ * every vertex (a label is a vertex id). */
+tp_status tp_lp_cluster(const tp_graph *g, int64_t max_cluster_weight, const tp_params *p,
+                        int32_t level, int32_t *d_cluster, void *stream);
+
+/* Contraction (Section "Contraction"): coarse vertex = cluster, coarse ids =
+ * ranks of the labels in ascending order, coarse node weight = cluster
+ * weight, coarse edge weight w'(a,b) = sum of w(u,v) over fine edges between
+ * the clusters (intra-cluster edges dropped), neighbours sorted ascending.
+ * *coarse receives a new CSR graph; d_map[n] (nullable) the coarse id of
+ * every fine vertex. Synchronises (to size the coarse graph). */
+tp_status tp_contract(const tp_graph *g, const int32_t *d_cluster, void *stream,
+                      tp_graph **coarse, int32_t *d_map);
+
+/* Initial partition of (usually) the coarsest graph by recursive bisection
+ * (Section "KaMinPar": greedy graph growing plus 2-way refinement; here BFS
+ * growing plus 2-way LP, p->ip_attempts seeded attempts per bisection, the
+ * smallest cut wins). d_part[n] receives blocks in [0, k). Synchronises. */
+tp_status tp_initial_partition(const tp_graph *g, int32_t k, int64_t l_max, const tp_params *p,
+                               int32_t *d_part, void *stream);
+
+/* Size-constrained LP refinement (Section "KaMinPar"): p->refine_rounds rounds
+ * of LP over blocks with cap l_max, in place on d_part[n]. */
+tp_status tp_lp_refine(const tp_graph *g, int32_t k, int64_t l_max, const tp_params *p,
+                       int32_t level, int32_t *d_part, void *stream);
+
+/* Greedy rebalancing: while a block exceeds l_max, move the vertex of the
+ * lowest-index overloaded block with the smallest connectivity loss to the
+ * best admissible block. *balanced = 1 when done, 0 if no vertex fits.
+ * Synchronises. */
+tp_status tp_rebalance(const tp_graph *g, int32_t k, int64_t l_max, int32_t *d_part,
+                       int *balanced, void *stream);
+
+/* Edge cut and block weights of a partition (problem statement of the
+ * paper's introduction). h_block_weights (nullable) has k entries.
+ * Synchronises. */
+tp_status tp_metrics(const tp_graph *g, const int32_t *d_part, int32_t k, int64_t *cut,
+                     int64_t *h_block_weights, void *stream);
+
+/* The full multilevel partitioner (Section "The Multilevel Scheme"):
+ * coarsen with LP clustering + contraction until n <= c_lim * k (or a level
+ * shrinks by less than 5%, or max_levels), partition the coarsest graph,
+ * then per level project, rebalance if needed and refine. Block cap
+ * L_max = floor((1e6 + eps_ppm) * ceil(W/k) / 1e6), eps_ppm = llround(eps * 1e6).
+ * p may be NULL (defaults). d_part[n] receives blocks in [0, k). stats
+ * (nullable) is filled on return; the call synchronises the stream. */
+tp_status tp_partition(const tp_graph *g, int32_t k, double eps, const tp_params *p,
+                       int32_t *d_part, tp_stats *stats, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

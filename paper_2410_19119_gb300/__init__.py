@@ -1,0 +1,226 @@
+"""GB300 (sm_103a) multilevel graph partitioner after "Tera-Scale Multilevel
+Graph Partitioning" (TeraPart): deterministic size-constrained label
+propagation over CSR or gap+VarInt compressed graphs, contraction, initial
+bisection and LP refinement, all in CUDA kernels behind the C-ABI of
+include/terapart.h.
+
+This module marshals arguments only. PyTorch provides device memory and
+streams; numpy arrays are accepted as host inputs.
+"""
+import ctypes
+
+import numpy as np
+
+from ._lib import Params, Stats, TpError, check, lib
+
+__all__ = ["Graph", "Params", "Stats", "TpError", "default_params", "graph_from_csr",
+           "graph_from_compressed", "partition", "lp_cluster", "lp_subround", "contract",
+           "initial_partition", "lp_refine", "rebalance", "metrics"]
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(x):
+    """Device pointer of a CUDA tensor or host pointer of a numpy array."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags.c_contiguous
+        return ctypes.c_void_p(x.ctypes.data)
+    assert x.is_contiguous()
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def default_params(**overrides) -> Params:
+    p = Params()
+    lib().tp_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Graph:
+    """Owning handle of a device-resident graph (CSR or compressed)."""
+
+    def __init__(self, handle):
+        self._h = ctypes.c_void_p(handle) if not isinstance(handle, ctypes.c_void_p) else handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        n, m2, comp = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        nb, sb = ctypes.c_size_t(), ctypes.c_size_t()
+        check(lib().tp_graph_info(self._h, ctypes.byref(n), ctypes.byref(m2), ctypes.byref(comp),
+                                  ctypes.byref(nb), ctypes.byref(sb)), "tp_graph_info")
+        return {"n": n.value, "m2": m2.value, "compressed": bool(comp.value), "bytes": nb.value,
+                "stream_bytes": sb.value}
+
+    @property
+    def n(self):
+        return self.info()["n"]
+
+    def compress(self, stream=None) -> "Graph":
+        out = ctypes.c_void_p()
+        check(lib().tp_graph_compress(self._h, _stream(stream), ctypes.byref(out)),
+              "tp_graph_compress")
+        return Graph(out)
+
+    def decompress(self, stream=None) -> "Graph":
+        out = ctypes.c_void_p()
+        check(lib().tp_graph_decompress(self._h, _stream(stream), ctypes.byref(out)),
+              "tp_graph_decompress")
+        return Graph(out)
+
+    def export_csr(self, stream=None):
+        torch = _torch()
+        inf = self.info()
+        n, m2 = inf["n"], inf["m2"]
+        xadj = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        adj = torch.empty(max(m2, 1), dtype=torch.int32, device="cuda")
+        vw = torch.empty(max(n, 1), dtype=torch.int64, device="cuda")
+        ew = torch.empty(max(m2, 1), dtype=torch.int64, device="cuda")
+        check(lib().tp_graph_export_csr(self._h, _ptr(xadj), _ptr(adj), _ptr(vw), _ptr(ew),
+                                        _stream(stream)), "tp_graph_export_csr")
+        return xadj, adj[:m2], vw[:n], ew[:m2]
+
+    def export_compressed(self, stream=None):
+        torch = _torch()
+        inf = self.info()
+        n, nbytes = inf["n"], inf["stream_bytes"]
+        data = torch.empty(max(nbytes, 1), dtype=torch.uint8, device="cuda")
+        off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        check(lib().tp_graph_export_compressed(self._h, _ptr(data), _ptr(off), _stream(stream)),
+              "tp_graph_export_compressed")
+        return data[:nbytes], off
+
+    def check(self, stream=None):
+        check(lib().tp_graph_check(self._h, _stream(stream)), "tp_graph_check")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                lib().tp_graph_destroy(h)
+            except Exception:
+                pass
+            self._h = ctypes.c_void_p()
+
+
+def graph_from_csr(xadj, adj, vw=None, ew=None, stream=None) -> Graph:
+    """xadj int64[n+1], adj int32[2m] (numpy = host, torch CUDA = device)."""
+    host = isinstance(xadj, np.ndarray)
+    if host:
+        xadj = np.ascontiguousarray(xadj, np.int64)
+        adj = np.ascontiguousarray(adj, np.int32)
+        vw = None if vw is None else np.ascontiguousarray(vw, np.int64)
+        ew = None if ew is None else np.ascontiguousarray(ew, np.int64)
+    out = ctypes.c_void_p()
+    check(lib().tp_graph_from_csr(len(xadj) - 1, _ptr(xadj), _ptr(adj), _ptr(vw), _ptr(ew),
+                                  int(host), _stream(stream), ctypes.byref(out)),
+          "tp_graph_from_csr")
+    return Graph(out)
+
+
+def graph_from_compressed(n, data, off, stream=None) -> Graph:
+    host = isinstance(data, np.ndarray)
+    if host:
+        data = np.ascontiguousarray(data, np.uint8)
+        off = np.ascontiguousarray(off, np.uint64)
+    out = ctypes.c_void_p()
+    nbytes = len(data) if host else data.numel()
+    check(lib().tp_graph_from_compressed(n, nbytes, _ptr(data), _ptr(off), int(host),
+                                         _stream(stream), ctypes.byref(out)),
+          "tp_graph_from_compressed")
+    return Graph(out)
+
+
+def lp_subround(g: Graph, label, lw, cap, round_key, S, s, stream=None):
+    """One synchronous LP sub-round in place on label (int32 CUDA) and lw (int64 CUDA)."""
+    check(lib().tp_lp_subround(g.handle, _ptr(label), _ptr(lw), lw.numel(), cap, round_key, S, s,
+                               _stream(stream)), "tp_lp_subround")
+
+
+def lp_cluster(g: Graph, max_cluster_weight, params=None, level=0, stream=None):
+    torch = _torch()
+    p = params or default_params()
+    C = torch.empty(max(g.n, 1), dtype=torch.int32, device="cuda")
+    check(lib().tp_lp_cluster(g.handle, max_cluster_weight, ctypes.byref(p), level, _ptr(C),
+                              _stream(stream)), "tp_lp_cluster")
+    return C[: g.n]
+
+
+def contract(g: Graph, C, stream=None):
+    torch = _torch()
+    out = ctypes.c_void_p()
+    mp = torch.empty(max(g.n, 1), dtype=torch.int32, device="cuda")
+    check(lib().tp_contract(g.handle, _ptr(C), _stream(stream), ctypes.byref(out), _ptr(mp)),
+          "tp_contract")
+    return Graph(out), mp[: g.n]
+
+
+def initial_partition(g: Graph, k, l_max, params=None, stream=None):
+    torch = _torch()
+    p = params or default_params()
+    part = torch.empty(max(g.n, 1), dtype=torch.int32, device="cuda")
+    check(lib().tp_initial_partition(g.handle, k, l_max, ctypes.byref(p), _ptr(part),
+                                     _stream(stream)), "tp_initial_partition")
+    return part[: g.n]
+
+
+def lp_refine(g: Graph, k, l_max, part, params=None, level=0, stream=None):
+    p = params or default_params()
+    check(lib().tp_lp_refine(g.handle, k, l_max, ctypes.byref(p), level, _ptr(part),
+                             _stream(stream)), "tp_lp_refine")
+    return part
+
+
+def rebalance(g: Graph, k, l_max, part, stream=None):
+    ok = ctypes.c_int()
+    check(lib().tp_rebalance(g.handle, k, l_max, _ptr(part), ctypes.byref(ok), _stream(stream)),
+          "tp_rebalance")
+    return bool(ok.value)
+
+
+def metrics(g: Graph, part, k, stream=None):
+    cut = ctypes.c_int64()
+    B = np.zeros(k, np.int64)
+    check(lib().tp_metrics(g.handle, _ptr(part), k, ctypes.byref(cut), _ptr(B), _stream(stream)),
+          "tp_metrics")
+    return cut.value, B
+
+
+def stats_dict(st: Stats):
+    L = st.levels
+    return {"cut": st.cut, "max_block_weight": st.max_block_weight, "l_max": st.l_max,
+            "u_max": st.u_max, "imbalance": st.imbalance, "levels": L,
+            "balanced": bool(st.balanced), "level_n": list(st.level_n[:L]),
+            "level_m2": list(st.level_m2[:L]), "ms_coarsen": st.ms_coarsen,
+            "ms_initial": st.ms_initial, "ms_uncoarsen": st.ms_uncoarsen,
+            "ms_lp_level0": st.ms_lp_level0}
+
+
+def partition(g: Graph, k, eps=0.03, params=None, out=None, stream=None):
+    """Full multilevel partition. Returns (part int32 CUDA tensor, stats dict)."""
+    torch = _torch()
+    p = params or default_params()
+    n = g.n
+    part = out if out is not None else torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    st = Stats()
+    check(lib().tp_partition(g.handle, k, eps, ctypes.byref(p), _ptr(part), ctypes.byref(st),
+                             _stream(stream)), "tp_partition")
+    return part[:n], stats_dict(st)
+

@@ -1,0 +1,262 @@
+// extern "C" entry points declared in include/terapart.h.
+#include <math.h>
+
+#include <algorithm>
+
+#include "tp_internal.cuh"
+
+namespace tp {
+tp_graph *from_csr(int64_t n, const int64_t *xadj, const int32_t *adj, const int64_t *vwgt,
+                   const int64_t *ewgt, int host, cudaStream_t s);
+tp_graph *compress(const tp_graph *c, cudaStream_t s);
+tp_graph *decompress(const tp_graph *z, cudaStream_t s);
+tp_graph *from_compressed(int64_t n, uint64_t nbytes, const uint8_t *bytes, const uint64_t *off,
+                          int host, cudaStream_t s);
+void export_csr(const tp_graph *g, int64_t *xadj, int32_t *adj, int64_t *vw, int64_t *ew,
+                cudaStream_t s);
+void export_compressed(const tp_graph *g, uint8_t *bytes, uint64_t *off, cudaStream_t s);
+void partition(tp_graph *g0, int32_t k, int64_t eps_ppm, const tp_params &p, int32_t *d_part,
+               tp_stats *st, cudaStream_t s);
+
+namespace {
+void pool_setup() {
+  static bool done = false;
+  if (done) return;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;  // keep freed blocks cached in this process
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  }
+  done = true;
+}
+
+bool params_ok(const tp_params &p) {
+  return p.cluster_rounds >= 0 && p.refine_rounds >= 0 && p.sub_rounds >= 1 && p.c_lim >= 1 &&
+         p.ip_attempts >= 1 && p.max_levels >= 1 && p.max_levels <= 64;
+}
+
+tp_params resolve(const tp_params *p) {
+  tp_params q;
+  if (p) q = *p;
+  else tp_params_default(&q);
+  TP_REQUIRE(params_ok(q), TP_ERR_INVALID);
+  return q;
+}
+
+int64_t eps_ppm_of(double eps) { return (int64_t)llround(eps * 1e6); }
+}  // namespace
+}  // namespace tp
+
+using namespace tp;
+
+extern "C" {
+
+void tp_params_default(tp_params *p) {
+  p->seed = 1;
+  p->cluster_rounds = 5;
+  p->refine_rounds = 5;
+  p->sub_rounds = 8;
+  p->c_lim = 160;
+  p->ip_attempts = 8;
+  p->two_hop = 1;
+  p->max_levels = 64;
+  p->tier_small = 64;
+  p->tier_mid = 1000;
+  p->warps_per_block = 8;
+  p->use_graphs = 1;
+  p->graph_n = 1 << 16;
+}
+
+const char *tp_status_string(tp_status s) {
+  switch (s) {
+  case TP_OK: return "ok";
+  case TP_ERR_INVALID: return "invalid argument or graph";
+  case TP_ERR_OOM: return "out of device memory";
+  case TP_ERR_CUDA: return "CUDA runtime error";
+  case TP_ERR_CORRUPT: return "corrupt compressed graph";
+  case TP_ERR_TIMEOUT: return "device wait timed out";
+  case TP_ERR_BUDGET: return "memory budget exceeded";
+  }
+  return "unknown status";
+}
+
+tp_status tp_set_allocator(void *(*alloc)(size_t, void *, void *),
+                           void (*free_fn)(void *, size_t, void *, void *), void *ctx);
+
+tp_status tp_graph_from_csr(int64_t n, const int64_t *xadj, const int32_t *adj,
+                            const int64_t *vwgt, const int64_t *ewgt, int host_ptrs, void *stream,
+                            tp_graph **out) {
+  if (!out) return TP_ERR_INVALID;
+  *out = nullptr;
+  return guard([&] {
+    pool_setup();
+    *out = from_csr(n, xadj, adj, vwgt, ewgt, host_ptrs, (cudaStream_t)stream);
+  });
+}
+
+tp_status tp_graph_compress(const tp_graph *csr, void *stream, tp_graph **out) {
+  if (!csr || !out) return TP_ERR_INVALID;
+  *out = nullptr;
+  return guard([&] { *out = compress(csr, (cudaStream_t)stream); });
+}
+
+tp_status tp_graph_from_compressed(int64_t n, uint64_t nbytes, const uint8_t *bytes,
+                                   const uint64_t *off, int host_ptrs, void *stream,
+                                   tp_graph **out) {
+  if (!out) return TP_ERR_INVALID;
+  *out = nullptr;
+  return guard([&] {
+    pool_setup();
+    *out = from_compressed(n, nbytes, bytes, off, host_ptrs, (cudaStream_t)stream);
+  });
+}
+
+tp_status tp_graph_decompress(const tp_graph *g, void *stream, tp_graph **out_csr) {
+  if (!g || !out_csr) return TP_ERR_INVALID;
+  *out_csr = nullptr;
+  return guard([&] { *out_csr = decompress(g, (cudaStream_t)stream); });
+}
+
+tp_status tp_graph_info(const tp_graph *g, int64_t *n, int64_t *m2, int *compressed,
+                        size_t *bytes, size_t *stream_bytes) {
+  if (!g) return TP_ERR_INVALID;
+  if (stream_bytes) *stream_bytes = g->compressed ? g->nbytes : 0;
+  if (n) *n = g->n;
+  if (m2) *m2 = g->m2;
+  if (compressed) *compressed = g->compressed;
+  if (bytes) {
+    if (g->compressed)
+      *bytes = g->nbytes + (g->n + 1) * (g->off_is64 ? 8 : 4);
+    else
+      *bytes = (g->n + 1) * 8 + g->m2 * 4 + (g->unit_vw ? 0 : g->n * 8) +
+               (g->unit_ew ? 0 : g->m2 * 8);
+  }
+  return TP_OK;
+}
+
+tp_status tp_graph_export_csr(const tp_graph *g, int64_t *d_xadj, int32_t *d_adj, int64_t *d_vw,
+                              int64_t *d_ew, void *stream) {
+  if (!g) return TP_ERR_INVALID;
+  return guard([&] { export_csr(g, d_xadj, d_adj, d_vw, d_ew, (cudaStream_t)stream); });
+}
+
+tp_status tp_graph_export_compressed(const tp_graph *g, uint8_t *d_bytes, uint64_t *d_off,
+                                     void *stream) {
+  if (!g) return TP_ERR_INVALID;
+  return guard([&] { export_compressed(g, d_bytes, d_off, (cudaStream_t)stream); });
+}
+
+tp_status tp_graph_check(const tp_graph *g, void *stream) {
+  if (!g) return TP_ERR_INVALID;
+  tp_status st = TP_OK;
+  tp_status r = guard([&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t e = read_scalar(g->err.get(), s);
+    if (e) TP_CUDA(cudaMemsetAsync(g->err.get(), 0, sizeof(int32_t), s));
+    TP_CUDA(cudaStreamSynchronize(s));
+    st = (tp_status)e;
+  });
+  return r != TP_OK ? r : st;
+}
+
+void tp_graph_destroy(tp_graph *g) { delete g; }
+
+tp_status tp_lp_subround(const tp_graph *g, int32_t *d_label, int64_t *d_lw, int64_t nlabels,
+                         int64_t cap, uint64_t round_key, int32_t S, int32_t s, void *stream) {
+  if (!g || S < 1 || s < 0 || s >= S || nlabels < 1) return TP_ERR_INVALID;
+  return guard([&] {
+    cudaStream_t st = (cudaStream_t)stream;
+    tp_params p;
+    tp_params_default(&p);
+    LpWork w;
+    w.init(g->n, nlabels, st);
+    LpState state{d_label, d_lw, nlabels, cap};
+    lp_subround(const_cast<tp_graph *>(g), state, w, round_key, S, s, p, st);
+    TP_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
+tp_status tp_lp_cluster(const tp_graph *g, int64_t max_cluster_weight, const tp_params *p,
+                        int32_t level, int32_t *d_cluster, void *stream) {
+  if (!g || max_cluster_weight < 1 || (g->n && !d_cluster)) return TP_ERR_INVALID;
+  return guard([&] {
+    tp_params q = resolve(p);
+    lp_cluster(const_cast<tp_graph *>(g), max_cluster_weight, q, level, d_cluster,
+               (cudaStream_t)stream);
+  });
+}
+
+tp_status tp_contract(const tp_graph *g, const int32_t *d_cluster, void *stream,
+                      tp_graph **coarse, int32_t *d_map) {
+  if (!g || !coarse || (g->n && !d_cluster)) return TP_ERR_INVALID;
+  *coarse = nullptr;
+  return guard([&] { *coarse = contract(g, d_cluster, d_map, (cudaStream_t)stream); });
+}
+
+tp_status tp_initial_partition(const tp_graph *g, int32_t k, int64_t l_max, const tp_params *p,
+                               int32_t *d_part, void *stream) {
+  if (!g || k < 1 || (g->n && !d_part)) return TP_ERR_INVALID;
+  return guard([&] {
+    tp_params q = resolve(p);
+    initial_partition(g, k, l_max, q, d_part, (cudaStream_t)stream);
+    TP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  });
+}
+
+tp_status tp_lp_refine(const tp_graph *g, int32_t k, int64_t l_max, const tp_params *p,
+                       int32_t level, int32_t *d_part, void *stream) {
+  if (!g || k < 1 || (g->n && !d_part)) return TP_ERR_INVALID;
+  return guard([&] {
+    tp_params q = resolve(p);
+    cudaStream_t s = (cudaStream_t)stream;
+    Buf<int64_t> B(k, s);
+    block_weights(g, d_part, k, B.get(), s);
+    lp_refine(const_cast<tp_graph *>(g), k, l_max, q, level, d_part, B.get(), s);
+  });
+}
+
+tp_status tp_rebalance(const tp_graph *g, int32_t k, int64_t l_max, int32_t *d_part,
+                       int *balanced, void *stream) {
+  if (!g || k < 1 || (g->n && !d_part)) return TP_ERR_INVALID;
+  return guard([&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    tp_params q;
+    tp_params_default(&q);
+    Buf<int64_t> B(k, s);
+    block_weights(g, d_part, k, B.get(), s);
+    int ok = 1;
+    rebalance_moves(const_cast<tp_graph *>(g), k, l_max, d_part, B.get(), &ok, q, s);
+    TP_CUDA(cudaStreamSynchronize(s));
+    if (balanced) *balanced = ok;
+  });
+}
+
+tp_status tp_metrics(const tp_graph *g, const int32_t *d_part, int32_t k, int64_t *cut,
+                     int64_t *h_block_weights, void *stream) {
+  if (!g || k < 1 || (g->n && !d_part)) return TP_ERR_INVALID;
+  return guard([&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h_block_weights) {
+      Buf<int64_t> B(k, s);
+      block_weights(g, d_part, k, B.get(), s);
+      TP_CUDA(cudaMemcpyAsync(h_block_weights, B.get(), k * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    }
+    int64_t c = edge_cut(g, d_part, s);
+    if (cut) *cut = c;
+  });
+}
+
+tp_status tp_partition(const tp_graph *g, int32_t k, double eps, const tp_params *p,
+                       int32_t *d_part, tp_stats *stats, void *stream) {
+  if (!g || k < 1 || !(eps >= 0.0 && eps < 1.0) || (g->n && !d_part)) return TP_ERR_INVALID;
+  return guard([&] {
+    tp_params q = resolve(p);
+    partition(const_cast<tp_graph *>(g), k, eps_ppm_of(eps), q, d_part, stats,
+              (cudaStream_t)stream);
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,431 @@
+// Initial partitioning of the coarsest graph by recursive bisection (the
+// paper's KaMinPar uses a portfolio of greedy graph growing and 2-way FM,
+// Section "KaMinPar"). Deterministic GPU form: every node of the bisection
+// tree owns the blocks [offset, offset + kk); its vertices are bisected with
+// kk0 = ceil(kk/2) and kk1 = floor(kk/2) blocks per side by T seeded attempts,
+// one CTA each:
+//   1. BFS from a hashed seed vertex (FIFO order, neighbours in ascending id,
+//      unreached vertices appended in ascending id), computed level by level:
+//      a vertex joins the next frontier behind the earliest frontier vertex
+//      adjacent to it;
+//   2. side 0 = the longest prefix of that order weighing at most
+//      floor(W_sub * kk0 / kk);
+//   3. refine_rounds rounds of 2-way label propagation with side caps
+//      kk0 * L_max and kk1 * L_max and the same prefix approval as k-way LP;
+//   4. the cut of the induced subgraph.
+// The attempt with the smallest cut (lowest attempt on ties) wins; the tree
+// is processed depth by depth, all nodes of a depth in one launch.
+#include <algorithm>
+#include <vector>
+
+#include "tp_internal.cuh"
+
+namespace tp {
+
+namespace {
+
+constexpr int kIPThreads = 512;
+
+struct IPCtx {
+  int64_t n;
+  const int64_t *xadj;
+  const int32_t *adj;
+  const int64_t *vw, *ew;  // null: unit
+  const int32_t *node_of;  // node index per vertex (-1: done)
+  const int32_t *vlist;    // vertices sorted by (node, id)
+  const int64_t *nstart;   // node start in vlist
+  const int32_t *loc;      // position of a vertex inside its node
+  const int32_t *noff, *nkk;
+  int32_t T;
+  uint64_t seed;
+  int64_t l_max;
+  int32_t rounds, S;
+  // scratch, T * n entries each
+  int32_t *ord, *disc, *claimer, *cnt, *side, *mvx0, *mvx1, *ok0, *ok1;
+  int64_t *mvg0, *mvg1;
+  int64_t *cut;  // nodes * T
+};
+
+__device__ __forceinline__ int64_t bscan_excl(int64_t v, int64_t &total) {
+  __shared__ int64_t ws[kIPThreads / 32];
+  int l = lane_id(), w = threadIdx.x >> 5;
+  int64_t incl = warp_incl_scan(v);
+  if (l == 31) ws[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int64_t x = l < kIPThreads / 32 ? ws[l] : 0;
+    x = warp_incl_scan(x);
+    if (l < kIPThreads / 32) ws[l] = x;
+  }
+  __syncthreads();
+  int64_t off = w > 0 ? ws[w - 1] : 0;
+  total = ws[kIPThreads / 32 - 1];
+  __syncthreads();
+  return off + incl - v;
+}
+
+__device__ __forceinline__ int64_t bsum(int64_t v) {
+  int64_t t;
+  bscan_excl(v, t);
+  return t;
+}
+
+// Weighted radix select (same contract as in lp.cu): first key in ascending
+// (hi, lo) order whose inclusive weight prefix exceeds rem.
+template <class Item>
+__device__ void ip_select(int64_t cnt, int64_t rem, Item item, uint64_t &khi, uint32_t &klo) {
+  __shared__ int64_t hist[256];
+  __shared__ uint64_t fhi, mhi;
+  __shared__ uint32_t flo, mlo;
+  __shared__ int64_t cum;
+  if (threadIdx.x == 0) fhi = 0, mhi = 0, flo = 0, mlo = 0, cum = 0;
+  __syncthreads();
+  for (int pass = 0; pass < 12; ++pass) {
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const bool in_hi = pass < 8;
+    const int shift = in_hi ? 56 - 8 * pass : 24 - 8 * (pass - 8);
+    for (int64_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+      uint64_t hi;
+      uint32_t lo;
+      int64_t w;
+      item(q, hi, lo, w);
+      if ((hi & mhi) != fhi || (lo & mlo) != flo) continue;
+      uint32_t d = in_hi ? (uint32_t)(hi >> shift) & 255u : (lo >> shift) & 255u;
+      atomicAdd((unsigned long long *)&hist[d], (unsigned long long)w);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int64_t run = cum;
+      int b = 0;
+      for (; b < 255; ++b) {
+        if (run + hist[b] > rem) break;
+        run += hist[b];
+      }
+      cum = run;
+      if (in_hi) fhi |= (uint64_t)b << shift, mhi |= 255ull << shift;
+      else flo |= (uint32_t)b << shift, mlo |= 255u << shift;
+    }
+    __syncthreads();
+  }
+  khi = fhi;
+  klo = flo;
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kIPThreads) k_bisect(IPCtx c) {
+  const int32_t j = blockIdx.x / c.T, a = blockIdx.x % c.T;
+  const int64_t nb = c.nstart[j], ns = c.nstart[j + 1] - nb;
+  const int64_t R = (int64_t)a * c.n + nb;  // scratch region of this attempt
+  int32_t *ord = c.ord + R, *disc = c.disc + R, *claimer = c.claimer + R, *cnt = c.cnt + R;
+  int32_t *side = c.side + R, *mvx0 = c.mvx0 + R, *mvx1 = c.mvx1 + R, *ok0 = c.ok0 + R,
+          *ok1 = c.ok1 + R;
+  int64_t *mvg0 = c.mvg0 + R, *mvg1 = c.mvg1 + R;
+  const int32_t *vs = c.vlist + nb;
+  const int32_t kk = c.nkk[j], k0 = (kk + 1) / 2, k1 = kk / 2;
+  const uint64_t key = ((uint64_t)(uint32_t)c.noff[j] << 32) | (uint32_t)kk;
+  auto cw = [&](int64_t x) -> int64_t { return c.vw ? c.vw[vs[x]] : 1; };
+  if (ns == 0) {
+    if (threadIdx.x == 0) c.cut[blockIdx.x] = 0;
+    return;
+  }
+  // ---------------- BFS order
+  for (int64_t x = threadIdx.x; x < ns; x += blockDim.x) disc[x] = 0, claimer[x] = INT32_MAX;
+  __syncthreads();
+  __shared__ int64_t sh_fb, sh_fe, sh_tail;
+  if (threadIdx.x == 0) {
+    int64_t s0 = (int64_t)(round_key(c.seed, kTagIPSeed, key, (uint64_t)a) % (uint64_t)ns);
+    ord[0] = (int32_t)s0;
+    disc[s0] = 1;
+    sh_fb = 0, sh_fe = 1, sh_tail = 1;
+  }
+  __syncthreads();
+  for (;;) {
+    int64_t fb = sh_fb, fe = sh_fe, tail = sh_tail;
+    if (fb >= fe) break;
+    for (int64_t i = fb + threadIdx.x; i < fe; i += blockDim.x) {
+      int32_t u = vs[ord[i]];
+      for (int64_t e = c.xadj[u]; e < c.xadj[u + 1]; ++e) {
+        int32_t v = c.adj[e];
+        if (c.node_of[v] != j) continue;
+        int32_t y = c.loc[v];
+        if (!disc[y]) atomicMin(&claimer[y], (int32_t)i);
+      }
+    }
+    __syncthreads();
+    int64_t carry = 0;
+    for (int64_t i0 = fb; i0 < fe; i0 += blockDim.x) {
+      int64_t i = i0 + threadIdx.x, k = 0;
+      if (i < fe) {
+        int32_t u = vs[ord[i]];
+        for (int64_t e = c.xadj[u]; e < c.xadj[u + 1]; ++e) {
+          int32_t v = c.adj[e];
+          if (c.node_of[v] != j) continue;
+          int32_t y = c.loc[v];
+          if (!disc[y] && claimer[y] == i) ++k;
+        }
+      }
+      int64_t tot;
+      int64_t ex = bscan_excl(k, tot);
+      if (i < fe) cnt[i - fb] = (int32_t)(carry + ex);
+      carry += tot;
+    }
+    __syncthreads();
+    for (int64_t i = fb + threadIdx.x; i < fe; i += blockDim.x) {
+      int64_t pos = tail + cnt[i - fb];
+      int32_t u = vs[ord[i]];
+      for (int64_t e = c.xadj[u]; e < c.xadj[u + 1]; ++e) {
+        int32_t v = c.adj[e];
+        if (c.node_of[v] != j) continue;
+        int32_t y = c.loc[v];
+        if (!disc[y] && claimer[y] == i) ord[pos++] = y;
+      }
+    }
+    __syncthreads();
+    for (int64_t q = tail + threadIdx.x; q < tail + carry; q += blockDim.x) disc[ord[q]] = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) sh_fb = tail, sh_fe = tail + carry, sh_tail = tail + carry;
+    __syncthreads();
+  }
+  {  // append unreached vertices in ascending id
+    int64_t carry = 0, tail = sh_tail;
+    for (int64_t x0 = 0; x0 < ns; x0 += blockDim.x) {
+      int64_t x = x0 + threadIdx.x;
+      int64_t f = x < ns && !disc[x];
+      int64_t tot;
+      int64_t ex = bscan_excl(f, tot);
+      if (f) ord[tail + carry + ex] = (int32_t)x;
+      carry += tot;
+    }
+    __syncthreads();
+  }
+  // ---------------- greedy growing: longest prefix within target0
+  __shared__ int64_t lw[2], inw[2], ncnt[2];
+  int64_t W = 0;
+  for (int64_t x = threadIdx.x; x < ns; x += blockDim.x) W += cw(x);
+  W = bsum(W);
+  const int64_t target0 = (int64_t)(((__int128)W * k0) / kk);
+  const int64_t caps[2] = {(int64_t)k0 * c.l_max, (int64_t)k1 * c.l_max};
+  {
+    int64_t carry = 0, w0 = 0;
+    for (int64_t q0 = 0; q0 < ns; q0 += blockDim.x) {
+      int64_t q = q0 + threadIdx.x;
+      int64_t w = q < ns ? cw(ord[q]) : 0;
+      int64_t tot;
+      int64_t incl = carry + bscan_excl(w, tot) + w;
+      if (q < ns) {
+        bool in0 = incl <= target0;
+        side[ord[q]] = in0 ? 0 : 1;
+        if (in0) w0 += w;
+      }
+      carry += tot;
+    }
+    w0 = bsum(w0);
+    if (threadIdx.x == 0) lw[0] = w0, lw[1] = W - w0;
+    __syncthreads();
+  }
+  // ---------------- 2-way label propagation
+  for (int32_t r = 0; r < c.rounds; ++r) {
+    const uint64_t rk = round_key(c.seed, kTagIPLP, key, ((uint64_t)a << 8) + (uint64_t)r);
+    for (int32_t s = 0; s < c.S; ++s) {
+      if (threadIdx.x == 0) inw[0] = inw[1] = 0, ncnt[0] = ncnt[1] = 0;
+      __syncthreads();
+      for (int64_t x = threadIdx.x; x < ns; x += blockDim.x) {
+        if ((int32_t)(hstep(rk, (uint64_t)x) % (uint64_t)c.S) != s) continue;
+        int32_t u = vs[x];
+        int64_t Rs[2] = {0, 0};
+        for (int64_t e = c.xadj[u]; e < c.xadj[u + 1]; ++e) {
+          int32_t v = c.adj[e];
+          if (c.node_of[v] != j) continue;
+          Rs[side[c.loc[v]]] += c.ew ? c.ew[e] : 1;
+        }
+        int32_t own = side[x], oth = 1 - own;
+        int64_t w = cw(x);
+        if (Rs[oth] > Rs[own] && lw[oth] + w <= caps[oth]) {
+          int64_t g = Rs[oth] - Rs[own];
+          unsigned long long p = atomicAdd((unsigned long long *)&ncnt[oth], 1ull);
+          atomicAdd((unsigned long long *)&inw[oth], (unsigned long long)w);
+          if (oth == 0) mvx0[p] = (int32_t)x, mvg0[p] = g, ok0[p] = 0;
+          else mvx1[p] = (int32_t)x, mvg1[p] = g, ok1[p] = 0;
+        }
+      }
+      __syncthreads();
+      for (int t = 0; t < 2; ++t) {
+        int32_t *mx = t == 0 ? mvx0 : mvx1, *ok = t == 0 ? ok0 : ok1;
+        int64_t *mg = t == 0 ? mvg0 : mvg1;
+        int64_t m = ncnt[t];
+        if (lw[t] + inw[t] <= caps[t]) {
+          for (int64_t q = threadIdx.x; q < m; q += blockDim.x) ok[q] = 1;
+        } else if (caps[t] - lw[t] >= 0) {
+          auto item = [&](int64_t q, uint64_t &hi, uint32_t &lo, int64_t &w) {
+            hi = ~(uint64_t)mg[q];
+            lo = (uint32_t)mx[q];
+            w = cw(mx[q]);
+          };
+          uint64_t khi;
+          uint32_t klo;
+          ip_select(m, caps[t] - lw[t], item, khi, klo);
+          for (int64_t q = threadIdx.x; q < m; q += blockDim.x) {
+            uint64_t hi = ~(uint64_t)mg[q];
+            uint32_t lo = (uint32_t)mx[q];
+            ok[q] = hi < khi || (hi == khi && lo < klo);
+          }
+        }
+        __syncthreads();
+      }
+      for (int t = 0; t < 2; ++t) {
+        int32_t *mx = t == 0 ? mvx0 : mvx1, *ok = t == 0 ? ok0 : ok1;
+        for (int64_t q = threadIdx.x; q < ncnt[t]; q += blockDim.x) {
+          if (!ok[q]) continue;
+          int64_t w = cw(mx[q]);
+          side[mx[q]] = t;
+          atomicAdd((unsigned long long *)&lw[t], (unsigned long long)w);
+          atomicAdd((unsigned long long *)&lw[1 - t], (unsigned long long)(-w));
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // ---------------- cut of the induced subgraph
+  int64_t cutv = 0;
+  for (int64_t x = threadIdx.x; x < ns; x += blockDim.x) {
+    int32_t u = vs[x];
+    for (int64_t e = c.xadj[u]; e < c.xadj[u + 1]; ++e) {
+      int32_t v = c.adj[e];
+      if (c.node_of[v] == j && side[c.loc[v]] != side[x]) cutv += c.ew ? c.ew[e] : 1;
+    }
+  }
+  cutv = bsum(cutv);
+  if (threadIdx.x == 0) c.cut[blockIdx.x] = cutv / 2;
+}
+
+// Pick the winning attempt of every node and move its vertices on.
+__global__ void k_pick(IPCtx c, const int32_t *child0, const int32_t *child1, int32_t *next_node,
+                       int32_t *part) {
+  const int32_t j = blockIdx.x;
+  __shared__ int32_t best;
+  if (threadIdx.x == 0) {
+    int32_t b = 0;
+    for (int32_t a = 1; a < c.T; ++a)
+      if (c.cut[j * c.T + a] < c.cut[j * c.T + b]) b = a;
+    best = b;
+  }
+  __syncthreads();
+  const int64_t nb = c.nstart[j], ns = c.nstart[j + 1] - nb;
+  const int32_t kk = c.nkk[j], k0 = (kk + 1) / 2;
+  for (int64_t x = threadIdx.x; x < ns; x += blockDim.x) {
+    int32_t u = c.vlist[nb + x];
+    int32_t sd = c.side[(int64_t)best * c.n + nb + x];
+    int32_t ch = sd == 0 ? child0[j] : child1[j];
+    next_node[u] = ch;
+    if (ch < 0) part[u] = sd == 0 ? c.noff[j] : c.noff[j] + k0;
+  }
+}
+
+__global__ void k_node_keys(const int32_t *node_of, int64_t n, uint64_t *keys, int64_t *count) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    int32_t nd = node_of[u];
+    keys[u] = nd < 0 ? ~0ull : ((uint64_t)nd << 32) | (uint64_t)u;
+    if (nd >= 0) atomicAdd((unsigned long long *)&count[nd], 1ull);
+  }
+}
+
+__global__ void k_node_lists(const uint64_t *keys, const int64_t *nstart, int64_t m, int32_t *vlist,
+                             int32_t *loc) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t k = keys[i];
+    int32_t u = (int32_t)(k & 0xffffffffu), nd = (int32_t)(k >> 32);
+    vlist[i] = u;
+    loc[u] = (int32_t)(i - nstart[nd]);
+  }
+}
+
+__global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+}  // namespace
+
+void initial_partition(const tp_graph *g, int32_t k, int64_t l_max, const tp_params &p,
+                       int32_t *d_part, cudaStream_t s) {
+  TP_REQUIRE(!g->compressed, TP_ERR_INVALID);
+  const int64_t n = g->n;
+  if (n == 0) return;
+  k_fill_i32<<<grid_for(n, 256), 256, 0, s>>>(d_part, n, 0);
+  TP_LAUNCH_CHECK();
+  if (k <= 1) return;
+  const int32_t T = std::max(1, p.ip_attempts);
+  Buf<int32_t> node_of(n, s), next_node(n, s), vlist(n, s), loc(n, s);
+  k_fill_i32<<<grid_for(n, 256), 256, 0, s>>>(node_of.get(), n, 0);
+  Buf<int32_t> ord(T * n, s), disc(T * n, s), claimer(T * n, s), cnt(T * n, s), side(T * n, s),
+      mvx0(T * n, s), mvx1(T * n, s), ok0(T * n, s), ok1(T * n, s);
+  Buf<int64_t> mvg0(T * n, s), mvg1(T * n, s);
+  Buf<uint64_t> keys(n, s);
+  std::vector<int32_t> off = {0}, kks = {k};
+  while (!off.empty()) {
+    const int32_t nodes = (int32_t)off.size();
+    // vertex lists per node
+    Buf<int64_t> nstart(nodes + 1, s);
+    TP_CUDA(cudaMemsetAsync(nstart.get(), 0, (nodes + 1) * sizeof(int64_t), s));
+    k_node_keys<<<grid_for(n, 256), 256, 0, s>>>(node_of.get(), n, keys.get(), nstart.get());
+    TP_LAUNCH_CHECK();
+    radix_sort_pairs(keys.get(), nullptr, n, 64, s);
+    exclusive_scan_i64(nstart.get(), nstart.get(), nodes, s);
+    int64_t m = read_scalar(nstart.get() + nodes, s);
+    if (m) {
+      k_node_lists<<<grid_for(m, 256), 256, 0, s>>>(keys.get(), nstart.get(), m, vlist.get(), loc.get());
+      TP_LAUNCH_CHECK();
+    }
+    // children of every node at the next depth (-1: leaf, assign the block)
+    std::vector<int32_t> c0(nodes), c1(nodes), noff, nkk;
+    for (int32_t jn = 0; jn < nodes; ++jn) {
+      int32_t k0 = (kks[jn] + 1) / 2, k1 = kks[jn] / 2;
+      c0[jn] = -1, c1[jn] = -1;
+      if (k0 >= 2) c0[jn] = (int32_t)noff.size(), noff.push_back(off[jn]), nkk.push_back(k0);
+      if (k1 >= 2) c1[jn] = (int32_t)noff.size(), noff.push_back(off[jn] + k0), nkk.push_back(k1);
+    }
+    Buf<int32_t> d_off(nodes, s), d_kk(nodes, s), d_c0(nodes, s), d_c1(nodes, s);
+    TP_CUDA(cudaMemcpyAsync(d_off.get(), off.data(), nodes * 4, cudaMemcpyHostToDevice, s));
+    TP_CUDA(cudaMemcpyAsync(d_kk.get(), kks.data(), nodes * 4, cudaMemcpyHostToDevice, s));
+    TP_CUDA(cudaMemcpyAsync(d_c0.get(), c0.data(), nodes * 4, cudaMemcpyHostToDevice, s));
+    TP_CUDA(cudaMemcpyAsync(d_c1.get(), c1.data(), nodes * 4, cudaMemcpyHostToDevice, s));
+    Buf<int64_t> cut((int64_t)nodes * T, s);
+    IPCtx c;
+    c.n = n;
+    c.xadj = g->xadj.get();
+    c.adj = g->adj.get();
+    c.vw = g->unit_vw ? nullptr : g->vw.get();
+    c.ew = g->unit_ew ? nullptr : g->ew.get();
+    c.node_of = node_of.get();
+    c.vlist = vlist.get();
+    c.nstart = nstart.get();
+    c.loc = loc.get();
+    c.noff = d_off.get();
+    c.nkk = d_kk.get();
+    c.T = T;
+    c.seed = p.seed;
+    c.l_max = l_max;
+    c.rounds = p.refine_rounds;
+    c.S = p.sub_rounds;
+    c.ord = ord.get(), c.disc = disc.get(), c.claimer = claimer.get(), c.cnt = cnt.get();
+    c.side = side.get(), c.mvx0 = mvx0.get(), c.mvx1 = mvx1.get(), c.ok0 = ok0.get(),
+    c.ok1 = ok1.get();
+    c.mvg0 = mvg0.get(), c.mvg1 = mvg1.get();
+    c.cut = cut.get();
+    k_bisect<<<(unsigned)(nodes * T), kIPThreads, 0, s>>>(c);
+    TP_LAUNCH_CHECK();
+    k_fill_i32<<<grid_for(n, 256), 256, 0, s>>>(next_node.get(), n, -1);
+    k_pick<<<(unsigned)nodes, 256, 0, s>>>(c, d_c0.get(), d_c1.get(), next_node.get(), d_part);
+    TP_LAUNCH_CHECK();
+    std::swap(node_of, next_node);
+    TP_CUDA(cudaStreamSynchronize(s));  // host vectors above outlive their copies
+    off.swap(noff);
+    kks.swap(nkk);
+  }
+}
+
+}  // namespace tp

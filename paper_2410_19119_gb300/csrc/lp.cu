@@ -1,0 +1,933 @@
+// Size-constrained label propagation on the GPU (Algorithm 1 of the paper,
+// made synchronous and deterministic), its two-hop packing and rebalancing.
+//
+// Rating (Section "Rating Maps", Algorithm 2): a vertex's ratings R[C[v]] +=
+// w(u,v) accumulate in a hash table. The paper's split into a first phase
+// with small per-thread tables and a second phase for "bumped" high-degree
+// vertices becomes four degree tiers, each a different kernel:
+//   small (deg <= tier_small): one warp per vertex, 128-slot shared table, and
+//          for one-window unit-weight neighbourhoods no table at all (lanes
+//          with equal labels are grouped by __match_any_sync);
+//   mid   (deg <= tier_mid):   one warp per vertex, 2048-slot shared table;
+//   big   (deg <= 10000):      one warp per vertex, table in global memory;
+//   huge  (deg > 10000):       one warp per chunk of 1000 neighbours (the
+//          compressed format's independently decodable chunks) aggregates in
+//          a shared table and flushes into the vertex's global table with
+//          atomics (the paper's "hash tables as flush buffers" against
+//          contention); one block per vertex then scans that table.
+// The tier only decides where the sums are formed; integer sums commute and
+// the argmax uses a total order, so the result is tier-independent.
+//
+// Approval: movers add their weight to in_w[target] with atomics. Targets
+// whose weight plus in_w fits approve every mover; for the others one block
+// per target runs a weighted radix select over the key (gain desc, vertex
+// asc) and approves exactly the longest fitting prefix.
+#include <algorithm>
+
+#include "decode.cuh"
+
+namespace tp {
+
+namespace {
+
+enum Mode { M_LP = 0, M_FAV = 1, M_REBAL = 2 };
+
+constexpr int kSmallLog = 7;   // 128 slots
+constexpr int kMidLog = 11;    // 2048 slots
+constexpr int kMidWarps = 4;
+constexpr int kHugeWarps = 4;  // warps per block in the chunk kernel
+constexpr int kDecideThreads = 256;
+
+struct RateCtx {
+  GView g;
+  const uint8_t *tier;
+  const int32_t *label;
+  const int64_t *lw;
+  int64_t cap;
+  uint64_t rk;
+  int32_t S, s;
+  // M_LP outputs
+  int32_t *mv_u, *mv_t;
+  int64_t *mv_g;
+  int64_t *in_w;
+  int32_t *in_cnt;
+  unsigned long long *counters;
+  // M_FAV output
+  int32_t *fav;
+  // M_REBAL
+  int32_t blk, k;
+  int64_t *rb_loss;
+  int32_t *rb_t;
+  long long *rb_best;
+  // lists and global tables
+  const int32_t *list;
+  int64_t list_n;
+  int32_t *tkeys;
+  int64_t *tvals;
+  const int64_t *toff;
+  const int32_t *tcap;
+  int64_t tbase;  // slot offset of this tier's tables inside tkeys/tvals
+  const int64_t *chunk_start;
+  int64_t n_chunks;
+};
+
+__device__ __forceinline__ int64_t node_w(const GView &g, int64_t u) { return g.vw ? g.vw[u] : 1; }
+
+template <int MODE>
+__device__ __forceinline__ bool active(const RateCtx &c, int64_t u) {
+  if (MODE == M_LP) return (int32_t)(hstep(c.rk, (uint64_t)u) % (uint64_t)c.S) == c.s;
+  if (MODE == M_FAV) return c.label[u] == u && c.lw[u] == node_w(c.g, u);
+  return c.label[u] == c.blk;
+}
+
+template <int MODE>
+__device__ __forceinline__ uint64_t tie_key(const RateCtx &c, int64_t u) {
+  return MODE == M_REBAL ? 0 : hstep(hstep(c.rk, (uint64_t)u), kTagTie);
+}
+
+__device__ __forceinline__ uint32_t slot_of(int32_t x, int logcap) {
+  return ((uint32_t)x * 0x9E3779B1u) >> (32 - logcap);
+}
+
+// Adds w to the rating of label x (open addressing, linear probing).
+__device__ __forceinline__ void tbl_add(int32_t *keys, int64_t *vals, int logcap, int32_t x,
+                                        int64_t w, int32_t *err) {
+  uint32_t mask = (1u << logcap) - 1u, h = slot_of(x, logcap);
+  for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
+    int32_t k = *(volatile int32_t *)&keys[h];
+    if (k == -1) {
+      int32_t prev = atomicCAS(&keys[h], -1, x);
+      k = prev == -1 ? x : prev;
+    }
+    if (k == x) {
+      atomicAdd((unsigned long long *)&vals[h], (unsigned long long)w);
+      return;
+    }
+  }
+  latch_error(err, TP_ERR_CORRUPT);  // more distinct labels than the degree allows
+}
+
+struct Best {
+  int64_t r;
+  uint32_t t;
+  int32_t x;
+  int64_t rown;
+  __device__ __forceinline__ void init() { r = -1, t = 0xffffffffu, x = INT32_MAX, rown = 0; }
+};
+
+template <int MODE>
+__device__ __forceinline__ void consider(const RateCtx &c, Best &b, int32_t x, int64_t R,
+                                         int32_t own, int64_t cu, uint64_t hv) {
+  if (x == own) {
+    b.rown = R;
+    return;
+  }
+  if (MODE != M_FAV && c.lw[x] + cu > c.cap) return;
+  uint32_t t = MODE == M_REBAL ? 0u : tie_hash(hv, x);
+  if (better(R, t, x, b.r, b.t, b.x)) b.r = R, b.t = t, b.x = x;
+}
+
+__device__ __forceinline__ void warp_reduce_best(Best &b) {
+  warp_best(b.r, b.t, b.x);
+  b.rown = warp_max(b.rown);
+}
+
+// Per-warp buffer of mover records, flushed with one atomic per 32 movers.
+struct MoverBuf {
+  int32_t *u, *t;
+  int64_t *gain;
+  int cnt;
+};
+
+__device__ __forceinline__ void flush_movers(const RateCtx &c, MoverBuf &mb) {
+  __syncwarp();
+  if (mb.cnt == 0) return;
+  unsigned long long base = 0;
+  if (lane_id() == 0) base = atomicAdd(c.counters, (unsigned long long)mb.cnt);
+  base = __shfl_sync(kFull, base, 0);
+  int l = lane_id();
+  if (l < mb.cnt) {
+    c.mv_u[base + l] = mb.u[l];
+    c.mv_t[base + l] = mb.t[l];
+    c.mv_g[base + l] = mb.gain[l];
+  }
+  mb.cnt = 0;
+  __syncwarp();
+}
+
+// Acts on the (warp-uniform) decision for vertex u.
+template <int MODE>
+__device__ __forceinline__ void finalize_warp(const RateCtx &c, const Best &b, int64_t u, int64_t cu,
+                                              MoverBuf *mb) {
+  int lane = lane_id();
+  if (MODE == M_LP) {
+    if (b.r > b.rown) {
+      if (lane == 0) {
+        mb->u[mb->cnt] = (int32_t)u;
+        mb->t[mb->cnt] = b.x;
+        mb->gain[mb->cnt] = b.r - b.rown;
+        atomicAdd((unsigned long long *)&c.in_w[b.x], (unsigned long long)cu);
+        atomicAdd(&c.in_cnt[b.x], 1);
+      }
+      if (++mb->cnt == 32) flush_movers(c, *mb);
+    }
+  } else if (MODE == M_FAV) {
+    if (lane == 0) c.fav[u] = b.r > 0 ? b.x : (int32_t)c.g.n;
+  } else {
+    int32_t tz = -1;
+    if (b.r <= 0) {  // no admissible neighbouring block: smallest admissible block
+      for (int32_t base = 0; base < c.k && tz < 0; base += 32) {
+        int32_t t = base + lane;
+        bool ok = t < c.k && t != c.blk && c.lw[t] + cu <= c.cap;
+        unsigned m = __ballot_sync(kFull, ok);
+        if (m) tz = base + __ffs(m) - 1;
+      }
+    }
+    if (lane == 0) {
+      int32_t tt = b.r > 0 ? b.x : tz;
+      c.rb_t[u] = tt;
+      if (tt >= 0) {
+        int64_t loss = b.rown - (b.r > 0 ? b.r : 0);
+        c.rb_loss[u] = loss;
+        atomicMin(c.rb_best, (long long)loss);
+      }
+    }
+  }
+}
+
+// Rates vertex u with one warp; the table (shared or global) must be empty
+// on entry and is empty again on exit.
+template <bool COMP, int MODE>
+__device__ void rate_vertex_warp(const RateCtx &c, int64_t u, int32_t *keys, int64_t *vals,
+                                 int logcap, bool allow_fast, MoverBuf *mb) {
+  const int lane = lane_id();
+  const int32_t own = c.label[u];
+  const int64_t cu = node_w(c.g, u);
+  const uint64_t hv = tie_key<MODE>(c, u);
+  Best b;
+  b.init();
+  bool fast = false;
+  if (allow_fast && !c.g.ew) {
+    if (!COMP) {
+      fast = c.g.xadj[u + 1] - c.g.xadj[u] <= 32;
+    } else {
+      ZipNbr z = zip_nbr(c.g, u);
+      fast = z.nchunks == 1 && z.end - z.data <= 32;
+    }
+  }
+  if (fast) {
+    // one batch: group equal labels across lanes, no table
+    warp_neighbours<COMP>(c.g, u, -1, [&](bool has, int32_t v, int64_t) {
+      int32_t x = has ? c.label[v] : -1;
+      unsigned peers = __match_any_sync(kFull, x);
+      if (has && (peers & lanemask_lt()) == 0) consider<MODE>(c, b, x, __popc(peers), own, cu, hv);
+    });
+  } else {
+    warp_neighbours<COMP>(c.g, u, -1, [&](bool has, int32_t v, int64_t w) {
+      int32_t x = has ? c.label[v] : -1;
+      if (!c.g.ew) {
+        unsigned peers = __match_any_sync(kFull, x);
+        if (has && (peers & lanemask_lt()) == 0)
+          tbl_add(keys, vals, logcap, x, __popc(peers), c.g.err);
+      } else if (has) {
+        tbl_add(keys, vals, logcap, x, w, c.g.err);
+      }
+    });
+    __syncwarp();
+    __threadfence_block();
+    const int cap = 1 << logcap;
+    for (int i = lane; i < cap; i += 32) {
+      int32_t x = keys[i];
+      if (x >= 0) {
+        consider<MODE>(c, b, x, vals[i], own, cu, hv);
+        keys[i] = -1;
+        vals[i] = 0;
+      }
+    }
+    __syncwarp();
+  }
+  warp_reduce_best(b);
+  finalize_warp<MODE>(c, b, u, cu, mb);
+}
+
+// Shared memory per warp: table keys + values, then the mover buffer.
+template <int LOG>
+struct WarpSmem {
+  int32_t keys[1 << LOG];
+  int64_t vals[1 << LOG];
+  int32_t mu[32], mt[32];
+  int64_t mg[32];
+};
+
+template <int LOG>
+__device__ __forceinline__ void init_table(WarpSmem<LOG> &w) {
+  for (int i = lane_id(); i < (1 << LOG); i += 32) w.keys[i] = -1, w.vals[i] = 0;
+  __syncwarp();
+}
+
+// Small tier: every vertex, filtered by tier and predicate in 32-vertex slabs.
+template <bool COMP, int MODE>
+__global__ void k_rate_small(RateCtx c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WarpSmem<kSmallLog> &ws = reinterpret_cast<WarpSmem<kSmallLog> *>(smem_raw)[threadIdx.x >> 5];
+  init_table(ws);
+  MoverBuf mb{ws.mu, ws.mt, ws.mg, 0};
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = gw * 32; base < c.g.n; base += nw * 32) {
+    int64_t u = base + lane_id();
+    bool act = u < c.g.n && c.tier[u] == TIER_SMALL && active<MODE>(c, u);
+    unsigned am = __ballot_sync(kFull, act);
+    while (am) {
+      int j = __ffs(am) - 1;
+      am &= am - 1;
+      rate_vertex_warp<COMP, MODE>(c, base + j, ws.keys, ws.vals, kSmallLog, true, &mb);
+    }
+  }
+  if (MODE == M_LP) flush_movers(c, mb);
+}
+
+// Mid tier (shared table) and big tier (global table): one warp per listed vertex.
+template <bool COMP, int MODE, bool GLOBAL>
+__global__ void k_rate_list(RateCtx c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WarpSmem<kMidLog> *wsp = nullptr;
+  __shared__ int32_t mu[kMidWarps][32], mt[kMidWarps][32];
+  __shared__ int64_t mg[kMidWarps][32];
+  int w = threadIdx.x >> 5;
+  if (!GLOBAL) {
+    wsp = &reinterpret_cast<WarpSmem<kMidLog> *>(smem_raw)[w];
+    init_table(*wsp);
+  }
+  MoverBuf mb{mu[w], mt[w], mg[w], 0};
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = gw; i < c.list_n; i += nw) {
+    int64_t u = c.list[i];
+    if (!active<MODE>(c, u)) continue;
+    if (GLOBAL) {
+      int64_t off = c.tbase + c.toff[i];
+      rate_vertex_warp<COMP, MODE>(c, u, c.tkeys + off, c.tvals + off, c.tcap[i], false, &mb);
+    } else {
+      rate_vertex_warp<COMP, MODE>(c, u, wsp->keys, wsp->vals, kMidLog, false, &mb);
+    }
+  }
+  if (MODE == M_LP) flush_movers(c, mb);
+}
+
+// Huge tier, phase 1: one warp per (vertex, chunk) aggregates the chunk in a
+// shared table and flushes it into the vertex's global table.
+template <bool COMP, int MODE>
+__global__ void k_rate_huge_chunks(RateCtx c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WarpSmem<kMidLog> &ws = reinterpret_cast<WarpSmem<kMidLog> *>(smem_raw)[threadIdx.x >> 5];
+  init_table(ws);
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int lane = lane_id();
+  for (int64_t item = gw; item < c.n_chunks; item += nw) {
+    // vertex index: last i with chunk_start[i] <= item
+    int64_t lo = 0, hi = c.list_n - 1;
+    while (lo < hi) {
+      int64_t mid = (lo + hi + 1) / 2;
+      if (c.chunk_start[mid] <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    int64_t i = lo, j = item - c.chunk_start[i];
+    int64_t u = c.list[i];
+    if (!active<MODE>(c, u)) continue;
+    warp_neighbours<COMP>(c.g, u, j, [&](bool has, int32_t v, int64_t w) {
+      int32_t x = has ? c.label[v] : -1;
+      if (!c.g.ew) {
+        unsigned peers = __match_any_sync(kFull, x);
+        if (has && (peers & lanemask_lt()) == 0)
+          tbl_add(ws.keys, ws.vals, kMidLog, x, __popc(peers), c.g.err);
+      } else if (has) {
+        tbl_add(ws.keys, ws.vals, kMidLog, x, w, c.g.err);
+      }
+    });
+    __syncwarp();
+    __threadfence_block();
+    int64_t off = c.tbase + c.toff[i];
+    int lc = c.tcap[i];
+    for (int s = lane; s < (1 << kMidLog); s += 32) {
+      int32_t x = ws.keys[s];
+      if (x >= 0) {
+        tbl_add(c.tkeys + off, c.tvals + off, lc, x, ws.vals[s], c.g.err);
+        ws.keys[s] = -1;
+        ws.vals[s] = 0;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Huge tier, phase 2: one block per vertex scans its global table.
+template <int MODE>
+__global__ void k_rate_huge_decide(RateCtx c) {
+  __shared__ Best wb[kDecideThreads / 32];
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  for (int64_t i = blockIdx.x; i < c.list_n; i += gridDim.x) {
+    int64_t u = c.list[i];
+    if (!active<MODE>(c, u)) continue;
+    const int32_t own = c.label[u];
+    const int64_t cu = node_w(c.g, u);
+    const uint64_t hv = tie_key<MODE>(c, u);
+    int64_t off = c.tbase + c.toff[i];
+    int64_t cap = (int64_t)1 << c.tcap[i];
+    Best b;
+    b.init();
+    for (int64_t sl = threadIdx.x; sl < cap; sl += blockDim.x) {
+      int32_t x = c.tkeys[off + sl];
+      if (x >= 0) {
+        consider<MODE>(c, b, x, c.tvals[off + sl], own, cu, hv);
+        c.tkeys[off + sl] = -1;
+        c.tvals[off + sl] = 0;
+      }
+    }
+    warp_reduce_best(b);
+    if (lane == 0) wb[w] = b;
+    __syncthreads();
+    if (w == 0) {
+      b = lane < (int)(blockDim.x >> 5) ? wb[lane] : Best{-1, 0xffffffffu, INT32_MAX, 0};
+      warp_reduce_best(b);
+      __shared__ int32_t mu[32], mt[32];
+      __shared__ int64_t mg[32];
+      MoverBuf mb{mu, mt, mg, 0};
+      finalize_warp<MODE>(c, b, u, cu, &mb);
+      if (MODE == M_LP) flush_movers(c, mb);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- approval
+struct ApproveCtx {
+  const int32_t *mv_u, *mv_t;
+  const int64_t *mv_g;
+  int8_t *mv_ok;
+  int64_t *in_w;
+  int32_t *in_cnt, *cstate, *cfill, *cseg, *ctarget;
+  int64_t *cbase;
+  unsigned long long *counters;  // [0] movers [1] contested targets [2] contested pool
+  int32_t *label;
+  int64_t *lw;
+  int64_t cap;
+  const int64_t *vw;
+};
+
+__device__ __forceinline__ int64_t vwt(const ApproveCtx &a, int64_t u) { return a.vw ? a.vw[u] : 1; }
+
+// A: targets that fit take every mover; the others become contested.
+__global__ void k_approve_fit(ApproveCtx a) {
+  int64_t nm = (int64_t)a.counters[0];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nm;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t t = a.mv_t[i];
+    bool fits = a.lw[t] + a.in_w[t] <= a.cap;
+    a.mv_ok[i] = fits;
+    if (!fits && atomicCAS(&a.cstate[t], 0, 1) == 0) {
+      unsigned long long j = atomicAdd(&a.counters[1], 1ull);
+      a.ctarget[j] = t;
+      a.cbase[t] = (int64_t)atomicAdd(&a.counters[2], (unsigned long long)a.in_cnt[t]);
+    }
+  }
+}
+
+// B: contested movers are grouped by target.
+__global__ void k_approve_scatter(ApproveCtx a) {
+  int64_t nm = (int64_t)a.counters[0];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nm;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (a.mv_ok[i]) continue;
+    int32_t t = a.mv_t[i];
+    a.cseg[a.cbase[t] + atomicAdd(&a.cfill[t], 1)] = (int32_t)i;
+  }
+}
+
+// Weighted radix select over 96-bit keys (hi = ~gain, lo = vertex): finds the
+// first key whose inclusive weight prefix exceeds rem and returns it in
+// (khi, klo). Every thread of the block must call it.
+template <class Item>
+__device__ void block_select(int64_t cnt, int64_t rem, Item item, uint64_t &khi, uint32_t &klo) {
+  __shared__ int64_t hist[256];
+  __shared__ uint64_t fhi, mhi;
+  __shared__ uint32_t flo, mlo;
+  __shared__ int64_t cum;
+  if (threadIdx.x == 0) fhi = 0, mhi = 0, flo = 0, mlo = 0, cum = 0;
+  __syncthreads();
+  for (int pass = 0; pass < 12; ++pass) {
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const bool in_hi = pass < 8;
+    const int shift = in_hi ? 56 - 8 * pass : 24 - 8 * (pass - 8);
+    for (int64_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+      uint64_t hi;
+      uint32_t lo;
+      int64_t w;
+      item(q, hi, lo, w);
+      if ((hi & mhi) != fhi || (lo & mlo) != flo) continue;
+      uint32_t d = in_hi ? (uint32_t)(hi >> shift) & 255u : (lo >> shift) & 255u;
+      atomicAdd((unsigned long long *)&hist[d], (unsigned long long)w);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int64_t run = cum;
+      int b = 0;
+      for (; b < 255; ++b) {
+        if (run + hist[b] > rem) break;
+        run += hist[b];
+      }
+      cum = run;
+      if (in_hi) {
+        fhi |= (uint64_t)b << shift;
+        mhi |= 255ull << shift;
+      } else {
+        flo |= (uint32_t)b << shift;
+        mlo |= 255u << shift;
+      }
+    }
+    __syncthreads();
+  }
+  khi = fhi;
+  klo = flo;
+  __syncthreads();
+}
+
+// C: one block per contested target approves the longest fitting prefix in
+// (gain desc, vertex asc) order.
+__global__ void k_approve_contested(ApproveCtx a) {
+  int64_t nt = (int64_t)a.counters[1];
+  for (int64_t j = blockIdx.x; j < nt; j += gridDim.x) {
+    int32_t t = a.ctarget[j];
+    int64_t base = a.cbase[t], cnt = a.in_cnt[t];
+    int64_t rem = a.cap - a.lw[t];
+    auto item = [&](int64_t q, uint64_t &hi, uint32_t &lo, int64_t &w) {
+      int32_t i = a.cseg[base + q];
+      hi = ~(uint64_t)a.mv_g[i];
+      lo = (uint32_t)a.mv_u[i];
+      w = vwt(a, a.mv_u[i]);
+    };
+    if (rem < 0) continue;  // nothing can enter (mv_ok already 0)
+    uint64_t khi;
+    uint32_t klo;
+    block_select(cnt, rem, item, khi, klo);
+    for (int64_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+      uint64_t hi;
+      uint32_t lo;
+      int64_t w;
+      item(q, hi, lo, w);
+      if (hi < khi || (hi == khi && lo < klo)) a.mv_ok[a.cseg[base + q]] = 1;
+    }
+  }
+}
+
+// D: apply approved moves and reset the per-target counters.
+__global__ void k_apply(ApproveCtx a) {
+  int64_t nm = (int64_t)a.counters[0];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nm;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t t = a.mv_t[i];
+    if (a.mv_ok[i]) {
+      int32_t u = a.mv_u[i];
+      int64_t w = vwt(a, u);
+      int32_t own = a.label[u];
+      a.label[u] = t;
+      atomicAdd((unsigned long long *)&a.lw[t], (unsigned long long)w);
+      atomicAdd((unsigned long long *)&a.lw[own], (unsigned long long)(-w));
+    }
+    a.in_w[t] = 0;
+    a.in_cnt[t] = 0;
+    a.cstate[t] = 0;
+    a.cfill[t] = 0;
+  }
+}
+
+__global__ void k_init_singletons(const int64_t *vw, int64_t n, int32_t *label, int64_t *lw) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    label[u] = (int32_t)u;
+    lw[u] = vw ? vw[u] : 1;
+  }
+}
+
+// ---------------------------------------------------------------- tier dispatch
+template <int MODE>
+void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
+  build_tiers(g, p, s);
+  TierCache &T = g->tiers;
+  c.g = view(g);
+  c.tier = T.tier.get();
+  c.tkeys = T.tkeys.get();
+  c.tvals = T.tvals.get();
+  const int sms = num_sms();
+  const bool comp = g->compressed;
+  int64_t n_small = g->n - T.n_mid - T.n_big - T.n_huge;
+  if (n_small > 0) {
+    int wpb = p.warps_per_block >= 1 && p.warps_per_block <= 16 ? p.warps_per_block : 8;
+    size_t sm = sizeof(WarpSmem<kSmallLog>) * wpb;
+    unsigned blocks = (unsigned)std::min<int64_t>((g->n + 32 * wpb - 1) / (32 * wpb), (int64_t)sms * 16);
+    if (comp) k_rate_small<true, MODE><<<blocks, 32 * wpb, sm, s>>>(c);
+    else k_rate_small<false, MODE><<<blocks, 32 * wpb, sm, s>>>(c);
+    TP_LAUNCH_CHECK();
+  }
+  if (T.n_mid > 0) {
+    RateCtx m = c;
+    m.list = T.mid.get();
+    m.list_n = T.n_mid;
+    size_t sm = sizeof(WarpSmem<kMidLog>) * kMidWarps;
+    unsigned blocks = (unsigned)std::min<int64_t>((T.n_mid + kMidWarps - 1) / kMidWarps, (int64_t)sms * 8);
+    if (comp) k_rate_list<true, MODE, false><<<blocks, 32 * kMidWarps, sm, s>>>(m);
+    else k_rate_list<false, MODE, false><<<blocks, 32 * kMidWarps, sm, s>>>(m);
+    TP_LAUNCH_CHECK();
+  }
+  if (T.n_big > 0) {
+    RateCtx m = c;
+    m.list = T.big.get();
+    m.list_n = T.n_big;
+    m.toff = T.big_toff.get();
+    m.tcap = T.big_tcap.get();
+    m.tbase = 0;
+    unsigned blocks = (unsigned)std::min<int64_t>((T.n_big + kMidWarps - 1) / kMidWarps, (int64_t)sms * 16);
+    if (comp) k_rate_list<true, MODE, true><<<blocks, 32 * kMidWarps, 0, s>>>(m);
+    else k_rate_list<false, MODE, true><<<blocks, 32 * kMidWarps, 0, s>>>(m);
+    TP_LAUNCH_CHECK();
+  }
+  if (T.n_huge > 0) {
+    RateCtx m = c;
+    m.list = T.huge.get();
+    m.list_n = T.n_huge;
+    m.toff = T.huge_toff.get();
+    m.tcap = T.huge_tcap.get();
+    m.tbase = T.big_slots;
+    m.chunk_start = T.huge_chunk_start.get();
+    m.n_chunks = T.n_huge_chunks;
+    size_t sm = sizeof(WarpSmem<kMidLog>) * kHugeWarps;
+    unsigned blocks = (unsigned)std::min<int64_t>((T.n_huge_chunks + kHugeWarps - 1) / kHugeWarps, (int64_t)sms * 8);
+    if (comp) k_rate_huge_chunks<true, MODE><<<blocks, 32 * kHugeWarps, sm, s>>>(m);
+    else k_rate_huge_chunks<false, MODE><<<blocks, 32 * kHugeWarps, sm, s>>>(m);
+    TP_LAUNCH_CHECK();
+    unsigned db = (unsigned)std::min<int64_t>(T.n_huge, (int64_t)sms * 4);
+    k_rate_huge_decide<MODE><<<db, kDecideThreads, 0, s>>>(m);
+    TP_LAUNCH_CHECK();
+  }
+}
+
+template <class K>
+void set_smem_limits(K kernel, size_t bytes) {
+  TP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+void configure_kernels() {
+  static bool done = false;
+  if (done) return;
+  size_t small16 = sizeof(WarpSmem<kSmallLog>) * 16;
+  size_t mid = sizeof(WarpSmem<kMidLog>) * kMidWarps;
+  size_t huge = sizeof(WarpSmem<kMidLog>) * kHugeWarps;
+#define TP_CFG_MODE(M)                                              \
+  set_smem_limits(k_rate_small<true, M>, small16);                  \
+  set_smem_limits(k_rate_small<false, M>, small16);                 \
+  set_smem_limits(k_rate_list<true, M, false>, mid);                \
+  set_smem_limits(k_rate_list<false, M, false>, mid);               \
+  set_smem_limits(k_rate_huge_chunks<true, M>, huge);               \
+  set_smem_limits(k_rate_huge_chunks<false, M>, huge);
+  TP_CFG_MODE(M_LP)
+  TP_CFG_MODE(M_FAV)
+  TP_CFG_MODE(M_REBAL)
+#undef TP_CFG_MODE
+  done = true;
+}
+
+ApproveCtx approve_ctx(tp_graph *g, const LpState &st, LpWork &w) {
+  ApproveCtx a;
+  a.mv_u = w.mv_u.get();
+  a.mv_t = w.mv_t.get();
+  a.mv_g = w.mv_g.get();
+  a.mv_ok = w.mv_ok.get();
+  a.in_w = w.in_w.get();
+  a.in_cnt = w.in_cnt.get();
+  a.cstate = w.cstate.get();
+  a.cfill = w.cfill.get();
+  a.cseg = w.cseg.get();
+  a.ctarget = w.ctarget.get();
+  a.cbase = w.cbase.get();
+  a.counters = (unsigned long long *)w.counters.get();
+  a.label = st.label;
+  a.lw = st.lw;
+  a.cap = st.cap;
+  a.vw = g->unit_vw ? nullptr : g->vw.get();
+  return a;
+}
+
+}  // namespace
+
+void LpWork::init(int64_t n_vertices, int64_t n_labels, cudaStream_t s) {
+  if (n_vertices <= n && n_labels <= nlabels) return;
+  n = std::max(n, n_vertices);
+  nlabels = std::max(nlabels, n_labels);
+  size_t L = (size_t)std::max<int64_t>(nlabels, 1), N = (size_t)std::max<int64_t>(n, 1);
+  in_w.alloc(L, s);
+  in_cnt.alloc(L, s);
+  cstate.alloc(L, s);
+  cfill.alloc(L, s);
+  cbase.alloc(L, s);
+  ctarget.alloc(L, s);
+  mv_u.alloc(N, s);
+  mv_t.alloc(N, s);
+  mv_g.alloc(N, s);
+  mv_ok.alloc(N, s);
+  cseg.alloc(N, s);
+  counters.alloc(4, s);
+  TP_CUDA(cudaMemsetAsync(in_w.get(), 0, L * 8, s));
+  TP_CUDA(cudaMemsetAsync(in_cnt.get(), 0, L * 4, s));
+  TP_CUDA(cudaMemsetAsync(cstate.get(), 0, L * 4, s));
+  TP_CUDA(cudaMemsetAsync(cfill.get(), 0, L * 4, s));
+  TP_CUDA(cudaMemsetAsync(counters.get(), 0, 4 * 8, s));
+}
+
+void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t S, int32_t s,
+                 const tp_params &p, cudaStream_t stream) {
+  configure_kernels();
+  RateCtx c{};
+  c.label = st.label;
+  c.lw = st.lw;
+  c.cap = st.cap;
+  c.rk = rk;
+  c.S = S;
+  c.s = s;
+  c.mv_u = w.mv_u.get();
+  c.mv_t = w.mv_t.get();
+  c.mv_g = w.mv_g.get();
+  c.in_w = w.in_w.get();
+  c.in_cnt = w.in_cnt.get();
+  c.counters = (unsigned long long *)w.counters.get();
+  rate_tiers<M_LP>(g, c, p, stream);
+  ApproveCtx a = approve_ctx(g, st, w);
+  const unsigned blocks = (unsigned)num_sms() * 4;
+  k_approve_fit<<<blocks, 256, 0, stream>>>(a);
+  k_approve_scatter<<<blocks, 256, 0, stream>>>(a);
+  k_approve_contested<<<(unsigned)num_sms() * 2, 256, 0, stream>>>(a);
+  k_apply<<<blocks, 256, 0, stream>>>(a);
+  TP_LAUNCH_CHECK();
+  TP_CUDA(cudaMemsetAsync(w.counters.get(), 0, 4 * sizeof(int64_t), stream));
+}
+
+void lp_rounds(tp_graph *g, const LpState &st, LpWork &w, uint64_t seed, uint64_t tag, uint64_t a,
+               uint64_t b0, int32_t rounds, int32_t S, const tp_params &p, cudaStream_t stream) {
+  for (int32_t r = 0; r < rounds; ++r) {
+    uint64_t rk = round_key(seed, tag, a, b0 + (uint64_t)r);
+    for (int32_t s = 0; s < S; ++s) lp_subround(g, st, w, rk, S, s, p, stream);
+  }
+}
+
+// ---------------------------------------------------------------- two-hop packing
+namespace {
+
+__global__ void k_fav_init(int32_t *fav, int64_t n) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x)
+    fav[u] = -2;
+}
+
+__global__ void k_th_flags(const int32_t *fav, int64_t n, int32_t *flag) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x)
+    flag[u] = fav[u] >= 0;
+}
+
+__global__ void k_th_gather(const int32_t *fav, const int32_t *flag, const int64_t *pos, int64_t n,
+                            uint64_t *keys, uint64_t *vals) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x)
+    if (flag[u]) {
+      keys[pos[u]] = (uint64_t)fav[u];
+      vals[pos[u]] = (uint64_t)u;
+    }
+}
+
+// weights in sorted order and run-start markers
+__global__ void k_th_prep(const uint64_t *keys, const uint64_t *vals, const int64_t *vw, int64_t m,
+                          int64_t *wt, int64_t *rs) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    wt[i] = vw ? vw[vals[i]] : 1;
+    rs[i] = (i == 0 || keys[i] != keys[i - 1]) ? i : -1;
+  }
+}
+
+// bins, straddlers and group heads
+__global__ void k_th_heads(const int64_t *excl, const int64_t *rs, const int64_t *wt, int64_t m,
+                           int64_t U, int64_t *head) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t P = excl[i] - excl[rs[i]];
+    int64_t bin = P / U;
+    bool str = P + wt[i] > (bin + 1) * U;
+    bool h = false;
+    if (!str) {
+      if (i == rs[i]) h = true;
+      else {
+        int64_t Pp = excl[i - 1] - excl[rs[i - 1]];
+        int64_t binp = Pp / U;
+        bool strp = Pp + wt[i - 1] > (binp + 1) * U;
+        h = strp || binp != bin;
+      }
+    }
+    head[i] = str ? -2 : (h ? i : -1);
+  }
+}
+
+__global__ void k_th_assign(const int64_t *head_raw, const int64_t *head_scan,
+                            const uint64_t *vals, int64_t m, int32_t *C) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (head_raw[i] == -2) continue;  // straddler stays alone
+    C[vals[i]] = (int32_t)vals[head_scan[i]];
+  }
+}
+
+}  // namespace
+
+void favourites(tp_graph *g, const int32_t *C, const int64_t *Wc, uint64_t rk, int32_t *fav,
+                const tp_params &p, cudaStream_t s) {
+  configure_kernels();
+  k_fav_init<<<grid_for(g->n, 256), 256, 0, s>>>(fav, g->n);
+  TP_LAUNCH_CHECK();
+  RateCtx c{};
+  c.label = C;
+  c.lw = Wc;
+  c.rk = rk;
+  c.fav = fav;
+  rate_tiers<M_FAV>(g, c, p, s);
+}
+
+void two_hop(tp_graph *g, int32_t *C, const int64_t *Wc, int64_t U, uint64_t seed, int32_t level,
+             const tp_params &p, cudaStream_t s) {
+  int64_t n = g->n;
+  if (n == 0) return;
+  Buf<int32_t> fav(n, s), flag(n, s);
+  favourites(g, C, Wc, round_key(seed, kTagTwoHop, (uint64_t)level, 0), fav.get(), p, s);
+  k_th_flags<<<grid_for(n, 256), 256, 0, s>>>(fav.get(), n, flag.get());
+  TP_LAUNCH_CHECK();
+  Buf<int64_t> pos(n + 1, s);
+  exclusive_scan_i32_to_i64(flag.get(), pos.get(), n, s);
+  int64_t m = read_scalar(pos.get() + n, s);
+  if (m == 0) return;
+  Buf<uint64_t> keys(m, s), vals(m, s);
+  k_th_gather<<<grid_for(n, 256), 256, 0, s>>>(fav.get(), flag.get(), pos.get(), n, keys.get(),
+                                                 vals.get());
+  TP_LAUNCH_CHECK();
+  radix_sort_pairs(keys.get(), vals.get(), m, bits_for((uint64_t)n), s);
+  Buf<int64_t> wt(m, s), rs(m, s), excl(m + 1, s), head(m, s), hs(m, s);
+  k_th_prep<<<grid_for(m, 256), 256, 0, s>>>(keys.get(), vals.get(),
+                                               g->unit_vw ? nullptr : g->vw.get(), m, wt.get(),
+                                               rs.get());
+  TP_LAUNCH_CHECK();
+  inclusive_max_scan_i64(rs.get(), rs.get(), m, s);
+  exclusive_scan_i64(wt.get(), excl.get(), m, s);
+  k_th_heads<<<grid_for(m, 256), 256, 0, s>>>(excl.get(), rs.get(), wt.get(), m, U, head.get());
+  TP_LAUNCH_CHECK();
+  inclusive_max_scan_i64(head.get(), hs.get(), m, s);
+  k_th_assign<<<grid_for(m, 256), 256, 0, s>>>(head.get(), hs.get(), vals.get(), m, C);
+  TP_LAUNCH_CHECK();
+}
+
+void lp_cluster(tp_graph *g, int64_t U, const tp_params &p, int32_t level, int32_t *d_cluster,
+                cudaStream_t s) {
+  int64_t n = g->n;
+  if (n == 0) return;
+  Buf<int64_t> Wc(n, s);
+  k_init_singletons<<<grid_for(n, 256), 256, 0, s>>>(g->unit_vw ? nullptr : g->vw.get(), n,
+                                                       d_cluster, Wc.get());
+  TP_LAUNCH_CHECK();
+  LpWork w;
+  w.init(n, n, s);
+  LpState st{d_cluster, Wc.get(), n, U};
+  lp_rounds(g, st, w, p.seed, kTagCluster, (uint64_t)level, 0, p.cluster_rounds, p.sub_rounds, p, s);
+  if (p.two_hop) two_hop(g, d_cluster, Wc.get(), U, p.seed, level, p, s);
+}
+
+void lp_refine(tp_graph *g, int32_t k, int64_t l_max, const tp_params &p, int32_t level,
+               int32_t *d_part, int64_t *d_B, cudaStream_t s) {
+  if (g->n == 0) return;
+  LpWork w;
+  w.init(g->n, k, s);
+  LpState st{d_part, d_B, k, l_max};
+  lp_rounds(g, st, w, p.seed, kTagRefine, (uint64_t)level, 0, p.refine_rounds, p.sub_rounds, p, s);
+}
+
+// ---------------------------------------------------------------- rebalancing
+namespace {
+
+__global__ void k_find_over(const int64_t *B, int32_t k, int64_t l_max, int32_t *out) {
+  __shared__ int32_t best;
+  if (threadIdx.x == 0) best = INT32_MAX;
+  __syncthreads();
+  for (int32_t b = threadIdx.x; b < k; b += blockDim.x)
+    if (B[b] > l_max) atomicMin(&best, b);
+  __syncthreads();
+  if (threadIdx.x == 0) out[0] = best == INT32_MAX ? -1 : best;
+}
+
+__global__ void k_rb_pick(const int32_t *part, int32_t blk, const int32_t *rb_t,
+                          const int64_t *rb_loss, const long long *best, int64_t n, int32_t *best_u) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x)
+    if (part[u] == blk && rb_t[u] >= 0 && rb_loss[u] == *best) atomicMin(best_u, (int32_t)u);
+}
+
+__global__ void k_rb_apply(int32_t *part, int64_t *B, const int64_t *vw, const int32_t *rb_t,
+                           const int32_t *best_u) {
+  int32_t u = *best_u;
+  if (u == INT32_MAX) return;
+  int32_t t = rb_t[u], b = part[u];
+  int64_t w = vw ? vw[u] : 1;
+  B[b] -= w;
+  B[t] += w;
+  part[u] = t;
+}
+
+}  // namespace
+
+void rebalance_moves(tp_graph *g, int32_t k, int64_t l_max, int32_t *d_part, int64_t *d_B,
+                     int *balanced, const tp_params &p, cudaStream_t s) {
+  configure_kernels();
+  int64_t n = g->n;
+  Buf<int32_t> small(4, s);  // [0] overloaded block [1] best vertex
+  Buf<long long> best(1, s);
+  Buf<int32_t> rb_t(std::max<int64_t>(n, 1), s);
+  Buf<int64_t> rb_loss(std::max<int64_t>(n, 1), s);
+  *balanced = 1;
+  for (;;) {
+    k_find_over<<<1, 256, 0, s>>>(d_B, k, l_max, small.get());
+    TP_LAUNCH_CHECK();
+    int32_t blk = read_scalar(small.get(), s);
+    if (blk < 0) return;
+    long long init_best = INT64_MAX;
+    int32_t init_u = INT32_MAX;
+    TP_CUDA(cudaMemcpyAsync(best.get(), &init_best, sizeof(init_best), cudaMemcpyHostToDevice, s));
+    TP_CUDA(cudaMemcpyAsync(small.get() + 1, &init_u, sizeof(init_u), cudaMemcpyHostToDevice, s));
+    RateCtx c{};
+    c.label = d_part;
+    c.lw = d_B;
+    c.cap = l_max;
+    c.blk = blk;
+    c.k = k;
+    c.rb_loss = rb_loss.get();
+    c.rb_t = rb_t.get();
+    c.rb_best = best.get();
+    rate_tiers<M_REBAL>(g, c, p, s);
+    k_rb_pick<<<grid_for(n, 256), 256, 0, s>>>(d_part, blk, rb_t.get(), rb_loss.get(), best.get(),
+                                                 n, small.get() + 1);
+    k_rb_apply<<<1, 1, 0, s>>>(d_part, d_B, g->unit_vw ? nullptr : g->vw.get(), rb_t.get(),
+                               small.get() + 1);
+    TP_LAUNCH_CHECK();
+    int32_t bu = read_scalar(small.get() + 1, s);
+    if (bu == INT32_MAX) {
+      *balanced = 0;
+      return;
+    }
+  }
+}
+
+}  // namespace tp

@@ -1,0 +1,323 @@
+// Internal definitions shared by the library's CUDA translation units.
+// Target: sm_103a (GB300). Nothing here is visible through the C-ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <utility>
+#include <vector>
+
+#include "../../include/terapart.h"
+
+namespace tp {
+
+// ---------------------------------------------------------------- status / errors
+struct Error {
+  tp_status code;
+};
+
+#define TP_CUDA(call)                                                                    \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      fprintf(stderr, "terapart: %s failed: %s (%s:%d)\n", #call, cudaGetErrorString(e_), \
+              __FILE__, __LINE__);                                                       \
+      throw ::tp::Error{e_ == cudaErrorMemoryAllocation ? TP_ERR_OOM : TP_ERR_CUDA};     \
+    }                                                                                    \
+  } while (0)
+
+#define TP_REQUIRE(cond, code)          \
+  do {                                  \
+    if (!(cond)) throw ::tp::Error{code}; \
+  } while (0)
+
+#define TP_LAUNCH_CHECK() TP_CUDA(cudaGetLastError())
+
+// Runs f, converting library exceptions into status codes at the ABI edge.
+template <class F>
+tp_status guard(F &&f) {
+  try {
+    f();
+    return TP_OK;
+  } catch (const Error &e) {
+    return e.code;
+  } catch (...) {
+    return TP_ERR_CUDA;
+  }
+}
+
+// ---------------------------------------------------------------- device memory
+void *dev_alloc(size_t bytes, cudaStream_t s);
+void dev_free(void *p, size_t bytes, cudaStream_t s);
+
+// Owning, stream-ordered device buffer.
+template <class T>
+struct Buf {
+  T *p = nullptr;
+  size_t n = 0;
+  cudaStream_t s = nullptr;
+  Buf() = default;
+  Buf(size_t count, cudaStream_t st) { alloc(count, st); }
+  void alloc(size_t count, cudaStream_t st) {
+    release();
+    s = st;
+    n = count;
+    p = count ? static_cast<T *>(dev_alloc(count * sizeof(T), st)) : nullptr;
+  }
+  void release() {
+    if (p) dev_free(p, n * sizeof(T), s);
+    p = nullptr;
+    n = 0;
+  }
+  T *get() const { return p; }
+  ~Buf() { release(); }
+  Buf(const Buf &) = delete;
+  Buf &operator=(const Buf &) = delete;
+  Buf(Buf &&o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr, o.n = 0; }
+  Buf &operator=(Buf &&o) noexcept {
+    release();
+    p = o.p, n = o.n, s = o.s;
+    o.p = nullptr, o.n = 0;
+    return *this;
+  }
+};
+
+// ---------------------------------------------------------------- graph
+// Degree tiers used by the rating kernels (performance only; the result of
+// a rating never depends on its tier).
+enum : uint8_t { TIER_SMALL = 0, TIER_MID = 1, TIER_BIG = 2, TIER_HUGE = 3 };
+constexpr int64_t kChunkThreshold = 10000;  // compressed format: chunked above this degree
+constexpr int64_t kChunkSize = 1000;        // neighbours per chunk
+
+struct TierCache {
+  bool built = false;
+  int32_t small_max = 0, mid_max = 0;
+  Buf<uint8_t> tier;         // n
+  Buf<int32_t> mid, big, huge;  // vertex lists per tier (ascending)
+  int64_t n_mid = 0, n_big = 0, n_huge = 0;
+  Buf<int64_t> big_toff, huge_toff;  // global table offsets (slots), size n_tier + 1
+  Buf<int32_t> big_tcap, huge_tcap;  // log2 of the table capacity per vertex
+  int64_t big_slots = 0, huge_slots = 0;
+  Buf<int64_t> huge_chunk_start;  // prefix of chunk counts over the huge list (n_huge + 1)
+  int64_t n_huge_chunks = 0;
+  Buf<int32_t> tkeys;  // global rating tables (big + huge), EMPTY = -1
+  Buf<int64_t> tvals;
+};
+
+}  // namespace tp
+
+struct tp_graph {
+  int64_t n = 0, m2 = 0;
+  int compressed = 0;
+  int unit_vw = 1, unit_ew = 1;
+  int64_t total_vw = 0;
+  int64_t max_deg = 0;
+  // CSR
+  tp::Buf<int64_t> xadj;
+  tp::Buf<int32_t> adj;
+  tp::Buf<int64_t> vw, ew;
+  // compressed
+  tp::Buf<uint8_t> bytes;  // padded by kBytePad zero bytes
+  uint64_t nbytes = 0;
+  tp::Buf<uint32_t> off32;
+  tp::Buf<uint64_t> off64;
+  int off_is64 = 0;
+  // per-graph error word (device)
+  tp::Buf<int32_t> err;
+  tp::TierCache tiers;
+};
+
+namespace tp {
+constexpr int kBytePad = 64;
+
+// Read-only device view of a graph for kernels.
+struct GView {
+  int64_t n, m2;
+  const int64_t *xadj;
+  const int32_t *adj;
+  const int64_t *vw;  // null: unit
+  const int64_t *ew;  // null: unit
+  const uint8_t *bytes;
+  const uint32_t *off32;
+  const uint64_t *off64;
+  int compressed;
+  int32_t *err;
+};
+GView view(const tp_graph *g);
+
+// ---------------------------------------------------------------- hashing
+// Counter-based hashing of the deterministic LP (library's own statement of
+// the splitmix64 output function, Steele, Lea and Flood, OOPSLA 2014; the
+// golden-gamma offset keeps a zero input off the fixed point mix(0) = 0).
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t hstep(uint64_t h, uint64_t x) {
+  return mix64(h ^ (x + 0x9e3779b97f4a7c15ULL));
+}
+__host__ __device__ __forceinline__ uint64_t round_key(uint64_t seed, uint64_t tag, uint64_t a,
+                                                       uint64_t b) {
+  return hstep(hstep(hstep(seed, tag), a), b);
+}
+// Phase tags: ASCII mnemonics packed into 64 bits.
+constexpr uint64_t kTagCluster = 0x4c50436c75737472ULL;  // "LPClustr"
+constexpr uint64_t kTagRefine = 0x4c50526566696e65ULL;   // "LPRefine"
+constexpr uint64_t kTagTwoHop = 0x54776f486f704d74ULL;   // "TwoHopMt"
+constexpr uint64_t kTagIPSeed = 0x495053656564566bULL;   // "IPSeedVk"
+constexpr uint64_t kTagIPLP = 0x49504c5032576179ULL;     // "IPLP2Way"
+constexpr uint64_t kTagTie = 0x5469654272656b72ULL;      // "TieBrekr"
+
+__device__ __forceinline__ uint32_t tie_hash(uint64_t hv, int32_t x) {
+  return (uint32_t)(hstep(hv, (uint64_t)(int64_t)x) >> 32);
+}
+
+// Rating order: larger rating, then smaller tie hash, then smaller label.
+__device__ __forceinline__ bool better(int64_t ra, uint32_t ta, int32_t xa, int64_t rb, uint32_t tb,
+                                       int32_t xb) {
+  if (ra != rb) return ra > rb;
+  if (ta != tb) return ta < tb;
+  return xa < xb;
+}
+
+// ---------------------------------------------------------------- warp helpers
+constexpr unsigned kFull = 0xffffffffu;
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Warp argmax under the rating order; returns the winner in all lanes.
+__device__ __forceinline__ void warp_best(int64_t &r, uint32_t &t, int32_t &x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    int64_t r2 = __shfl_xor_sync(kFull, r, o);
+    uint32_t t2 = __shfl_xor_sync(kFull, t, o);
+    int32_t x2 = __shfl_xor_sync(kFull, x, o);
+    if (better(r2, t2, x2, r, t, x)) r = r2, t = t2, x = x2;
+  }
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+template <class T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    T w = __shfl_xor_sync(kFull, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// Inclusive warp scan (sum).
+template <class T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+  int l = lane_id();
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T w = __shfl_up_sync(kFull, v, o);
+    if (l >= o) v += w;
+  }
+  return v;
+}
+
+__device__ __forceinline__ void latch_error(int32_t *err, int32_t code) {
+  if (err) atomicCAS(err, 0, code);
+}
+
+// ---------------------------------------------------------------- launch helpers
+int num_sms();
+inline unsigned grid_for(int64_t work, int block, int64_t max_blocks = 0) {
+  int64_t b = (work + block - 1) / block;
+  if (b < 1) b = 1;
+  int64_t cap = max_blocks ? max_blocks : (int64_t)num_sms() * 32;
+  if (b > cap) b = cap;
+  return (unsigned)b;
+}
+
+// ---------------------------------------------------------------- primitives (prims.cu)
+// Exclusive prefix sum of in[0..n) into out[0..n]; out[n] = total. In-place allowed.
+void exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+void exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
+// Inclusive max-scan of int64.
+void inclusive_max_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+// Stable LSD radix sort of (key, value) pairs by the low `bits` key bits.
+// vals may be null. Buffers are sorted in place (temporary storage internal).
+void radix_sort_pairs(uint64_t *keys, uint64_t *vals, int64_t n, int bits, cudaStream_t s);
+// Reads one device value synchronously.
+template <class T>
+T read_scalar(const T *d, cudaStream_t s) {
+  T h;
+  TP_CUDA(cudaMemcpyAsync(&h, d, sizeof(T), cudaMemcpyDeviceToHost, s));
+  TP_CUDA(cudaStreamSynchronize(s));
+  return h;
+}
+int bits_for(uint64_t max_value);  // bits needed to represent values <= max_value
+
+// ---------------------------------------------------------------- graph helpers (graph.cu)
+tp_graph *new_graph();
+void compute_degrees(const tp_graph *g, int64_t *d_deg, cudaStream_t s);  // n entries
+void build_tiers(tp_graph *g, const tp_params &p, cudaStream_t s);
+
+// ---------------------------------------------------------------- LP (lp.cu)
+struct LpState {
+  int32_t *label;
+  int64_t *lw;
+  int64_t nlabels;
+  int64_t cap;  // uniform cap for every label
+};
+// Workspace for sub-rounds on one graph (per-label counters + mover lists).
+struct LpWork {
+  int64_t nlabels = 0, n = 0;
+  Buf<int64_t> in_w;    // nlabels
+  Buf<int32_t> in_cnt;  // nlabels
+  Buf<int32_t> cstate;  // nlabels
+  Buf<int32_t> cfill;   // nlabels
+  Buf<int64_t> cbase;   // nlabels
+  Buf<int32_t> mv_u, mv_t;  // n
+  Buf<int64_t> mv_g;        // n
+  Buf<int8_t> mv_ok;        // n
+  Buf<int32_t> cseg;        // n (contested mover indices grouped by target)
+  Buf<int32_t> ctarget;     // nlabels (contested targets)
+  Buf<int64_t> counters;    // [0] movers, [1] contested targets, [2] contested pool
+  void init(int64_t n_vertices, int64_t n_labels, cudaStream_t s);
+};
+void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t S, int32_t s,
+                 const tp_params &p, cudaStream_t stream);
+void lp_rounds(tp_graph *g, const LpState &st, LpWork &w, uint64_t seed, uint64_t tag, uint64_t a,
+               uint64_t b0, int32_t rounds, int32_t S, const tp_params &p, cudaStream_t stream);
+void lp_cluster(tp_graph *g, int64_t U, const tp_params &p, int32_t level, int32_t *d_cluster,
+                cudaStream_t s);
+void lp_refine(tp_graph *g, int32_t k, int64_t l_max, const tp_params &p, int32_t level,
+               int32_t *d_part, int64_t *d_B, cudaStream_t s);
+// Per-vertex favourite cluster of singletons (two-hop): fav[u] = best label or n.
+void favourites(tp_graph *g, const int32_t *C, const int64_t *Wc, uint64_t rk, int32_t *fav,
+                const tp_params &p, cudaStream_t s);
+void two_hop(tp_graph *g, int32_t *C, const int64_t *Wc, int64_t U, uint64_t seed, int32_t level,
+             const tp_params &p, cudaStream_t s);
+void rebalance_moves(tp_graph *g, int32_t k, int64_t l_max, int32_t *d_part, int64_t *d_B,
+                     int *balanced, const tp_params &p, cudaStream_t s);
+
+// ---------------------------------------------------------------- contraction / IP / metrics
+tp_graph *contract(const tp_graph *g, const int32_t *C, int32_t *d_map, cudaStream_t s);
+void initial_partition(const tp_graph *g, int32_t k, int64_t l_max, const tp_params &p,
+                       int32_t *d_part, cudaStream_t s);
+void block_weights(const tp_graph *g, const int32_t *part, int32_t k, int64_t *d_B,
+                   cudaStream_t s);
+int64_t edge_cut(const tp_graph *g, const int32_t *part, cudaStream_t s);
+void project(const int32_t *coarse_part, const int32_t *map, int64_t n, int32_t *fine_part,
+             cudaStream_t s);
+
+int64_t cluster_cap(int64_t W, int32_t k, int64_t eps_ppm);
+int64_t block_cap(int64_t W, int32_t k, int64_t eps_ppm);
+
+}  // namespace tp
