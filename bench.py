@@ -1,0 +1,403 @@
+#!/usr/bin/env python3
+"""Benchmark of the GPU multilevel partitioner; prints one JSON line.
+
+A step is one pass of the whole hot path over the benchmark graph:
+compression of the CSR graph into the gap+VarInt format, a full multilevel
+partition of the compressed graph, and a full partition of the plain CSR
+graph (the metric compares both paths). Inputs are resident in HBM when the
+timed region starts and are larger than L2, so no flush is needed.
+
+value = level-0 LP clustering throughput on the compressed graph in GTEPS:
+(clustering rounds x 2m adjacency entries) / CUDA-event time of those rounds.
+
+--impl reference times the CPU oracle (the reference arm of this repo) on
+bounded samples of the same workload.
+
+Multi-GPU (torchrun, one process per GPU): the path shards as independent
+graphs, so every rank partitions its own replica of the workload with no
+collective on the data path (weak scaling); only the barrier and the
+max-over-ranks timing use the process group.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LP clustering GTEPS + partition time, compressed vs CSR; % of HBM peak"
+WORKLOADS = {
+    "rgg24": dict(gen="rgg2d", n=1 << 24, deg=16.0, k=64, seed=1,
+                  desc="2D random geometric graph n=2^24, expected degree 16, unit weights, "
+                       "k=64, eps=0.03, seed 1; gap+VarInt compressed and int32 CSR"),
+    "gnm14": dict(gen="gnm", n=1 << 14, m=1 << 17, k=8, seed=1,
+                  desc="G(n,m) n=2^14 m=2^17, unit weights, k=8, eps=0.03, seed 1"),
+    "rmat26": dict(gen="rmat", scale=26, ef=16, k=256, seed=1,
+                   desc="R-MAT scale 26 edge factor 16 (0.57,0.19,0.19,0.05), symmetrised, "
+                        "deduplicated, k=256, eps=0.03, seed 1; compressed with chunking and CSR"),
+}
+EPS = 0.03
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_NAMES = {"rate_lane": "k_rate_lane", "rate_small": "k_rate_small",
+                "rate_mid": "k_rate_list (shared tables)", "rate_big": "k_rate_list (global tables)",
+                "rate_huge": "k_rate_huge_chunks + k_rate_huge_decide"}
+
+
+def make_graph(w):
+    import synth
+
+    if w["gen"] == "rgg2d":
+        return synth.rgg2d(w["n"], w["deg"], w["seed"])
+    if w["gen"] == "gnm":
+        return synth.gnm(w["n"], w["m"], w["seed"])
+    return synth.rmat(w["scale"], w["ef"], seed=w["seed"])
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def library_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2410_19119_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_tag, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernels (same source hash) and workload."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}_{workload}.txt")
+    try:
+        fields = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    fields[k.strip()] = v.strip()
+        if fields.get("source_hash") != library_hash():
+            return None
+        return float(fields["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) < 9:
+                        continue
+                    try:
+                        sm.append(float(parts[1]))
+                        mx = float(parts[2])
+                    except ValueError:
+                        continue
+                    for name, val in zip(names, parts[5:9]):
+                        if val.lower().startswith("active"):
+                            reasons.add(name)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_lp(xadj, adj, k, seed, max_rounds=5, budget_s=12.0):
+    """Oracle level-0 clustering rounds (one thread) until the budget is spent."""
+    import oracle
+
+    g = oracle.Graph(xadj, adj)
+    n = g.n
+    U = oracle.cluster_cap(n, k, oracle.eps_to_ppm(EPS))
+    label = np.arange(n, dtype=np.int32)
+    lw = np.ones(n, np.int64)
+    t0 = time.perf_counter()
+    rounds = 0
+    while rounds < max_rounds:
+        oracle.lp_rounds(g, label, lw, n, U, None, seed, oracle.tag(oracle.TAG_CLUSTER), 0, rounds,
+                         1, 8)
+        rounds += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return rounds * len(adj) / dt / 1e9, rounds, dt
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    xadj, adj = make_graph(w)
+    g = oracle.Graph(xadj, adj)
+    n = g.n
+    U = oracle.cluster_cap(n, w["k"], oracle.eps_to_ppm(EPS))
+    label = np.arange(n, dtype=np.int32)
+    lw = np.ones(n, np.int64)
+    tag = oracle.tag(oracle.TAG_CLUSTER)
+    r = 0
+
+    def one_round():
+        nonlocal r, label, lw
+        if r == 5:  # a level has five rounds; start the level again
+            label = np.arange(n, dtype=np.int32)
+            lw = np.ones(n, np.int64)
+            r = 0
+        oracle.lp_rounds(g, label, lw, n, U, None, w["seed"], tag, 0, r, 1, 8)
+        r += 1
+
+    for _ in range(args.warmup):
+        one_round()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one_round()
+    dt = time.perf_counter() - t0
+    value = args.steps * len(adj) / dt / 1e9
+    sample = f"one level-0 LP clustering round (8 sub-rounds) of the full graph per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": w["desc"]},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args, w):
+    import torch
+
+    import paper_2410_19119_gb300 as tp
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    dev_index = vis.split(",")[local] if vis and len(vis.split(",")) > local else str(local)
+    xadj, adj = make_graph(w)
+    n, m2 = len(xadj) - 1, len(adj)
+    k = w["k"]
+    params = tp.default_params(seed=w["seed"])
+    stream = torch.cuda.current_stream()
+    g = tp.graph_from_csr(xadj, adj)
+
+    def step(profile):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        z = g.compress()
+        ev[1].record(stream)
+        if profile:
+            tp.profile_enable(True)
+        _, stz = tp.partition(z, k, EPS, params)
+        if profile:
+            tp.profile_enable(False)
+        ev[2].record(stream)
+        _, stc = tp.partition(g, k, EPS, params)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        zinfo = z.info()
+        return {"step_ms": ev[0].elapsed_time(ev[3]), "compress_ms": ev[0].elapsed_time(ev[1]),
+                "part_z_ms": ev[1].elapsed_time(ev[2]), "part_c_ms": ev[2].elapsed_time(ev[3]),
+                "stz": stz, "stc": stc, "zbytes": zinfo["bytes"], "zstream": zinfo["stream_bytes"]}
+
+    for _ in range(args.warmup):
+        step(False)
+        tp.profile_read()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = tp.launch_count()
+    prof = {}
+    recs = []
+    with ClockSampler(dev_index) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for _ in range(args.steps):
+            recs.append(step(True))
+            for fam, e in tp.profile_read().items():
+                acc = prof.setdefault(fam, {"launches": 0, "ms": 0.0, "bytes": 0.0})
+                for key in acc:
+                    acc[key] += e[key]
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    launches = tp.launch_count() - launches0
+    total_ms = t_start.elapsed_time(t_end)
+    rounds = params.cluster_rounds
+    lp_edges = rounds * m2 * args.steps
+    lp_ms_z = sum(r["stz"]["ms_lp_level0"] for r in recs)
+    lp_ms_c = sum(r["stc"]["ms_lp_level0"] for r in recs)
+    if dist:
+        t = torch.tensor([total_ms, lp_ms_z, lp_ms_c], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, lp_ms_z, lp_ms_c = t.tolist()
+    value = ws * lp_edges / lp_ms_z / 1e6
+    gteps_csr = ws * lp_edges / lp_ms_c / 1e6
+
+    # end to end through the public API: host CSR in pinned memory -> device
+    # graph -> compress -> partition -> partition read back to the host
+    px = torch.from_numpy(xadj).pin_memory()
+    pa = torch.from_numpy(adj).pin_memory()
+    host_part = torch.empty(n, dtype=torch.int32).pin_memory()
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gh = tp.graph_from_csr(px, pa)
+        zh = gh.compress()
+        part, _ = tp.partition(zh, k, EPS, params)
+        host_part.copy_(part, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        del gh, zh
+        if i >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_step = sum(e2e_ms) / len(e2e_ms)
+    if dist:
+        t = torch.tensor([e2e_step], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_step = t.item()
+    e2e_value = ws * rounds * m2 / e2e_step / 1e6
+
+    if rank != 0:
+        dist.barrier()
+        dist.destroy_process_group()
+        return
+    hbm, peak_kind = peaks()
+    r0 = recs[0]
+    # dominant rating kernel of the level-0 clustering rounds (by device time)
+    rating = {f: e for f, e in prof.items() if f.startswith("rate_") and e["launches"]}
+    top = max(rating, key=lambda f: rating[f]["ms"]) if rating else None
+    roofline = None
+    if top:
+        e = rating[top]
+        per_launch_bytes = e["bytes"] / e["launches"]
+        per_launch_ms = e["ms"] / e["launches"]
+        achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+        roofline = {"kernel": KERNEL_NAMES[top] + " (level-0 LP rating, compressed graph)",
+                    "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "peak_source": peak_kind,
+                    "traffic": ncu_traffic(top, args.workload),
+                    "alg_bytes_per_launch": per_launch_bytes, "launch_ms": per_launch_ms,
+                    "launches": e["launches"]}
+    line = {
+        "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": w["desc"], "n": n, "m2": m2, "k": k, "eps": EPS,
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"},
+        "lp_gteps_csr": gteps_csr,
+        "lp_ms_level0_compressed": lp_ms_z / args.steps, "lp_ms_level0_csr": lp_ms_c / args.steps,
+        "partition_ms_compressed": statistics.mean(r["part_z_ms"] for r in recs),
+        "partition_ms_csr": statistics.mean(r["part_c_ms"] for r in recs),
+        "partition_ms_compressed_incl_compress": statistics.mean(
+            r["part_z_ms"] + r["compress_ms"] for r in recs),
+        "compress_ms": statistics.mean(r["compress_ms"] for r in recs),
+        "compressed_bytes": r0["zbytes"], "csr_bytes": 8 * (n + 1) + 4 * m2,
+        "cut": r0["stz"]["cut"], "cut_csr_path": r0["stc"]["cut"],
+        "imbalance": r0["stz"]["imbalance"], "levels": r0["stz"]["levels"],
+        "phase_ms_compressed": {"coarsen": r0["stz"]["ms_coarsen"],
+                                "initial": r0["stz"]["ms_initial"],
+                                "uncoarsen": r0["stz"]["ms_uncoarsen"]},
+        "kernel_profile": prof,
+        "roofline": roofline,
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_value, "unit": "GTEPS (level-0 LP edges per end-to-end second)",
+                "ms_per_step": e2e_step, "h2d_bytes_per_step": 8 * (n + 1) + 4 * m2,
+                "d2h_bytes_per_step": 4 * n},
+        "gpu_launches": launches,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        v, rounds_done, dt = cpu_oracle_lp(xadj, adj, k, w["seed"])
+        line["cpu_baseline"] = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                                "sample": f"{rounds_done} level-0 LP clustering round(s) of the "
+                                          f"full CSR graph in {dt:.1f} s, one thread"}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="rgg24")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_native(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -67,6 +67,7 @@ typedef struct {
   int32_t two_hop;        /* pack leftover singletons after clustering (1) */
   int32_t max_levels;     /* hierarchy depth limit, <= 64 (64) */
   /* performance only */
+  int32_t tier_lane;     /* max degree rated one lane per vertex (32; 0 = off) */
   int32_t tier_small;    /* max degree rated with the small shared table (64) */
   int32_t tier_mid;      /* max degree rated with the large shared table (1000) */
   int32_t warps_per_block; /* warps per block in the small tier (8) */
@@ -220,6 +221,31 @@ tp_status tp_metrics(const tp_graph *g, const int32_t *d_part, int32_t k, int64_
  * (nullable) is filled on return; the call synchronises the stream. */
 tp_status tp_partition(const tp_graph *g, int32_t k, double eps, const tp_params *p,
                        int32_t *d_part, tp_stats *stats, void *stream);
+
+/* ---- tracing ---- */
+
+/* Number of kernels the library has launched in this process so far. */
+uint64_t tp_launch_count(void);
+
+/* Opt-in kernel timing. When enabled, the library records a CUDA event pair
+ * around selected launches of the level-0 clustering rounds (the hot path
+ * of Algorithm 1 / Algorithm 2) on the stream they run on, together with
+ * the algorithmic bytes the launch must move. Families: 0 small-degree
+ * rating (one warp per vertex), 1 mid-degree rating, 2 big-degree rating,
+ * 3 chunked hub rating (both of its kernels), 4 approval and apply,
+ * 5 low-degree rating with one lane per vertex. */
+typedef struct {
+  int32_t family;
+  int64_t launches;
+  double ms;    /* summed event time */
+  double bytes; /* summed algorithmic bytes */
+} tp_profile_entry;
+void tp_profile_enable(int on);
+
+/* Synchronises stream, folds the recorded events into out[0..max) (one
+ * entry per family, index = family) and clears them. Returns the number of
+ * entries written, -1 on a CUDA error. */
+int tp_profile_read(tp_profile_entry *out, int max, void *stream);
 
 #ifdef __cplusplus
 }

@@ -11,11 +11,14 @@ import ctypes
 
 import numpy as np
 
-from ._lib import Params, Stats, TpError, check, lib
+from ._lib import ProfileEntry, Params, Stats, TpError, check, lib
 
 __all__ = ["Graph", "Params", "Stats", "TpError", "default_params", "graph_from_csr",
            "graph_from_compressed", "partition", "lp_cluster", "lp_subround", "contract",
-           "initial_partition", "lp_refine", "rebalance", "metrics"]
+           "initial_partition", "lp_refine", "rebalance", "metrics", "launch_count",
+           "profile_enable", "profile_read", "PROFILE_FAMILIES"]
+
+PROFILE_FAMILIES = ("rate_small", "rate_mid", "rate_big", "rate_huge", "approve", "rate_lane")
 
 
 def _torch():
@@ -120,10 +123,15 @@ class Graph:
             self._h = ctypes.c_void_p()
 
 
+def _is_host(x):
+    return isinstance(x, np.ndarray) or getattr(getattr(x, "device", None), "type", "") == "cpu"
+
+
 def graph_from_csr(xadj, adj, vw=None, ew=None, stream=None) -> Graph:
-    """xadj int64[n+1], adj int32[2m] (numpy = host, torch CUDA = device)."""
-    host = isinstance(xadj, np.ndarray)
-    if host:
+    """xadj int64[n+1], adj int32[2m]: numpy arrays or CPU tensors (copied in
+    from host memory, pinned tensors asynchronously) or CUDA tensors."""
+    host = _is_host(xadj)
+    if isinstance(xadj, np.ndarray):
         xadj = np.ascontiguousarray(xadj, np.int64)
         adj = np.ascontiguousarray(adj, np.int32)
         vw = None if vw is None else np.ascontiguousarray(vw, np.int64)
@@ -224,3 +232,22 @@ def partition(g: Graph, k, eps=0.03, params=None, out=None, stream=None):
                              _stream(stream)), "tp_partition")
     return part[:n], stats_dict(st)
 
+
+
+def launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    return lib().tp_launch_count()
+
+
+def profile_enable(on: bool = True):
+    lib().tp_profile_enable(int(on))
+
+
+def profile_read(stream=None):
+    """Per-family {launches, ms, bytes} of the profiled level-0 LP launches (clears them)."""
+    arr = (ProfileEntry * len(PROFILE_FAMILIES))()
+    k = lib().tp_profile_read(arr, len(arr), _stream(stream))
+    if k < 0:
+        raise TpError(3, "tp_profile_read")
+    return {PROFILE_FAMILIES[i]: {"launches": arr[i].launches, "ms": arr[i].ms, "bytes": arr[i].bytes}
+            for i in range(k)}

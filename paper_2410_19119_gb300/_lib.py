@@ -25,7 +25,7 @@ class TpError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("seed", u64), ("cluster_rounds", i32), ("refine_rounds", i32),
                 ("sub_rounds", i32), ("c_lim", i32), ("ip_attempts", i32), ("two_hop", i32),
-                ("max_levels", i32), ("tier_small", i32), ("tier_mid", i32),
+                ("max_levels", i32), ("tier_lane", i32), ("tier_small", i32), ("tier_mid", i32),
                 ("warps_per_block", i32), ("use_graphs", i32), ("graph_n", i32)]
 
 
@@ -35,6 +35,10 @@ class Stats(ctypes.Structure):
                 ("level_n", i64 * 64), ("level_m2", i64 * 64), ("ms_coarsen", ctypes.c_double),
                 ("ms_initial", ctypes.c_double), ("ms_uncoarsen", ctypes.c_double),
                 ("ms_lp_level0", ctypes.c_double)]
+
+
+class ProfileEntry(ctypes.Structure):
+    _fields_ = [("family", i32), ("launches", i64), ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
 SIGNATURES = {
@@ -58,6 +62,9 @@ SIGNATURES = {
     "tp_rebalance": (ctypes.c_int, [vp, i32, i64, vp, P(ctypes.c_int), vp]),
     "tp_metrics": (ctypes.c_int, [vp, vp, i32, P(i64), vp, vp]),
     "tp_partition": (ctypes.c_int, [vp, i32, ctypes.c_double, P(Params), vp, P(Stats), vp]),
+    "tp_launch_count": (u64, []),
+    "tp_profile_enable": (None, [ctypes.c_int]),
+    "tp_profile_read": (ctypes.c_int, [P(ProfileEntry), ctypes.c_int, vp]),
 }
 
 _lib = None

@@ -63,6 +63,7 @@ void tp_params_default(tp_params *p) {
   p->ip_attempts = 8;
   p->two_hop = 1;
   p->max_levels = 64;
+  p->tier_lane = 32;
   p->tier_small = 64;
   p->tier_mid = 1000;
   p->warps_per_block = 8;

@@ -155,7 +155,7 @@ tp_graph *contract(const tp_graph *g, const int32_t *C, int32_t *d_map, cudaStre
     }
     Buf<int32_t> flag(n, s);
     TP_CUDA(cudaMemsetAsync(flag.get(), 0, n * sizeof(int32_t), s));
-    k_mark<<<grid_for(n, 256), 256, 0, s>>>(C, n, flag.get());
+    launch(k_mark, grid_for(n, 256), 256, 0, s, C, n, flag.get());
     TP_LAUNCH_CHECK();
     Buf<int64_t> rank(n + 1, s);
     exclusive_scan_i32_to_i64(flag.get(), rank.get(), n, s);
@@ -169,7 +169,7 @@ tp_graph *contract(const tp_graph *g, const int32_t *C, int32_t *d_map, cudaStre
     }
     cg->vw.alloc(nc, s);
     TP_CUDA(cudaMemsetAsync(cg->vw.get(), 0, nc * sizeof(int64_t), s));
-    k_map<<<grid_for(n, 256), 256, 0, s>>>(C, rank.get(), g->unit_vw ? nullptr : g->vw.get(), n,
+    launch(k_map, grid_for(n, 256), 256, 0, s, C, rank.get(), g->unit_vw ? nullptr : g->vw.get(), n,
                                              map, cg->vw.get());
     TP_LAUNCH_CHECK();
     cg->total_vw = g->total_vw;
@@ -183,8 +183,8 @@ tp_graph *contract(const tp_graph *g, const int32_t *C, int32_t *d_map, cudaStre
     const bool comp = g->compressed;
     Buf<int64_t> off(n + 1, s);
     unsigned wb = grid_for(n * 32, 256);
-    if (comp) k_count<true><<<wb, 256, 0, s>>>(v, T.tier.get(), map, off.get());
-    else k_count<false><<<wb, 256, 0, s>>>(v, T.tier.get(), map, off.get());
+    if (comp) launch(k_count<true>, wb, 256, 0, s, v, T.tier.get(), map, off.get());
+    else launch(k_count<false>, wb, 256, 0, s, v, T.tier.get(), map, off.get());
     TP_LAUNCH_CHECK();
     exclusive_scan_i64(off.get(), off.get(), n, s);
     int64_t m_small = read_scalar(off.get() + n, s);
@@ -194,10 +194,10 @@ tp_graph *contract(const tp_graph *g, const int32_t *C, int32_t *d_map, cudaStre
       hoff.alloc(T.n_huge_chunks + 1, s);
       unsigned hb = grid_for(T.n_huge_chunks * 32, 256);
       if (comp)
-        k_count_chunks<true><<<hb, 256, 0, s>>>(v, T.huge.get(), T.n_huge, T.huge_chunk_start.get(),
+        launch(k_count_chunks<true>, hb, 256, 0, s, v, T.huge.get(), T.n_huge, T.huge_chunk_start.get(),
                                                 T.n_huge_chunks, map, hoff.get());
       else
-        k_count_chunks<false><<<hb, 256, 0, s>>>(v, T.huge.get(), T.n_huge, T.huge_chunk_start.get(),
+        launch(k_count_chunks<false>, hb, 256, 0, s, v, T.huge.get(), T.n_huge, T.huge_chunk_start.get(),
                                                  T.n_huge_chunks, map, hoff.get());
       TP_LAUNCH_CHECK();
       exclusive_scan_i64(hoff.get(), hoff.get(), T.n_huge_chunks, s);
@@ -207,17 +207,17 @@ tp_graph *contract(const tp_graph *g, const int32_t *C, int32_t *d_map, cudaStre
     const bool weighted = !g->unit_ew;
     Buf<uint64_t> keys(std::max<int64_t>(m, 1), s), vals;
     if (weighted) vals.alloc(std::max<int64_t>(m, 1), s);
-    if (comp) k_emit<true><<<wb, 256, 0, s>>>(v, T.tier.get(), map, nc, off.get(), keys.get(), vals.get());
-    else k_emit<false><<<wb, 256, 0, s>>>(v, T.tier.get(), map, nc, off.get(), keys.get(), vals.get());
+    if (comp) launch(k_emit<true>, wb, 256, 0, s, v, T.tier.get(), map, nc, off.get(), keys.get(), vals.get());
+    else launch(k_emit<false>, wb, 256, 0, s, v, T.tier.get(), map, nc, off.get(), keys.get(), vals.get());
     TP_LAUNCH_CHECK();
     if (T.n_huge) {
       unsigned hb = grid_for(T.n_huge_chunks * 32, 256);
       if (comp)
-        k_emit_chunks<true><<<hb, 256, 0, s>>>(v, T.huge.get(), T.n_huge, T.huge_chunk_start.get(),
+        launch(k_emit_chunks<true>, hb, 256, 0, s, v, T.huge.get(), T.n_huge, T.huge_chunk_start.get(),
                                                T.n_huge_chunks, map, nc, m_small, hoff.get(),
                                                keys.get(), vals.get());
       else
-        k_emit_chunks<false><<<hb, 256, 0, s>>>(v, T.huge.get(), T.n_huge, T.huge_chunk_start.get(),
+        launch(k_emit_chunks<false>, hb, 256, 0, s, v, T.huge.get(), T.n_huge, T.huge_chunk_start.get(),
                                                 T.n_huge_chunks, map, nc, m_small, hoff.get(),
                                                 keys.get(), vals.get());
       TP_LAUNCH_CHECK();
@@ -228,19 +228,20 @@ tp_graph *contract(const tp_graph *g, const int32_t *C, int32_t *d_map, cudaStre
     Buf<int32_t> hf(std::max<int64_t>(m, 1), s);
     Buf<int64_t> idx(m + 1, s);
     if (m) {
-      k_heads<<<grid_for(m, 256), 256, 0, s>>>(keys.get(), m, hf.get());
+      launch(k_heads, grid_for(m, 256), 256, 0, s, keys.get(), m, hf.get());
       TP_LAUNCH_CHECK();
     }
     exclusive_scan_i32_to_i64(hf.get(), idx.get(), m, s);
     int64_t m2 = read_scalar(idx.get() + m, s);
     cg->m2 = m2;
-    cg->adj.alloc(m2, s);
+    cg->adj.alloc(m2 + kAdjPad, s);
+    TP_CUDA(cudaMemsetAsync(cg->adj.get() + m2, 0, kAdjPad * sizeof(int32_t), s));
     cg->ew.alloc(m2, s);
     cg->xadj.alloc(nc + 1, s);
     if (m2) TP_CUDA(cudaMemsetAsync(cg->ew.get(), 0, m2 * sizeof(int64_t), s));
     TP_CUDA(cudaMemsetAsync(cg->xadj.get(), 0, (nc + 1) * sizeof(int64_t), s));
     if (m) {
-      k_reduce<<<grid_for(m, 256), 256, 0, s>>>(keys.get(), weighted ? vals.get() : nullptr,
+      launch(k_reduce, grid_for(m, 256), 256, 0, s, keys.get(), weighted ? vals.get() : nullptr,
                                                   idx.get(), m, nc, cg->adj.get(), cg->ew.get(),
                                                   cg->xadj.get());
       TP_LAUNCH_CHECK();

@@ -43,6 +43,49 @@ void dev_free(void *p, size_t bytes, cudaStream_t s) {
   cudaFreeAsync(p, s);
 }
 
+namespace {
+std::atomic<uint64_t> g_launches{0};
+
+struct ProfRecord {
+  int family;
+  cudaEvent_t a, b;
+  double bytes;
+};
+struct Profiler {
+  bool enabled = false, scope = false;
+  std::vector<ProfRecord> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t open[PF_COUNT] = {};
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    TP_CUDA(cudaEventCreate(&e));
+    return e;
+  }
+} g_prof;
+}  // namespace
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+bool prof_active() { return g_prof.enabled && g_prof.scope; }
+void prof_scope(bool on) { g_prof.scope = on; }
+void prof_begin(int family, cudaStream_t s) {
+  if (!prof_active()) return;
+  cudaEvent_t e = g_prof.get();
+  TP_CUDA(cudaEventRecord(e, s));
+  g_prof.open[family] = e;
+}
+void prof_end(int family, cudaStream_t s, double alg_bytes) {
+  if (!prof_active() || !g_prof.open[family]) return;
+  cudaEvent_t e = g_prof.get();
+  TP_CUDA(cudaEventRecord(e, s));
+  g_prof.recs.push_back({family, g_prof.open[family], e, alg_bytes});
+  g_prof.open[family] = nullptr;
+}
+
 int num_sms() {
   if (!g_sms) {
     int dev = 0;
@@ -151,29 +194,39 @@ void compute_degrees(const tp_graph *g, int64_t *d_deg, cudaStream_t s) {
   if (g->n == 0) return;
   GView v = view(g);
   if (g->compressed)
-    k_zip_degrees<<<grid_for(g->n, 256), 256, 0, s>>>(v, d_deg);
+    launch(k_zip_degrees, grid_for(g->n, 256), 256, 0, s, v, d_deg);
   else
-    k_csr_degrees<<<grid_for(g->n, 256), 256, 0, s>>>(g->xadj.get(), g->n, d_deg);
+    launch(k_csr_degrees, grid_for(g->n, 256), 256, 0, s, g->xadj.get(), g->n, d_deg);
   TP_LAUNCH_CHECK();
 }
 
 // ---------------------------------------------------------------- tiers
 namespace {
 
-__global__ void k_classify(const int64_t *deg, int64_t n, int32_t small_max, int32_t mid_max,
-                           uint8_t *tier, int32_t *flag_mid, int32_t *flag_big,
-                           int32_t *flag_huge) {
+__global__ void k_classify(const int64_t *deg, int64_t n, int32_t lane_max, int32_t small_max,
+                           int32_t mid_max, uint8_t *tier, int32_t *flag_small, int32_t *flag_mid,
+                           int32_t *flag_big, int32_t *flag_huge, unsigned long long *stats) {
+  int64_t e[5] = {0, 0, 0, 0, 0}, c[5] = {0, 0, 0, 0, 0};
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
        u += (int64_t)gridDim.x * blockDim.x) {
     int64_t d = deg[u];
-    uint8_t t = d <= small_max ? TIER_SMALL
+    uint8_t t = (lane_max > 0 && d <= lane_max) ? TIER_LANE
+                : d <= small_max ? TIER_SMALL
                 : d <= mid_max ? TIER_MID
                 : d <= kChunkThreshold ? TIER_BIG
                                : TIER_HUGE;
     tier[u] = t;
+    flag_small[u] = t == TIER_SMALL;
     flag_mid[u] = t == TIER_MID;
     flag_big[u] = t == TIER_BIG;
     flag_huge[u] = t == TIER_HUGE;
+    e[t] += d;
+    c[t] += 1;
+  }
+  for (int t = 0; t < 5; ++t) {
+    int64_t v = warp_sum(e[t]), w = warp_sum(c[t]);
+    if (lane_id() == 0 && v) atomicAdd(&stats[t], (unsigned long long)v);
+    if (lane_id() == 0 && w) atomicAdd(&stats[5 + t], (unsigned long long)w);
   }
 }
 
@@ -209,10 +262,13 @@ __global__ void k_fill_table(int32_t *keys, int64_t *vals, int64_t n) {
 
 void build_tiers(tp_graph *g, const tp_params &p, cudaStream_t s) {
   TierCache &T = g->tiers;
-  int32_t small_max = std::min(p.tier_small, 64);
+  // the lane tier rates with one lane per vertex and needs unit edge weights
+  int32_t lane_max = g->unit_ew ? std::max(0, std::min(p.tier_lane, kLaneMaxDeg)) : 0;
+  int32_t small_max = std::max(lane_max, std::min(p.tier_small, 64));
   int32_t mid_max = std::max(small_max, std::min(p.tier_mid, 1024));
-  if (T.built && T.small_max == small_max && T.mid_max == mid_max) return;
+  if (T.built && T.small_max == small_max && T.mid_max == mid_max && T.lane_max == lane_max) return;
   T = TierCache();
+  T.lane_max = lane_max;
   T.small_max = small_max;
   T.mid_max = mid_max;
   int64_t n = g->n;
@@ -223,20 +279,27 @@ void build_tiers(tp_graph *g, const tp_params &p, cudaStream_t s) {
   }
   Buf<int64_t> deg(n, s);
   compute_degrees(g, deg.get(), s);
-  Buf<int32_t> fm(n, s), fb(n, s), fh(n, s);
-  k_classify<<<grid_for(n, 256), 256, 0, s>>>(deg.get(), n, small_max, mid_max, T.tier.get(),
-                                                fm.get(), fb.get(), fh.get());
+  Buf<int32_t> fs(n, s), fm(n, s), fb(n, s), fh(n, s);
+  Buf<unsigned long long> te(10, s);
+  TP_CUDA(cudaMemsetAsync(te.get(), 0, 10 * sizeof(unsigned long long), s));
+  launch(k_classify, grid_for(n, 256), 256, 0, s, deg.get(), n, lane_max, small_max, mid_max,
+         T.tier.get(), fs.get(), fm.get(), fb.get(), fh.get(), te.get());
   TP_LAUNCH_CHECK();
+  unsigned long long hte[10];
+  TP_CUDA(cudaMemcpyAsync(hte, te.get(), sizeof(hte), cudaMemcpyDeviceToHost, s));
+  TP_CUDA(cudaStreamSynchronize(s));
+  for (int t = 0; t < 5; ++t) T.edges[t] = (int64_t)hte[t], T.count[t] = (int64_t)hte[5 + t];
   Buf<int64_t> pos(n + 1, s);
   auto make_list = [&](Buf<int32_t> &flag, Buf<int32_t> &list, int64_t &cnt) {
     exclusive_scan_i32_to_i64(flag.get(), pos.get(), n, s);
     cnt = read_scalar(pos.get() + n, s);
     list.alloc(cnt, s);
     if (cnt) {
-      k_compact<<<grid_for(n, 256), 256, 0, s>>>(flag.get(), pos.get(), n, list.get());
+      launch(k_compact, grid_for(n, 256), 256, 0, s, flag.get(), pos.get(), n, list.get());
       TP_LAUNCH_CHECK();
     }
   };
+  make_list(fs, T.small, T.n_small);
   make_list(fm, T.mid, T.n_mid);
   make_list(fb, T.big, T.n_big);
   make_list(fh, T.huge, T.n_huge);
@@ -252,7 +315,7 @@ void build_tiers(tp_graph *g, const tp_params &p, cudaStream_t s) {
       chunk_start->alloc(cnt + 1, s);
       ch.alloc(cnt, s);
     }
-    k_table_caps<<<grid_for(cnt, 256), 256, 0, s>>>(list.get(), cnt, deg.get(), toff.get(),
+    launch(k_table_caps, grid_for(cnt, 256), 256, 0, s, list.get(), cnt, deg.get(), toff.get(),
                                                       tcap.get(), chunk_start ? ch.get() : nullptr);
     TP_LAUNCH_CHECK();
     exclusive_scan_i64(toff.get(), toff.get(), cnt, s);
@@ -269,7 +332,7 @@ void build_tiers(tp_graph *g, const tp_params &p, cudaStream_t s) {
   if (total) {
     T.tkeys.alloc(total, s);
     T.tvals.alloc(total, s);
-    k_fill_table<<<grid_for(total, 256), 256, 0, s>>>(T.tkeys.get(), T.tvals.get(), total);
+    launch(k_fill_table, grid_for(total, 256), 256, 0, s, T.tkeys.get(), T.tvals.get(), total);
     TP_LAUNCH_CHECK();
   }
   T.built = true;
@@ -422,7 +485,7 @@ static void finish_graph_stats(tp_graph *g, cudaStream_t s) {
   Buf<int64_t> acc(2, s);
   TP_CUDA(cudaMemsetAsync(acc.get(), 0, 2 * sizeof(int64_t), s));
   if (g->n) {
-    k_sum_max<<<grid_for(g->n, 256), 256, 0, s>>>(g->unit_vw ? nullptr : g->vw.get(),
+    launch(k_sum_max, grid_for(g->n, 256), 256, 0, s, g->unit_vw ? nullptr : g->vw.get(),
                                                     g->compressed ? nullptr : g->xadj.get(), g->n,
                                                     acc.get());
     TP_LAUNCH_CHECK();
@@ -448,7 +511,7 @@ tp_graph *compress(const tp_graph *c, cudaStream_t s) {
     int64_t n = c->n;
     Buf<int64_t> off(n + 1, s);
     if (n) {
-      k_zip_size<<<grid_for(n * 32, 256), 256, 0, s>>>(v, off.get());
+      launch(k_zip_size, grid_for(n * 32, 256), 256, 0, s, v, off.get());
       TP_LAUNCH_CHECK();
     }
     exclusive_scan_i64(off.get(), off.get(), n, s);
@@ -459,18 +522,18 @@ tp_graph *compress(const tp_graph *c, cudaStream_t s) {
     z->bytes.alloc(z->nbytes + kBytePad, s);
     TP_CUDA(cudaMemsetAsync(z->bytes.get(), 0, z->nbytes + kBytePad, s));
     if (n) {
-      k_zip_write<<<grid_for(n * 32, 256), 256, 0, s>>>(v, off.get(), z->bytes.get());
+      launch(k_zip_write, grid_for(n * 32, 256), 256, 0, s, v, off.get(), z->bytes.get());
       TP_LAUNCH_CHECK();
     }
-    k_zip_terminal<<<1, 1, 0, s>>>((uint64_t)body, c->m2, z->bytes.get());
+    launch(k_zip_terminal, 1, 1, 0, s, (uint64_t)body, c->m2, z->bytes.get());
     TP_LAUNCH_CHECK();
     z->off_is64 = z->nbytes >= (1ull << 32);
     if (z->off_is64) {
       z->off64.alloc(n + 1, s);
-      k_off_copy<<<grid_for(n + 1, 256), 256, 0, s>>>(off.get(), n + 1, z->off64.get());
+      launch(k_off_copy, grid_for(n + 1, 256), 256, 0, s, off.get(), n + 1, z->off64.get());
     } else {
       z->off32.alloc(n + 1, s);
-      k_off_narrow<<<grid_for(n + 1, 256), 256, 0, s>>>(off.get(), n + 1, z->off32.get());
+      launch(k_off_narrow, grid_for(n + 1, 256), 256, 0, s, off.get(), n + 1, z->off32.get());
     }
     TP_LAUNCH_CHECK();
     z->total_vw = c->total_vw;
@@ -495,7 +558,7 @@ tp_graph *decompress(const tp_graph *z, cudaStream_t s) {
     Buf<int32_t> bad(1, s);
     TP_CUDA(cudaMemsetAsync(bad.get(), 0, sizeof(int32_t), s));
     if (n) {
-      k_zip_header_check<<<grid_for(n, 256), 256, 0, s>>>(v, bad.get());
+      launch(k_zip_header_check, grid_for(n, 256), 256, 0, s, v, bad.get());
       TP_LAUNCH_CHECK();
     }
     TP_REQUIRE(read_scalar(bad.get(), s) == 0, TP_ERR_CORRUPT);
@@ -504,9 +567,10 @@ tp_graph *decompress(const tp_graph *z, cudaStream_t s) {
     exclusive_scan_i64(c->xadj.get(), c->xadj.get(), n, s);
     int64_t m2 = read_scalar(c->xadj.get() + n, s);
     TP_REQUIRE(m2 == z->m2, TP_ERR_CORRUPT);
-    c->adj.alloc(m2, s);
+    c->adj.alloc(m2 + kAdjPad, s);
+    TP_CUDA(cudaMemsetAsync(c->adj.get() + m2, 0, kAdjPad * sizeof(int32_t), s));
     if (n) {
-      k_unzip<<<grid_for(n * 32, 256), 256, 0, s>>>(v, c->xadj.get(), c->adj.get());
+      launch(k_unzip, grid_for(n * 32, 256), 256, 0, s, v, c->xadj.get(), c->adj.get());
       TP_LAUNCH_CHECK();
     }
     int32_t e = read_scalar(z->err.get(), s);
@@ -555,18 +619,18 @@ tp_graph *from_compressed(int64_t n, uint64_t nbytes, const uint8_t *bytes, cons
       z->off64 = std::move(o);
     } else {
       z->off32.alloc(n + 1, s);
-      k_off_narrow_u64<<<grid_for(n + 1, 256), 256, 0, s>>>(o.get(), n + 1, z->off32.get());
+      launch(k_off_narrow_u64, grid_for(n + 1, 256), 256, 0, s, o.get(), n + 1, z->off32.get());
       TP_LAUNCH_CHECK();
     }
     Buf<int64_t> m2(1, s);
-    k_terminal_m2<<<1, 1, 0, s>>>(z->bytes.get(), z->off_is64 ? z->off64.get() : o.get(), n, m2.get());
+    launch(k_terminal_m2, 1, 1, 0, s, z->bytes.get(), z->off_is64 ? z->off64.get() : o.get(), n, m2.get());
     TP_LAUNCH_CHECK();
     z->m2 = read_scalar(m2.get(), s);
     TP_REQUIRE(z->m2 >= 0, TP_ERR_CORRUPT);
     tp_graph *c = decompress(z, s);  // throws TP_ERR_CORRUPT on a malformed stream
     Buf<int32_t> bad(1, s);
     TP_CUDA(cudaMemsetAsync(bad.get(), 0, sizeof(int32_t), s));
-    k_validate<<<grid_for(std::max<int64_t>(n, 1) * 32, 256), 256, 0, s>>>(view(c), bad.get());
+    launch(k_validate, grid_for(std::max<int64_t>(n, 1) * 32, 256), 256, 0, s, view(c), bad.get());
     TP_LAUNCH_CHECK();
     int32_t b = read_scalar(bad.get(), s);
     z->total_vw = n;
@@ -595,7 +659,8 @@ tp_graph *from_csr(int64_t n, const int64_t *xadj, const int32_t *adj, const int
     TP_REQUIRE(m2 >= 0, TP_ERR_INVALID);
     g->m2 = m2;
     TP_REQUIRE(m2 == 0 || adj != nullptr, TP_ERR_INVALID);
-    g->adj.alloc(m2, s);
+    g->adj.alloc(m2 + kAdjPad, s);  // padded: 16-byte loads may run past the last entry
+    TP_CUDA(cudaMemsetAsync(g->adj.get() + m2, 0, kAdjPad * sizeof(int32_t), s));
     if (m2) TP_CUDA(cudaMemcpyAsync(g->adj.get(), adj, m2 * sizeof(int32_t), kind, s));
     g->unit_vw = vwgt == nullptr;
     g->unit_ew = ewgt == nullptr;
@@ -609,7 +674,7 @@ tp_graph *from_csr(int64_t n, const int64_t *xadj, const int32_t *adj, const int
     }
     Buf<int32_t> bad(1, s);
     TP_CUDA(cudaMemsetAsync(bad.get(), 0, sizeof(int32_t), s));
-    k_validate<<<grid_for(std::max<int64_t>(n, 1) * 32, 256), 256, 0, s>>>(view(g), bad.get());
+    launch(k_validate, grid_for(std::max<int64_t>(n, 1) * 32, 256), 256, 0, s, view(g), bad.get());
     TP_LAUNCH_CHECK();
     TP_REQUIRE(read_scalar(bad.get(), s) == 0, TP_ERR_INVALID);
     finish_graph_stats(g, s);
@@ -626,11 +691,11 @@ void export_csr(const tp_graph *g, int64_t *xadj, int32_t *adj, int64_t *vw, int
   if (xadj) TP_CUDA(cudaMemcpyAsync(xadj, g->xadj.get(), (g->n + 1) * 8, cudaMemcpyDeviceToDevice, s));
   if (adj && g->m2) TP_CUDA(cudaMemcpyAsync(adj, g->adj.get(), g->m2 * 4, cudaMemcpyDeviceToDevice, s));
   if (vw && g->n) {
-    if (g->unit_vw) k_ones<<<grid_for(g->n, 256), 256, 0, s>>>(vw, g->n);
+    if (g->unit_vw) launch(k_ones, grid_for(g->n, 256), 256, 0, s, vw, g->n);
     else TP_CUDA(cudaMemcpyAsync(vw, g->vw.get(), g->n * 8, cudaMemcpyDeviceToDevice, s));
   }
   if (ew && g->m2) {
-    if (g->unit_ew) k_ones<<<grid_for(g->m2, 256), 256, 0, s>>>(ew, g->m2);
+    if (g->unit_ew) launch(k_ones, grid_for(g->m2, 256), 256, 0, s, ew, g->m2);
     else TP_CUDA(cudaMemcpyAsync(ew, g->ew.get(), g->m2 * 8, cudaMemcpyDeviceToDevice, s));
   }
   TP_LAUNCH_CHECK();
@@ -643,13 +708,39 @@ void export_compressed(const tp_graph *g, uint8_t *bytes, uint64_t *off, cudaStr
     if (g->off_is64) {
       TP_CUDA(cudaMemcpyAsync(off, g->off64.get(), (g->n + 1) * 8, cudaMemcpyDeviceToDevice, s));
     } else {
-      k_widen<<<grid_for(g->n + 1, 256), 256, 0, s>>>(g->off32.get(), off, g->n + 1);
+      launch(k_widen, grid_for(g->n + 1, 256), 256, 0, s, g->off32.get(), off, g->n + 1);
       TP_LAUNCH_CHECK();
     }
   }
 }
 
 }  // namespace tp
+
+extern "C" uint64_t tp_launch_count(void) { return tp::g_launches.load(); }
+
+extern "C" void tp_profile_enable(int on) {
+  tp::g_prof.enabled = on != 0;
+  if (!on) tp::g_prof.scope = false;
+}
+
+extern "C" int tp_profile_read(tp_profile_entry *out, int max, void *stream) {
+  using namespace tp;
+  for (int f = 0; f < max && f < PF_COUNT; ++f) out[f] = tp_profile_entry{f, 0, 0.0, 0.0};
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return -1;
+  for (const ProfRecord &r : g_prof.recs) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    if (r.family < max) {
+      out[r.family].launches += 1;
+      out[r.family].ms += ms;
+      out[r.family].bytes += r.bytes;
+    }
+    g_prof.pool.push_back(r.a);
+    g_prof.pool.push_back(r.b);
+  }
+  g_prof.recs.clear();
+  return PF_COUNT < max ? PF_COUNT : max;
+}
 
 extern "C" tp_status tp_set_allocator(void *(*alloc)(size_t, void *, void *),
                                       void (*free_fn)(void *, size_t, void *, void *), void *ctx) {

@@ -355,12 +355,12 @@ void initial_partition(const tp_graph *g, int32_t k, int64_t l_max, const tp_par
   TP_REQUIRE(!g->compressed, TP_ERR_INVALID);
   const int64_t n = g->n;
   if (n == 0) return;
-  k_fill_i32<<<grid_for(n, 256), 256, 0, s>>>(d_part, n, 0);
+  launch(k_fill_i32, grid_for(n, 256), 256, 0, s, d_part, n, 0);
   TP_LAUNCH_CHECK();
   if (k <= 1) return;
   const int32_t T = std::max(1, p.ip_attempts);
   Buf<int32_t> node_of(n, s), next_node(n, s), vlist(n, s), loc(n, s);
-  k_fill_i32<<<grid_for(n, 256), 256, 0, s>>>(node_of.get(), n, 0);
+  launch(k_fill_i32, grid_for(n, 256), 256, 0, s, node_of.get(), n, 0);
   Buf<int32_t> ord(T * n, s), disc(T * n, s), claimer(T * n, s), cnt(T * n, s), side(T * n, s),
       mvx0(T * n, s), mvx1(T * n, s), ok0(T * n, s), ok1(T * n, s);
   Buf<int64_t> mvg0(T * n, s), mvg1(T * n, s);
@@ -371,13 +371,13 @@ void initial_partition(const tp_graph *g, int32_t k, int64_t l_max, const tp_par
     // vertex lists per node
     Buf<int64_t> nstart(nodes + 1, s);
     TP_CUDA(cudaMemsetAsync(nstart.get(), 0, (nodes + 1) * sizeof(int64_t), s));
-    k_node_keys<<<grid_for(n, 256), 256, 0, s>>>(node_of.get(), n, keys.get(), nstart.get());
+    launch(k_node_keys, grid_for(n, 256), 256, 0, s, node_of.get(), n, keys.get(), nstart.get());
     TP_LAUNCH_CHECK();
     radix_sort_pairs(keys.get(), nullptr, n, 64, s);
     exclusive_scan_i64(nstart.get(), nstart.get(), nodes, s);
     int64_t m = read_scalar(nstart.get() + nodes, s);
     if (m) {
-      k_node_lists<<<grid_for(m, 256), 256, 0, s>>>(keys.get(), nstart.get(), m, vlist.get(), loc.get());
+      launch(k_node_lists, grid_for(m, 256), 256, 0, s, keys.get(), nstart.get(), m, vlist.get(), loc.get());
       TP_LAUNCH_CHECK();
     }
     // children of every node at the next depth (-1: leaf, assign the block)
@@ -416,10 +416,10 @@ void initial_partition(const tp_graph *g, int32_t k, int64_t l_max, const tp_par
     c.ok1 = ok1.get();
     c.mvg0 = mvg0.get(), c.mvg1 = mvg1.get();
     c.cut = cut.get();
-    k_bisect<<<(unsigned)(nodes * T), kIPThreads, 0, s>>>(c);
+    launch(k_bisect, (unsigned)(nodes * T), kIPThreads, 0, s, c);
     TP_LAUNCH_CHECK();
-    k_fill_i32<<<grid_for(n, 256), 256, 0, s>>>(next_node.get(), n, -1);
-    k_pick<<<(unsigned)nodes, 256, 0, s>>>(c, d_c0.get(), d_c1.get(), next_node.get(), d_part);
+    launch(k_fill_i32, grid_for(n, 256), 256, 0, s, next_node.get(), n, -1);
+    launch(k_pick, (unsigned)nodes, 256, 0, s, c, d_c0.get(), d_c1.get(), next_node.get(), d_part);
     TP_LAUNCH_CHECK();
     std::swap(node_of, next_node);
     TP_CUDA(cudaStreamSynchronize(s));  // host vectors above outlive their copies

@@ -50,7 +50,6 @@ struct RateCtx {
   int32_t *mv_u, *mv_t;
   int64_t *mv_g;
   int64_t *in_w;
-  int32_t *in_cnt;
   unsigned long long *counters;
   // M_FAV output
   int32_t *fav;
@@ -167,7 +166,6 @@ __device__ __forceinline__ void finalize_warp(const RateCtx &c, const Best &b, i
         mb->t[mb->cnt] = b.x;
         mb->gain[mb->cnt] = b.r - b.rown;
         atomicAdd((unsigned long long *)&c.in_w[b.x], (unsigned long long)cu);
-        atomicAdd(&c.in_cnt[b.x], 1);
       }
       if (++mb->cnt == 32) flush_movers(c, *mb);
     }
@@ -265,7 +263,9 @@ __device__ __forceinline__ void init_table(WarpSmem<LOG> &w) {
   __syncwarp();
 }
 
-// Small tier: every vertex, filtered by tier and predicate in 32-vertex slabs.
+// Small tier: one warp per listed vertex (c.list), or, in rebalancing mode
+// (c.list == nullptr), every vertex of the small and lane tiers, filtered in
+// 32-vertex slabs.
 template <bool COMP, int MODE>
 __global__ void k_rate_small(RateCtx c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -274,17 +274,266 @@ __global__ void k_rate_small(RateCtx c) {
   MoverBuf mb{ws.mu, ws.mt, ws.mg, 0};
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = gw * 32; base < c.g.n; base += nw * 32) {
-    int64_t u = base + lane_id();
-    bool act = u < c.g.n && c.tier[u] == TIER_SMALL && active<MODE>(c, u);
-    unsigned am = __ballot_sync(kFull, act);
-    while (am) {
-      int j = __ffs(am) - 1;
-      am &= am - 1;
-      rate_vertex_warp<COMP, MODE>(c, base + j, ws.keys, ws.vals, kSmallLog, true, &mb);
+  if (c.list) {
+    for (int64_t i0 = gw * 32; i0 < c.list_n; i0 += nw * 32) {
+      int64_t i = i0 + lane_id();
+      int64_t u = i < c.list_n ? c.list[i] : 0;
+      unsigned am = __ballot_sync(kFull, i < c.list_n && active<MODE>(c, u));
+      while (am) {
+        int j = __ffs(am) - 1;
+        am &= am - 1;
+        rate_vertex_warp<COMP, MODE>(c, __shfl_sync(kFull, u, j), ws.keys, ws.vals, kSmallLog,
+                                     true, &mb);
+      }
+    }
+  } else {
+    for (int64_t base = gw * 32; base < c.g.n; base += nw * 32) {
+      int64_t u = base + lane_id();
+      bool act = u < c.g.n && (c.tier[u] == TIER_SMALL || c.tier[u] == TIER_LANE) &&
+                 active<MODE>(c, u);
+      unsigned am = __ballot_sync(kFull, act);
+      while (am) {
+        int j = __ffs(am) - 1;
+        am &= am - 1;
+        rate_vertex_warp<COMP, MODE>(c, base + j, ws.keys, ws.vals, kSmallLog, true, &mb);
+      }
     }
   }
   if (MODE == M_LP) flush_movers(c, mb);
+}
+
+// ---------------------------------------------------------------- lane tier
+// Low-degree vertices of unit-edge-weight graphs, one lane per vertex, so a
+// warp keeps 32 neighbourhoods in flight:
+//   1. the active vertices of a 256-vertex slab are compacted onto lanes;
+//   2. each lane loads its offsets, then its whole record with 16-byte
+//      loads, and decodes header, first neighbour and gaps in registers
+//      (CSR: the adjacency words directly) into a per-lane column of shared
+//      memory;
+//   3. label gathers for all neighbours are issued back to back;
+//   4. the labels are sorted in registers (bitonic network of 32) so equal
+//      labels form runs whose lengths are the ratings (unit edge weights);
+//   5. runs are scanned for the own rating and the two best candidates by
+//      the rating order; the cap is checked lazily (a label-weight gather only
+//      for the winner, falling back to a full feasible scan if both top
+//      candidates are full).
+constexpr int kLaneWarps = 8;
+
+struct LaneCand {
+  int32_t r;
+  uint32_t t;
+  int32_t x;
+};
+
+__device__ __forceinline__ bool lane_better(const LaneCand &a, const LaneCand &b) {
+  return better(a.r, a.t, a.x, b.r, b.t, b.x);
+}
+
+// Decodes the record of u into col[i * 32] (compressed); returns the degree.
+// A rolled loop over aligned 32-bit words keeps the code small; the stream
+// and offsets are read with evict-first loads so label arrays stay in L2.
+// Streams are validated when a graph is created, so the hot loop only
+// clamps ids into [0, n) to keep every later access in bounds.
+__device__ __forceinline__ int lane_decode_zip(const GView &g, int64_t u, int32_t *col) {
+  const uint64_t b = g.off32 ? (uint64_t)__ldcs(g.off32 + u) : __ldcs(g.off64 + u);
+  const uint64_t e = g.off32 ? (uint64_t)__ldcs(g.off32 + u + 1) : __ldcs(g.off64 + u + 1);
+  const int32_t nmax = (int32_t)(g.n - 1);
+  const uint32_t *wp = reinterpret_cast<const uint32_t *>(g.bytes + (b & ~(uint64_t)3));
+  uint32_t word = __ldcs(wp) >> (8 * (b & 3));
+  uint32_t nextw = __ldcs(wp + 1);
+  int left = 4 - (int)(b & 3);  // bytes still unread in `word`
+  int remaining = (int)(e - b);
+  // header (first edge id): skip to its last byte
+  while (remaining > 0) {
+    uint32_t byte = word & 255u;
+    word >>= 8;
+    --remaining;
+    if (--left == 0) word = nextw, nextw = __ldcs(++wp + 1), left = 4;
+    if (!(byte & 0x80u)) break;
+  }
+  uint32_t val = 0;
+  int shift = 0, cntv = 0;
+  int32_t prev = (int32_t)u;
+  bool first = true;
+  while (remaining > 0) {
+    uint32_t byte = word & 255u;
+    word >>= 8;
+    --remaining;
+    if (--left == 0) word = nextw, nextw = __ldcs(++wp + 1), left = 4;
+    val |= (byte & 0x7fu) << shift;
+    shift += 7;
+    if (byte & 0x80u) continue;
+    int32_t v = first ? ((val & 1u) ? prev - (int32_t)(val >> 1) : prev + (int32_t)(val >> 1))
+                      : prev + (int32_t)val;
+    v = min(max(v, 0), nmax);
+    first = false;
+    prev = v;
+    col[min(cntv, kLaneMaxDeg - 1) * 32] = v;
+    ++cntv;
+    val = 0;
+    shift = 0;
+  }
+  return min(cntv, kLaneMaxDeg);
+}
+
+// Loads the adjacency of u into col[i * 32] (CSR); returns the degree.
+__device__ __forceinline__ int lane_load_csr(const GView &g, int64_t u, int32_t *col) {
+  const int64_t b = __ldcs(g.xadj + u), e = __ldcs(g.xadj + u + 1);
+#pragma unroll 4
+  for (int64_t k = b; k < e; ++k) col[(k - b) * 32] = __ldcs(g.adj + k);
+  return (int)(e - b);
+}
+
+// Sorts a[0..N) ascending with a bitonic network (registers only).
+template <int N>
+__device__ __forceinline__ void bitonic_sort(int32_t (&a)[kLaneMaxDeg]) {
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+    for (int jd = k >> 1; jd > 0; jd >>= 1) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int l = i ^ jd;
+        if (l > i) {
+          const int32_t lo = min(a[i], a[l]), hi = max(a[i], a[l]);
+          if ((i & k) == 0) a[i] = lo, a[l] = hi;
+          else a[i] = hi, a[l] = lo;
+        }
+      }
+    }
+  }
+}
+
+// Sorted labels -> (label, run length) pairs compacted to the front of the
+// column; returns the number of distinct labels (padding excluded).
+template <int N>
+__device__ __forceinline__ int runs_to_column(const int32_t (&a)[kLaneMaxDeg], int32_t *col,
+                                              uint8_t *cnt) {
+  int k = 0, run = 1;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const bool last = i + 1 == N || a[i + 1] != a[i];
+    if (last && a[i] != INT32_MAX) {
+      col[k * 32] = a[i];
+      cnt[k * 32] = (uint8_t)run;
+      ++k;
+    }
+    run = last ? 1 : run + 1;
+  }
+  return k;
+}
+
+template <bool COMP, int MODE>
+__global__ void __launch_bounds__(kLaneWarps * 32) k_rate_lane(RateCtx c) {
+  __shared__ int32_t lab_all[kLaneWarps][kLaneMaxDeg][32];
+  __shared__ uint8_t cnt_all[kLaneWarps][kLaneMaxDeg][32];
+  __shared__ int32_t queue_all[kLaneWarps][64];
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  int32_t *col = &lab_all[w][0][lane];
+  uint8_t *cnt = &cnt_all[w][0][lane];
+  int32_t *queue = queue_all[w];
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int pending = 0;  // active vertices queued for this warp (warp-uniform)
+  int64_t base = gw * 256;
+  int j = 0;
+  for (;;) {
+    // fill the queue, 32 vertices of the current 256-vertex slab at a time
+    while (pending < 32 && base < c.g.n) {
+      int64_t v = base + 32 * j + lane;
+      bool act = v < c.g.n && c.tier[v] == TIER_LANE && active<MODE>(c, v);
+      unsigned m = __ballot_sync(kFull, act);
+      if (act) queue[pending + __popc(m & lanemask_lt())] = (int32_t)v;
+      pending += __popc(m);
+      if (++j == 8) j = 0, base += nw * 256;
+    }
+    if (pending == 0) break;
+    __syncwarp();
+    // one batch: up to 32 queued vertices, one per lane
+    const int take = pending < 32 ? pending : 32;
+    const bool has = lane < take;
+    const int64_t u = has ? queue[lane] : 0;
+    __syncwarp();
+    if (pending > 32 && lane < pending - 32) queue[lane] = queue[32 + lane];
+    __syncwarp();
+    pending -= take;
+    int deg = 0;
+    if (has) deg = COMP ? lane_decode_zip(c.g, u, col) : lane_load_csr(c.g, u, col);
+    // label gathers, independent loads
+#pragma unroll 4
+    for (int i = 0; i < deg; ++i) col[i * 32] = __ldg(c.label + col[i * 32]);
+    // ratings: sort the labels; runs of equal labels are the ratings
+    int32_t a[kLaneMaxDeg];
+    int ncand;
+    const int maxdeg = __reduce_max_sync(kFull, (unsigned)deg);
+    if (maxdeg <= 16) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) a[i] = i < deg ? col[i * 32] : INT32_MAX;
+      bitonic_sort<16>(a);
+      ncand = runs_to_column<16>(a, col, cnt);
+    } else {
+#pragma unroll
+      for (int i = 0; i < kLaneMaxDeg; ++i) a[i] = i < deg ? col[i * 32] : INT32_MAX;
+      bitonic_sort<kLaneMaxDeg>(a);
+      ncand = runs_to_column<kLaneMaxDeg>(a, col, cnt);
+    }
+    // own rating and the two best candidates
+    const int32_t own = has ? c.label[u] : -1;
+    const int64_t cu = has ? node_w(c.g, u) : 1;
+    const uint64_t hv = has ? tie_key<MODE>(c, u) : 0;
+    LaneCand b1{-1, 0xffffffffu, INT32_MAX}, b2{-1, 0xffffffffu, INT32_MAX};
+    int32_t rown = 0;
+    for (int k = 0; k < ncand; ++k) {
+      const int32_t x = col[k * 32];
+      const int r = cnt[k * 32];
+      if (x == own) {
+        rown = r;
+        continue;
+      }
+      if (r < b2.r) continue;  // cannot enter the top two
+      LaneCand cand{r, tie_hash(hv, x), x};
+      if (lane_better(cand, b1)) b2 = b1, b1 = cand;
+      else if (lane_better(cand, b2)) b2 = cand;
+    }
+    // lazy cap check
+    LaneCand best{-1, 0xffffffffu, INT32_MAX};
+    if (MODE == M_FAV) {
+      best = b1;
+    } else if (b1.r > 0) {
+      if (c.lw[b1.x] + cu <= c.cap) {
+        best = b1;
+      } else if (b2.r > 0 && c.lw[b2.x] + cu <= c.cap) {
+        best = b2;
+      } else if (b2.r > 0) {
+        // both leaders are full: the best admissible among the rest
+        for (int k = 0; k < ncand; ++k) {
+          const int32_t x = col[k * 32];
+          if (x == own || x == b1.x || x == b2.x) continue;
+          LaneCand cand{cnt[k * 32], tie_hash(hv, x), x};
+          if (lane_better(cand, best) && c.lw[x] + cu <= c.cap) best = cand;
+        }
+      }
+    }
+    if (MODE == M_FAV) {
+      if (has) c.fav[u] = best.r > 0 ? best.x : (int32_t)c.g.n;
+    } else {
+      bool mv = has && best.r > rown;
+      unsigned mm = __ballot_sync(kFull, mv);
+      if (mm) {
+        unsigned long long basep = 0;
+        if (lane == 0) basep = atomicAdd(c.counters, (unsigned long long)__popc(mm));
+        basep = __shfl_sync(kFull, basep, 0);
+        if (mv) {
+          unsigned long long at = basep + __popc(mm & lanemask_lt());
+          c.mv_u[at] = (int32_t)u;
+          c.mv_t[at] = best.x;
+          c.mv_g[at] = best.r - rown;
+          atomicAdd((unsigned long long *)&c.in_w[best.x], (unsigned long long)cu);
+        }
+      }
+    }
+    __syncwarp();
+  }
 }
 
 // Mid tier (shared table) and big tier (global table): one warp per listed vertex.
@@ -407,7 +656,7 @@ struct ApproveCtx {
   const int64_t *mv_g;
   int8_t *mv_ok;
   int64_t *in_w;
-  int32_t *in_cnt, *cstate, *cfill, *cseg, *ctarget;
+  int32_t *ccnt, *cfill, *cseg, *ctarget;
   int64_t *cbase;
   unsigned long long *counters;  // [0] movers [1] contested targets [2] contested pool
   int32_t *label;
@@ -418,7 +667,8 @@ struct ApproveCtx {
 
 __device__ __forceinline__ int64_t vwt(const ApproveCtx &a, int64_t u) { return a.vw ? a.vw[u] : 1; }
 
-// A: targets that fit take every mover; the others become contested.
+// A: targets that fit take every mover; the others become contested and
+// count their movers (the first one also lists the target).
 __global__ void k_approve_fit(ApproveCtx a) {
   int64_t nm = (int64_t)a.counters[0];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nm;
@@ -426,11 +676,20 @@ __global__ void k_approve_fit(ApproveCtx a) {
     int32_t t = a.mv_t[i];
     bool fits = a.lw[t] + a.in_w[t] <= a.cap;
     a.mv_ok[i] = fits;
-    if (!fits && atomicCAS(&a.cstate[t], 0, 1) == 0) {
+    if (!fits && atomicAdd(&a.ccnt[t], 1) == 0) {
       unsigned long long j = atomicAdd(&a.counters[1], 1ull);
       a.ctarget[j] = t;
-      a.cbase[t] = (int64_t)atomicAdd(&a.counters[2], (unsigned long long)a.in_cnt[t]);
     }
+  }
+}
+
+// A2: every contested target reserves its segment of the contested list.
+__global__ void k_approve_alloc(ApproveCtx a) {
+  int64_t nt = (int64_t)a.counters[1];
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nt;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    int32_t t = a.ctarget[j];
+    a.cbase[t] = (int64_t)atomicAdd(&a.counters[2], (unsigned long long)a.ccnt[t]);
   }
 }
 
@@ -500,8 +759,10 @@ __global__ void k_approve_contested(ApproveCtx a) {
   int64_t nt = (int64_t)a.counters[1];
   for (int64_t j = blockIdx.x; j < nt; j += gridDim.x) {
     int32_t t = a.ctarget[j];
-    int64_t base = a.cbase[t], cnt = a.in_cnt[t];
+    int64_t base = a.cbase[t], cnt = a.ccnt[t];
     int64_t rem = a.cap - a.lw[t];
+    __syncthreads();  // every thread has read ccnt before it is reset below
+    if (threadIdx.x == 0) a.ccnt[t] = 0, a.cfill[t] = 0;
     auto item = [&](int64_t q, uint64_t &hi, uint32_t &lo, int64_t &w) {
       int32_t i = a.cseg[base + q];
       hi = ~(uint64_t)a.mv_g[i];
@@ -537,9 +798,6 @@ __global__ void k_apply(ApproveCtx a) {
       atomicAdd((unsigned long long *)&a.lw[own], (unsigned long long)(-w));
     }
     a.in_w[t] = 0;
-    a.in_cnt[t] = 0;
-    a.cstate[t] = 0;
-    a.cfill[t] = 0;
   }
 }
 
@@ -552,6 +810,18 @@ __global__ void k_init_singletons(const int64_t *vw, int64_t n, int32_t *label, 
 }
 
 // ---------------------------------------------------------------- tier dispatch
+// Algorithmic bytes one round of rating must move for the vertices of one
+// tier (level 0, unit weights): the tier's share of the adjacency stream and
+// its offsets, one 4-byte label gather per adjacency entry, the own label
+// and one 8-byte label-weight read per vertex.
+double tier_round_bytes(const tp_graph *g, int64_t n_t, int64_t e_t) {
+  double adj = g->compressed
+                   ? (double)g->nbytes * (g->m2 ? (double)e_t / (double)g->m2 : 0.0) +
+                         (double)n_t * (g->off_is64 ? 8.0 : 4.0)
+                   : 4.0 * (double)e_t + 8.0 * (double)n_t;
+  return adj + 4.0 * (double)e_t + 12.0 * (double)n_t;
+}
+
 template <int MODE>
 void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
   build_tiers(g, p, s);
@@ -562,26 +832,52 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
   c.tvals = T.tvals.get();
   const int sms = num_sms();
   const bool comp = g->compressed;
-  int64_t n_small = g->n - T.n_mid - T.n_big - T.n_huge;
+  const bool prof = MODE == M_LP && prof_active();
+  const double per_launch = MODE == M_LP && c.S > 0 ? 1.0 / c.S : 0.0;
+  const int64_t n_lane = MODE == M_REBAL ? 0 : T.count[TIER_LANE];
+  const int64_t n_small = T.count[TIER_SMALL] + (MODE == M_REBAL ? T.count[TIER_LANE] : 0);
+  if (n_lane > 0) {
+    if (prof) prof_begin(PF_RATE_LANE, s);
+    unsigned blocks = (unsigned)std::min<int64_t>((g->n + 256 * kLaneWarps - 1) / (256 * kLaneWarps),
+                                                  (int64_t)sms * 8);
+    if (comp) launch(k_rate_lane<true, MODE == M_REBAL ? M_LP : MODE>, blocks, 32 * kLaneWarps, 0, s, c);
+    else launch(k_rate_lane<false, MODE == M_REBAL ? M_LP : MODE>, blocks, 32 * kLaneWarps, 0, s, c);
+    TP_LAUNCH_CHECK();
+    if (prof) prof_end(PF_RATE_LANE, s, per_launch * tier_round_bytes(g, n_lane, T.edges[TIER_LANE]));
+  }
   if (n_small > 0) {
+    if (prof) prof_begin(PF_RATE_SMALL, s);
     int wpb = p.warps_per_block >= 1 && p.warps_per_block <= 16 ? p.warps_per_block : 8;
     size_t sm = sizeof(WarpSmem<kSmallLog>) * wpb;
-    unsigned blocks = (unsigned)std::min<int64_t>((g->n + 32 * wpb - 1) / (32 * wpb), (int64_t)sms * 16);
-    if (comp) k_rate_small<true, MODE><<<blocks, 32 * wpb, sm, s>>>(c);
-    else k_rate_small<false, MODE><<<blocks, 32 * wpb, sm, s>>>(c);
+    RateCtx m = c;
+    int64_t items = g->n;
+    if (MODE != M_REBAL) {
+      m.list = T.small.get();
+      m.list_n = T.n_small;
+      items = T.n_small;
+    } else {
+      m.list = nullptr;
+    }
+    unsigned blocks = (unsigned)std::min<int64_t>((items + 32 * wpb - 1) / (32 * wpb), (int64_t)sms * 16);
+    if (comp) launch(k_rate_small<true, MODE>, blocks, 32 * wpb, sm, s, m);
+    else launch(k_rate_small<false, MODE>, blocks, 32 * wpb, sm, s, m);
     TP_LAUNCH_CHECK();
+    if (prof) prof_end(PF_RATE_SMALL, s, per_launch * tier_round_bytes(g, T.count[TIER_SMALL], T.edges[TIER_SMALL]));
   }
   if (T.n_mid > 0) {
+    if (prof) prof_begin(PF_RATE_MID, s);
     RateCtx m = c;
     m.list = T.mid.get();
     m.list_n = T.n_mid;
     size_t sm = sizeof(WarpSmem<kMidLog>) * kMidWarps;
     unsigned blocks = (unsigned)std::min<int64_t>((T.n_mid + kMidWarps - 1) / kMidWarps, (int64_t)sms * 8);
-    if (comp) k_rate_list<true, MODE, false><<<blocks, 32 * kMidWarps, sm, s>>>(m);
-    else k_rate_list<false, MODE, false><<<blocks, 32 * kMidWarps, sm, s>>>(m);
+    if (comp) launch(k_rate_list<true, MODE, false>, blocks, 32 * kMidWarps, sm, s, m);
+    else launch(k_rate_list<false, MODE, false>, blocks, 32 * kMidWarps, sm, s, m);
     TP_LAUNCH_CHECK();
+    if (prof) prof_end(PF_RATE_MID, s, per_launch * tier_round_bytes(g, T.n_mid, T.edges[TIER_MID]));
   }
   if (T.n_big > 0) {
+    if (prof) prof_begin(PF_RATE_BIG, s);
     RateCtx m = c;
     m.list = T.big.get();
     m.list_n = T.n_big;
@@ -589,11 +885,13 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
     m.tcap = T.big_tcap.get();
     m.tbase = 0;
     unsigned blocks = (unsigned)std::min<int64_t>((T.n_big + kMidWarps - 1) / kMidWarps, (int64_t)sms * 16);
-    if (comp) k_rate_list<true, MODE, true><<<blocks, 32 * kMidWarps, 0, s>>>(m);
-    else k_rate_list<false, MODE, true><<<blocks, 32 * kMidWarps, 0, s>>>(m);
+    if (comp) launch(k_rate_list<true, MODE, true>, blocks, 32 * kMidWarps, 0, s, m);
+    else launch(k_rate_list<false, MODE, true>, blocks, 32 * kMidWarps, 0, s, m);
     TP_LAUNCH_CHECK();
+    if (prof) prof_end(PF_RATE_BIG, s, per_launch * tier_round_bytes(g, T.n_big, T.edges[TIER_BIG]));
   }
   if (T.n_huge > 0) {
+    if (prof) prof_begin(PF_RATE_HUGE, s);
     RateCtx m = c;
     m.list = T.huge.get();
     m.list_n = T.n_huge;
@@ -604,12 +902,13 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
     m.n_chunks = T.n_huge_chunks;
     size_t sm = sizeof(WarpSmem<kMidLog>) * kHugeWarps;
     unsigned blocks = (unsigned)std::min<int64_t>((T.n_huge_chunks + kHugeWarps - 1) / kHugeWarps, (int64_t)sms * 8);
-    if (comp) k_rate_huge_chunks<true, MODE><<<blocks, 32 * kHugeWarps, sm, s>>>(m);
-    else k_rate_huge_chunks<false, MODE><<<blocks, 32 * kHugeWarps, sm, s>>>(m);
+    if (comp) launch(k_rate_huge_chunks<true, MODE>, blocks, 32 * kHugeWarps, sm, s, m);
+    else launch(k_rate_huge_chunks<false, MODE>, blocks, 32 * kHugeWarps, sm, s, m);
     TP_LAUNCH_CHECK();
     unsigned db = (unsigned)std::min<int64_t>(T.n_huge, (int64_t)sms * 4);
-    k_rate_huge_decide<MODE><<<db, kDecideThreads, 0, s>>>(m);
+    launch(k_rate_huge_decide<MODE>, db, kDecideThreads, 0, s, m);
     TP_LAUNCH_CHECK();
+    if (prof) prof_end(PF_RATE_HUGE, s, per_launch * tier_round_bytes(g, T.n_huge, T.edges[TIER_HUGE]));
   }
 }
 
@@ -645,8 +944,7 @@ ApproveCtx approve_ctx(tp_graph *g, const LpState &st, LpWork &w) {
   a.mv_g = w.mv_g.get();
   a.mv_ok = w.mv_ok.get();
   a.in_w = w.in_w.get();
-  a.in_cnt = w.in_cnt.get();
-  a.cstate = w.cstate.get();
+  a.ccnt = w.ccnt.get();
   a.cfill = w.cfill.get();
   a.cseg = w.cseg.get();
   a.ctarget = w.ctarget.get();
@@ -667,8 +965,7 @@ void LpWork::init(int64_t n_vertices, int64_t n_labels, cudaStream_t s) {
   nlabels = std::max(nlabels, n_labels);
   size_t L = (size_t)std::max<int64_t>(nlabels, 1), N = (size_t)std::max<int64_t>(n, 1);
   in_w.alloc(L, s);
-  in_cnt.alloc(L, s);
-  cstate.alloc(L, s);
+  ccnt.alloc(L, s);
   cfill.alloc(L, s);
   cbase.alloc(L, s);
   ctarget.alloc(L, s);
@@ -679,8 +976,7 @@ void LpWork::init(int64_t n_vertices, int64_t n_labels, cudaStream_t s) {
   cseg.alloc(N, s);
   counters.alloc(4, s);
   TP_CUDA(cudaMemsetAsync(in_w.get(), 0, L * 8, s));
-  TP_CUDA(cudaMemsetAsync(in_cnt.get(), 0, L * 4, s));
-  TP_CUDA(cudaMemsetAsync(cstate.get(), 0, L * 4, s));
+  TP_CUDA(cudaMemsetAsync(ccnt.get(), 0, L * 4, s));
   TP_CUDA(cudaMemsetAsync(cfill.get(), 0, L * 4, s));
   TP_CUDA(cudaMemsetAsync(counters.get(), 0, 4 * 8, s));
 }
@@ -699,17 +995,19 @@ void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t
   c.mv_t = w.mv_t.get();
   c.mv_g = w.mv_g.get();
   c.in_w = w.in_w.get();
-  c.in_cnt = w.in_cnt.get();
   c.counters = (unsigned long long *)w.counters.get();
   rate_tiers<M_LP>(g, c, p, stream);
   ApproveCtx a = approve_ctx(g, st, w);
   const unsigned blocks = (unsigned)num_sms() * 4;
-  k_approve_fit<<<blocks, 256, 0, stream>>>(a);
-  k_approve_scatter<<<blocks, 256, 0, stream>>>(a);
-  k_approve_contested<<<(unsigned)num_sms() * 2, 256, 0, stream>>>(a);
-  k_apply<<<blocks, 256, 0, stream>>>(a);
+  prof_begin(PF_APPROVE, stream);
+  launch(k_approve_fit, blocks, 256, 0, stream, a);
+  launch(k_approve_alloc, (unsigned)num_sms(), 256, 0, stream, a);
+  launch(k_approve_scatter, blocks, 256, 0, stream, a);
+  launch(k_approve_contested, (unsigned)num_sms() * 2, 256, 0, stream, a);
+  launch(k_apply, blocks, 256, 0, stream, a);
   TP_LAUNCH_CHECK();
   TP_CUDA(cudaMemsetAsync(w.counters.get(), 0, 4 * sizeof(int64_t), stream));
+  prof_end(PF_APPROVE, stream, 0.0);
 }
 
 void lp_rounds(tp_graph *g, const LpState &st, LpWork &w, uint64_t seed, uint64_t tag, uint64_t a,
@@ -791,7 +1089,7 @@ __global__ void k_th_assign(const int64_t *head_raw, const int64_t *head_scan,
 void favourites(tp_graph *g, const int32_t *C, const int64_t *Wc, uint64_t rk, int32_t *fav,
                 const tp_params &p, cudaStream_t s) {
   configure_kernels();
-  k_fav_init<<<grid_for(g->n, 256), 256, 0, s>>>(fav, g->n);
+  launch(k_fav_init, grid_for(g->n, 256), 256, 0, s, fav, g->n);
   TP_LAUNCH_CHECK();
   RateCtx c{};
   c.label = C;
@@ -807,43 +1105,47 @@ void two_hop(tp_graph *g, int32_t *C, const int64_t *Wc, int64_t U, uint64_t see
   if (n == 0) return;
   Buf<int32_t> fav(n, s), flag(n, s);
   favourites(g, C, Wc, round_key(seed, kTagTwoHop, (uint64_t)level, 0), fav.get(), p, s);
-  k_th_flags<<<grid_for(n, 256), 256, 0, s>>>(fav.get(), n, flag.get());
+  launch(k_th_flags, grid_for(n, 256), 256, 0, s, fav.get(), n, flag.get());
   TP_LAUNCH_CHECK();
   Buf<int64_t> pos(n + 1, s);
   exclusive_scan_i32_to_i64(flag.get(), pos.get(), n, s);
   int64_t m = read_scalar(pos.get() + n, s);
   if (m == 0) return;
   Buf<uint64_t> keys(m, s), vals(m, s);
-  k_th_gather<<<grid_for(n, 256), 256, 0, s>>>(fav.get(), flag.get(), pos.get(), n, keys.get(),
+  launch(k_th_gather, grid_for(n, 256), 256, 0, s, fav.get(), flag.get(), pos.get(), n, keys.get(),
                                                  vals.get());
   TP_LAUNCH_CHECK();
   radix_sort_pairs(keys.get(), vals.get(), m, bits_for((uint64_t)n), s);
   Buf<int64_t> wt(m, s), rs(m, s), excl(m + 1, s), head(m, s), hs(m, s);
-  k_th_prep<<<grid_for(m, 256), 256, 0, s>>>(keys.get(), vals.get(),
+  launch(k_th_prep, grid_for(m, 256), 256, 0, s, keys.get(), vals.get(),
                                                g->unit_vw ? nullptr : g->vw.get(), m, wt.get(),
                                                rs.get());
   TP_LAUNCH_CHECK();
   inclusive_max_scan_i64(rs.get(), rs.get(), m, s);
   exclusive_scan_i64(wt.get(), excl.get(), m, s);
-  k_th_heads<<<grid_for(m, 256), 256, 0, s>>>(excl.get(), rs.get(), wt.get(), m, U, head.get());
+  launch(k_th_heads, grid_for(m, 256), 256, 0, s, excl.get(), rs.get(), wt.get(), m, U, head.get());
   TP_LAUNCH_CHECK();
   inclusive_max_scan_i64(head.get(), hs.get(), m, s);
-  k_th_assign<<<grid_for(m, 256), 256, 0, s>>>(head.get(), hs.get(), vals.get(), m, C);
+  launch(k_th_assign, grid_for(m, 256), 256, 0, s, head.get(), hs.get(), vals.get(), m, C);
   TP_LAUNCH_CHECK();
 }
 
 void lp_cluster(tp_graph *g, int64_t U, const tp_params &p, int32_t level, int32_t *d_cluster,
-                cudaStream_t s) {
+                cudaStream_t s, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
   int64_t n = g->n;
   if (n == 0) return;
   Buf<int64_t> Wc(n, s);
-  k_init_singletons<<<grid_for(n, 256), 256, 0, s>>>(g->unit_vw ? nullptr : g->vw.get(), n,
+  launch(k_init_singletons, grid_for(n, 256), 256, 0, s, g->unit_vw ? nullptr : g->vw.get(), n,
                                                        d_cluster, Wc.get());
   TP_LAUNCH_CHECK();
   LpWork w;
   w.init(n, n, s);
   LpState st{d_cluster, Wc.get(), n, U};
+  prof_scope(level == 0);
+  if (ev_begin) TP_CUDA(cudaEventRecord(ev_begin, s));
   lp_rounds(g, st, w, p.seed, kTagCluster, (uint64_t)level, 0, p.cluster_rounds, p.sub_rounds, p, s);
+  if (ev_end) TP_CUDA(cudaEventRecord(ev_end, s));
+  prof_scope(false);
   if (p.two_hop) two_hop(g, d_cluster, Wc.get(), U, p.seed, level, p, s);
 }
 
@@ -899,7 +1201,7 @@ void rebalance_moves(tp_graph *g, int32_t k, int64_t l_max, int32_t *d_part, int
   Buf<int64_t> rb_loss(std::max<int64_t>(n, 1), s);
   *balanced = 1;
   for (;;) {
-    k_find_over<<<1, 256, 0, s>>>(d_B, k, l_max, small.get());
+    launch(k_find_over, 1, 256, 0, s, d_B, k, l_max, small.get());
     TP_LAUNCH_CHECK();
     int32_t blk = read_scalar(small.get(), s);
     if (blk < 0) return;
@@ -917,9 +1219,9 @@ void rebalance_moves(tp_graph *g, int32_t k, int64_t l_max, int32_t *d_part, int
     c.rb_t = rb_t.get();
     c.rb_best = best.get();
     rate_tiers<M_REBAL>(g, c, p, s);
-    k_rb_pick<<<grid_for(n, 256), 256, 0, s>>>(d_part, blk, rb_t.get(), rb_loss.get(), best.get(),
+    launch(k_rb_pick, grid_for(n, 256), 256, 0, s, d_part, blk, rb_t.get(), rb_loss.get(), best.get(),
                                                  n, small.get() + 1);
-    k_rb_apply<<<1, 1, 0, s>>>(d_part, d_B, g->unit_vw ? nullptr : g->vw.get(), rb_t.get(),
+    launch(k_rb_apply, 1, 1, 0, s, d_part, d_B, g->unit_vw ? nullptr : g->vw.get(), rb_t.get(),
                                small.get() + 1);
     TP_LAUNCH_CHECK();
     int32_t bu = read_scalar(small.get() + 1, s);

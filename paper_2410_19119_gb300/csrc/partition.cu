@@ -70,8 +70,7 @@ void block_weights(const tp_graph *g, const int32_t *part, int32_t k, int64_t *d
   TP_CUDA(cudaMemsetAsync(d_B, 0, (size_t)k * sizeof(int64_t), s));
   if (g->n == 0) return;
   size_t sm = k <= kHistMax ? (size_t)k * sizeof(int64_t) : 0;
-  k_block_weights<<<grid_for(g->n, 256, num_sms() * 4), 256, sm, s>>>(
-      part, g->unit_vw ? nullptr : g->vw.get(), g->n, k, d_B);
+  launch(k_block_weights, grid_for(g->n, 256, num_sms() * 4), 256, sm, s, part, g->unit_vw ? nullptr : g->vw.get(), g->n, k, d_B);
   TP_LAUNCH_CHECK();
 }
 
@@ -80,8 +79,8 @@ int64_t edge_cut(const tp_graph *g, const int32_t *part, cudaStream_t s) {
   TP_CUDA(cudaMemsetAsync(acc.get(), 0, sizeof(unsigned long long), s));
   if (g->n) {
     unsigned b = grid_for(g->n * 32, 256);
-    if (g->compressed) k_cut<true><<<b, 256, 0, s>>>(view(g), part, acc.get());
-    else k_cut<false><<<b, 256, 0, s>>>(view(g), part, acc.get());
+    if (g->compressed) launch(k_cut<true>, b, 256, 0, s, view(g), part, acc.get());
+    else launch(k_cut<false>, b, 256, 0, s, view(g), part, acc.get());
     TP_LAUNCH_CHECK();
   }
   return (int64_t)(read_scalar(acc.get(), s) / 2);
@@ -90,7 +89,7 @@ int64_t edge_cut(const tp_graph *g, const int32_t *part, cudaStream_t s) {
 void project(const int32_t *coarse_part, const int32_t *map, int64_t n, int32_t *fine_part,
              cudaStream_t s) {
   if (n == 0) return;
-  k_project<<<grid_for(n, 256), 256, 0, s>>>(coarse_part, map, n, fine_part);
+  launch(k_project, grid_for(n, 256), 256, 0, s, coarse_part, map, n, fine_part);
   TP_LAUNCH_CHECK();
 }
 
@@ -143,9 +142,8 @@ void partition(tp_graph *g0, int32_t k, int64_t eps_ppm, const tp_params &p, int
       tp_graph *g = levels.back();
       const int32_t level = (int32_t)levels.size() - 1;
       Buf<int32_t> C(g->n, s), map(g->n, s);
-      if (level == 0) t_lp.start();
-      lp_cluster(g, U, p, level, C.get(), s);
-      if (level == 0) t_lp.stop();
+      if (level == 0) lp_cluster(g, U, p, level, C.get(), s, t_lp.a, t_lp.b);
+      else lp_cluster(g, U, p, level, C.get(), s);
       tp_graph *cg = contract(g, C.get(), map.get(), s);
       if (20 * cg->n > 19 * g->n) {
         delete cg;

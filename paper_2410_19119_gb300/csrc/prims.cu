@@ -123,15 +123,15 @@ void scan(const Tin *in, T *out, int64_t n, bool exclusive, T *total_out, cudaSt
   }
   int64_t tiles = (n + kScanTile - 1) / kScanTile;
   if (tiles == 1) {
-    k_scan_down<Tin, T, Op><<<1, kScanThreads, 0, s>>>(in, out, nullptr, n, exclusive, total_out);
+    launch(k_scan_down<Tin, T, Op>, 1, kScanThreads, 0, s, in, out, nullptr, n, exclusive, total_out);
     TP_LAUNCH_CHECK();
     return;
   }
   Buf<T> tot(tiles, s);
-  k_scan_reduce<Tin, T, Op><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, tot.get(), n);
+  launch(k_scan_reduce<Tin, T, Op>, (unsigned)tiles, kScanThreads, 0, s, in, tot.get(), n);
   TP_LAUNCH_CHECK();
   scan<T, T, Op>(tot.get(), tot.get(), tiles, true, (T *)nullptr, s);
-  k_scan_down<Tin, T, Op><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, tot.get(), n, exclusive,
+  launch(k_scan_down<Tin, T, Op>, (unsigned)tiles, kScanThreads, 0, s, in, out, tot.get(), n, exclusive,
                                                                    total_out);
   TP_LAUNCH_CHECK();
 }
@@ -140,7 +140,6 @@ void scan(const Tin *in, T *out, int64_t n, bool exclusive, T *total_out, cudaSt
 constexpr int kSortWarps = 8;
 constexpr int kSortBatches = 32;                      // 32-key batches per warp
 constexpr int kSortWarpTile = 32 * kSortBatches;      // keys per warp
-constexpr int kSortBlockTile = kSortWarpTile * kSortWarps;
 
 __global__ void k_sort_hist(const uint64_t *keys, int64_t n, int shift, int64_t nwarps,
                             uint32_t *counts) {
@@ -221,11 +220,11 @@ void radix_sort_pairs(uint64_t *keys, uint64_t *vals, int64_t n, int bits, cudaS
   uint64_t *ka = keys, *kb = tk.get(), *va = vals, *vb = vals ? tv.get() : nullptr;
   for (int p = 0; p < passes; ++p) {
     int shift = 8 * p;
-    k_sort_hist<<<blocks, kSortWarps * 32, 0, s>>>(ka, n, shift, nwarps, counts.get());
+    launch(k_sort_hist, blocks, kSortWarps * 32, 0, s, ka, n, shift, nwarps, counts.get());
     TP_LAUNCH_CHECK();
     scan<uint32_t, int64_t, SumOp>(counts.get(), offs.get(), 256 * nwarps, true,
                                    (int64_t *)nullptr, s);
-    k_sort_scatter<<<blocks, kSortWarps * 32, 0, s>>>(ka, va, kb, vb, n, shift, nwarps,
+    launch(k_sort_scatter, blocks, kSortWarps * 32, 0, s, ka, va, kb, vb, n, shift, nwarps,
                                                       offs.get());
     TP_LAUNCH_CHECK();
     std::swap(ka, kb);

@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <atomic>
 #include <utility>
 #include <vector>
 
@@ -86,19 +87,22 @@ struct Buf {
 // ---------------------------------------------------------------- graph
 // Degree tiers used by the rating kernels (performance only; the result of
 // a rating never depends on its tier).
-enum : uint8_t { TIER_SMALL = 0, TIER_MID = 1, TIER_BIG = 2, TIER_HUGE = 3 };
+enum : uint8_t { TIER_SMALL = 0, TIER_MID = 1, TIER_BIG = 2, TIER_HUGE = 3, TIER_LANE = 4 };
+constexpr int kLaneMaxDeg = 32;  // lane tier: one lane per vertex, unit edge weights
 constexpr int64_t kChunkThreshold = 10000;  // compressed format: chunked above this degree
 constexpr int64_t kChunkSize = 1000;        // neighbours per chunk
 
 struct TierCache {
   bool built = false;
-  int32_t small_max = 0, mid_max = 0;
+  int32_t small_max = 0, mid_max = 0, lane_max = 0;
+  int64_t count[5] = {0, 0, 0, 0, 0};  // vertices per tier
   Buf<uint8_t> tier;         // n
-  Buf<int32_t> mid, big, huge;  // vertex lists per tier (ascending)
-  int64_t n_mid = 0, n_big = 0, n_huge = 0;
+  Buf<int32_t> small, mid, big, huge;  // vertex lists per tier (ascending)
+  int64_t n_small = 0, n_mid = 0, n_big = 0, n_huge = 0;
   Buf<int64_t> big_toff, huge_toff;  // global table offsets (slots), size n_tier + 1
   Buf<int32_t> big_tcap, huge_tcap;  // log2 of the table capacity per vertex
   int64_t big_slots = 0, huge_slots = 0;
+  int64_t edges[5] = {0, 0, 0, 0, 0};  // adjacency entries per tier
   Buf<int64_t> huge_chunk_start;  // prefix of chunk counts over the huge list (n_huge + 1)
   int64_t n_huge_chunks = 0;
   Buf<int32_t> tkeys;  // global rating tables (big + huge), EMPTY = -1
@@ -129,7 +133,8 @@ struct tp_graph {
 };
 
 namespace tp {
-constexpr int kBytePad = 64;
+constexpr int kBytePad = 64;  // zero bytes after a compressed stream
+constexpr int kAdjPad = 4;    // int32 entries after a CSR adjacency array
 
 // Read-only device view of a graph for kernels.
 struct GView {
@@ -236,6 +241,30 @@ __device__ __forceinline__ void latch_error(int32_t *err, int32_t code) {
 
 // ---------------------------------------------------------------- launch helpers
 int num_sms();
+void count_launch();
+
+// Every kernel of the library is launched through here (counts launches).
+template <class... KArgs, class... Args>
+inline void launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                   Args &&...args) {
+  k<<<grid, block, smem, s>>>(static_cast<KArgs>(args)...);
+  count_launch();
+}
+
+// Opt-in kernel timing (CUDA events around selected launches).
+enum ProfFamily {
+  PF_RATE_SMALL = 0,
+  PF_RATE_MID,
+  PF_RATE_BIG,
+  PF_RATE_HUGE,
+  PF_APPROVE,
+  PF_RATE_LANE,
+  PF_COUNT
+};
+bool prof_active();                 // profiling enabled and inside a profiled scope
+void prof_scope(bool on);           // level-0 clustering rounds open/close the scope
+void prof_begin(int family, cudaStream_t s);
+void prof_end(int family, cudaStream_t s, double alg_bytes);
 inline unsigned grid_for(int64_t work, int block, int64_t max_blocks = 0) {
   int64_t b = (work + block - 1) / block;
   if (b < 1) b = 1;
@@ -278,10 +307,9 @@ struct LpState {
 // Workspace for sub-rounds on one graph (per-label counters + mover lists).
 struct LpWork {
   int64_t nlabels = 0, n = 0;
-  Buf<int64_t> in_w;    // nlabels
-  Buf<int32_t> in_cnt;  // nlabels
-  Buf<int32_t> cstate;  // nlabels
-  Buf<int32_t> cfill;   // nlabels
+  Buf<int64_t> in_w;   // nlabels: weight of this sub-round's movers per target
+  Buf<int32_t> ccnt;   // nlabels: contested movers per target (zero between sub-rounds)
+  Buf<int32_t> cfill;  // nlabels: fill pointer inside a contested segment
   Buf<int64_t> cbase;   // nlabels
   Buf<int32_t> mv_u, mv_t;  // n
   Buf<int64_t> mv_g;        // n
@@ -295,8 +323,9 @@ void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t
                  const tp_params &p, cudaStream_t stream);
 void lp_rounds(tp_graph *g, const LpState &st, LpWork &w, uint64_t seed, uint64_t tag, uint64_t a,
                uint64_t b0, int32_t rounds, int32_t S, const tp_params &p, cudaStream_t stream);
+// ev_begin / ev_end (nullable) are recorded around the LP rounds alone.
 void lp_cluster(tp_graph *g, int64_t U, const tp_params &p, int32_t level, int32_t *d_cluster,
-                cudaStream_t s);
+                cudaStream_t s, cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
 void lp_refine(tp_graph *g, int32_t k, int64_t l_max, const tp_params &p, int32_t level,
                int32_t *d_part, int64_t *d_B, cudaStream_t s);
 // Per-vertex favourite cluster of singletons (two-hop): fav[u] = best label or n.

@@ -266,7 +266,8 @@ def test_performance_knobs_do_not_change_results():
     z = g.compress()
     rng = np.random.default_rng(0)
     for trial in range(4):
-        p = tp.default_params(seed=9, tier_small=int(rng.choice([1, 16, 32, 64])),
+        p = tp.default_params(seed=9, tier_lane=int(rng.choice([0, 8, 16, 32])),
+                              tier_small=int(rng.choice([1, 16, 32, 64])),
                               tier_mid=int(rng.choice([64, 200, 1000])),
                               warps_per_block=int(rng.choice([2, 4, 8, 16])))
         for gg in (g, z):
