@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(kIPThreads) k_bisect(IPCtx c) {
       if (threadIdx.x == 0) inw[0] = inw[1] = 0, ncnt[0] = ncnt[1] = 0;
       __syncthreads();
       for (int64_t x = threadIdx.x; x < ns; x += blockDim.x) {
-        if ((int32_t)(hstep(rk, (uint64_t)x) % (uint64_t)c.S) != s) continue;
+        if (sub_round_of(hstep(rk, (uint64_t)x), c.S) != s) continue;
         int32_t u = vs[x];
         int64_t Rs[2] = {0, 0};
         for (int64_t e = c.xadj[u]; e < c.xadj[u + 1]; ++e) {

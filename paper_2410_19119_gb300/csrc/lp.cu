@@ -68,13 +68,16 @@ struct RateCtx {
   int64_t tbase;  // slot offset of this tier's tables inside tkeys/tvals
   const int64_t *chunk_start;
   int64_t n_chunks;
+  // lane tier in LP mode: this sub-round's bucket (null: filter every vertex)
+  const int32_t *bucket;
+  const unsigned long long *bucket_cnt;  // [0..S) counts
 };
 
 __device__ __forceinline__ int64_t node_w(const GView &g, int64_t u) { return g.vw ? g.vw[u] : 1; }
 
 template <int MODE>
 __device__ __forceinline__ bool active(const RateCtx &c, int64_t u) {
-  if (MODE == M_LP) return (int32_t)(hstep(c.rk, (uint64_t)u) % (uint64_t)c.S) == c.s;
+  if (MODE == M_LP) return sub_round_of(hstep(c.rk, (uint64_t)u), c.S) == c.s;
   if (MODE == M_FAV) return c.label[u] == u && c.lw[u] == node_w(c.g, u);
   return c.label[u] == c.blk;
 }
@@ -275,16 +278,10 @@ __global__ void k_rate_small(RateCtx c) {
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   if (c.list) {
-    for (int64_t i0 = gw * 32; i0 < c.list_n; i0 += nw * 32) {
-      int64_t i = i0 + lane_id();
-      int64_t u = i < c.list_n ? c.list[i] : 0;
-      unsigned am = __ballot_sync(kFull, i < c.list_n && active<MODE>(c, u));
-      while (am) {
-        int j = __ffs(am) - 1;
-        am &= am - 1;
-        rate_vertex_warp<COMP, MODE>(c, __shfl_sync(kFull, u, j), ws.keys, ws.vals, kSmallLog,
-                                     true, &mb);
-      }
+    for (int64_t i = gw; i < c.list_n; i += nw) {
+      const int64_t u = c.list[i];
+      if (active<MODE>(c, u))
+        rate_vertex_warp<COMP, MODE>(c, u, ws.keys, ws.vals, kSmallLog, true, &mb);
     }
   } else {
     for (int64_t base = gw * 32; base < c.g.n; base += nw * 32) {
@@ -437,7 +434,21 @@ __global__ void __launch_bounds__(kLaneWarps * 32) k_rate_lane(RateCtx c) {
   int pending = 0;  // active vertices queued for this warp (warp-uniform)
   int64_t base = gw * 256;
   int j = 0;
+  // bucket mode: this sub-round's lane-tier vertices come as a list
+  int64_t bstart = 0, bcount = 0, bnext = gw * 32;
+  if (MODE == M_LP && c.bucket) {
+    for (int k = 0; k < c.s; ++k) bstart += (int64_t)c.bucket_cnt[k];
+    bcount = (int64_t)c.bucket_cnt[c.s];
+    base = c.g.n;  // no slab scan
+  }
   for (;;) {
+    if (MODE == M_LP && c.bucket && pending == 0 && bnext < bcount) {
+      int64_t i = bnext + lane;
+      bool act = i < bcount;
+      if (act) queue[lane] = c.bucket[bstart + i];
+      pending = (int)(bcount - bnext < 32 ? bcount - bnext : 32);
+      bnext += nw * 32;
+    }
     // fill the queue, 32 vertices of the current 256-vertex slab at a time
     while (pending < 32 && base < c.g.n) {
       int64_t v = base + 32 * j + lane;
@@ -783,7 +794,9 @@ __global__ void k_approve_contested(ApproveCtx a) {
   }
 }
 
-// D: apply approved moves and reset the per-target counters.
+// D: apply approved moves and reset the per-target counters. The grid covers
+// the largest possible mover count, so every mover has its own thread and
+// the dependent loads of different movers overlap.
 __global__ void k_apply(ApproveCtx a) {
   int64_t nm = (int64_t)a.counters[0];
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nm;
@@ -858,7 +871,9 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
     } else {
       m.list = nullptr;
     }
-    unsigned blocks = (unsigned)std::min<int64_t>((items + 32 * wpb - 1) / (32 * wpb), (int64_t)sms * 16);
+    const int64_t per_warp = MODE != M_REBAL ? 1 : 32;  // list entries / vertices per warp step
+    unsigned blocks = (unsigned)std::min<int64_t>((items + per_warp * wpb - 1) / (per_warp * wpb),
+                                                  (int64_t)sms * 16);
     if (comp) launch(k_rate_small<true, MODE>, blocks, 32 * wpb, sm, s, m);
     else launch(k_rate_small<false, MODE>, blocks, 32 * wpb, sm, s, m);
     TP_LAUNCH_CHECK();
@@ -957,7 +972,76 @@ ApproveCtx approve_ctx(tp_graph *g, const LpState &st, LpWork &w) {
   return a;
 }
 
+// A3: lane-tier vertices of one round grouped by sub-round. Every block
+// owns a contiguous range of vertices and counts per sub-round in shared
+// memory, so there is one global atomic per (block, sub-round); inside a
+// bucket, ids stay in runs of nearby vertices (the order inside a bucket does
+// not affect results). Pass 0 counts, pass 1 writes.
+__global__ void k_bucket(const uint8_t *tier, int64_t n, uint64_t rk, int32_t S, bool fill,
+                         unsigned long long *cnt, int32_t *bucket) {
+  __shared__ unsigned long long local[32], base[32];
+  const int lane = lane_id();
+  const int64_t per_block = ((n + gridDim.x - 1) / gridDim.x + 31) & ~(int64_t)31;
+  const int64_t lo = (int64_t)blockIdx.x * per_block;
+  const int64_t hi = lo + per_block < n ? lo + per_block : n;
+  for (int k = threadIdx.x; k < 32; k += blockDim.x) local[k] = 0;
+  __syncthreads();
+  auto sweep = [&](bool write) {
+    for (int64_t b0 = lo + (threadIdx.x & ~31); b0 < hi; b0 += blockDim.x) {
+      const int64_t u = b0 + lane;
+      const bool lt = u < hi && tier[u] == TIER_LANE;
+      const int32_t sub = lt ? sub_round_of(hstep(rk, (uint64_t)u), S) : -1;
+      for (int32_t k = 0; k < S; ++k) {
+        const unsigned m = __ballot_sync(kFull, sub == k);
+        if (!m) continue;
+        unsigned long long at = 0;
+        if (lane == 0) at = atomicAdd(&local[k], (unsigned long long)__popc(m));
+        if (write) {
+          at = __shfl_sync(kFull, at, 0);
+          if (sub == k) bucket[base[k] + at + __popc(m & lanemask_lt())] = (int32_t)u;
+        }
+      }
+    }
+  };
+  sweep(false);
+  __syncthreads();
+  if (!fill) {
+    for (int k = threadIdx.x; k < S; k += blockDim.x)
+      if (local[k]) atomicAdd(&cnt[k], local[k]);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    unsigned long long run = 0;
+    for (int32_t k = 0; k < S; ++k) {
+      base[k] = run + atomicAdd(&cnt[S + k], local[k]);  // bucket start + this block's slot
+      run += cnt[k];
+      local[k] = 0;
+    }
+  }
+  __syncthreads();
+  sweep(true);
+}
+
 }  // namespace
+
+void lp_bucket(tp_graph *g, LpWork &w, uint64_t rk, int32_t S, const tp_params &p,
+               cudaStream_t stream) {
+  build_tiers(g, p, stream);
+  w.bucket_S = 0;
+  if (S > 32 || g->tiers.count[TIER_LANE] == 0) return;
+  if (!w.bucket.get()) {
+    w.bucket.alloc(std::max<int64_t>(w.n, 1), stream);
+    w.bucket_cnt.alloc(64, stream);
+  }
+  TP_CUDA(cudaMemsetAsync(w.bucket_cnt.get(), 0, 64 * sizeof(unsigned long long), stream));
+  const unsigned blocks = grid_for(g->n, 2048, (int64_t)num_sms() * 4);
+  launch(k_bucket, blocks, 256, 0, stream, g->tiers.tier.get(), g->n, rk, S, false,
+         w.bucket_cnt.get(), w.bucket.get());
+  launch(k_bucket, blocks, 256, 0, stream, g->tiers.tier.get(), g->n, rk, S, true,
+         w.bucket_cnt.get(), w.bucket.get());
+  TP_LAUNCH_CHECK();
+  w.bucket_S = S;
+}
 
 void LpWork::init(int64_t n_vertices, int64_t n_labels, cudaStream_t s) {
   if (n_vertices <= n && n_labels <= nlabels) return;
@@ -996,15 +1080,21 @@ void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t
   c.mv_g = w.mv_g.get();
   c.in_w = w.in_w.get();
   c.counters = (unsigned long long *)w.counters.get();
+  if (w.bucket_S == S) {
+    c.bucket = w.bucket.get();
+    c.bucket_cnt = w.bucket_cnt.get();
+  }
   rate_tiers<M_LP>(g, c, p, stream);
   ApproveCtx a = approve_ctx(g, st, w);
   const unsigned blocks = (unsigned)num_sms() * 4;
   prof_begin(PF_APPROVE, stream);
-  launch(k_approve_fit, blocks, 256, 0, stream, a);
+  launch(k_approve_fit, grid_for(std::max<int64_t>(w.n, 1), 256, (int64_t)num_sms() * 64), 256, 0,
+         stream, a);
   launch(k_approve_alloc, (unsigned)num_sms(), 256, 0, stream, a);
   launch(k_approve_scatter, blocks, 256, 0, stream, a);
   launch(k_approve_contested, (unsigned)num_sms() * 2, 256, 0, stream, a);
-  launch(k_apply, blocks, 256, 0, stream, a);
+  const unsigned wide = grid_for(std::max<int64_t>(w.n, 1), 256, (int64_t)num_sms() * 64);
+  launch(k_apply, wide, 256, 0, stream, a);
   TP_LAUNCH_CHECK();
   TP_CUDA(cudaMemsetAsync(w.counters.get(), 0, 4 * sizeof(int64_t), stream));
   prof_end(PF_APPROVE, stream, 0.0);
@@ -1014,7 +1104,9 @@ void lp_rounds(tp_graph *g, const LpState &st, LpWork &w, uint64_t seed, uint64_
                uint64_t b0, int32_t rounds, int32_t S, const tp_params &p, cudaStream_t stream) {
   for (int32_t r = 0; r < rounds; ++r) {
     uint64_t rk = round_key(seed, tag, a, b0 + (uint64_t)r);
+    lp_bucket(g, w, rk, S, p, stream);
     for (int32_t s = 0; s < S; ++s) lp_subround(g, st, w, rk, S, s, p, stream);
+    w.bucket_S = 0;
   }
 }
 

@@ -175,6 +175,11 @@ constexpr uint64_t kTagIPSeed = 0x495053656564566bULL;   // "IPSeedVk"
 constexpr uint64_t kTagIPLP = 0x49504c5032576179ULL;     // "IPLP2Way"
 constexpr uint64_t kTagTie = 0x5469654272656b72ULL;      // "TieBrekr"
 
+// hash mod S; a mask when S is a power of two (the same value, no division).
+__host__ __device__ __forceinline__ int32_t sub_round_of(uint64_t h, int32_t S) {
+  return (S & (S - 1)) == 0 ? (int32_t)(h & (uint64_t)(S - 1)) : (int32_t)(h % (uint64_t)S);
+}
+
 __device__ __forceinline__ uint32_t tie_hash(uint64_t hv, int32_t x) {
   return (uint32_t)(hstep(hv, (uint64_t)(int64_t)x) >> 32);
 }
@@ -317,10 +322,17 @@ struct LpWork {
   Buf<int32_t> cseg;        // n (contested mover indices grouped by target)
   Buf<int32_t> ctarget;     // nlabels (contested targets)
   Buf<int64_t> counters;    // [0] movers, [1] contested targets, [2] contested pool
+  // sub-round buckets of the lane tier for the current round (A3)
+  Buf<int32_t> bucket;               // n
+  Buf<unsigned long long> bucket_cnt;  // [0..S) counts, [S..2S) fill pointers
+  int32_t bucket_S = 0;              // S of the current buckets (0: none)
   void init(int64_t n_vertices, int64_t n_labels, cudaStream_t s);
 };
 void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t S, int32_t s,
                  const tp_params &p, cudaStream_t stream);
+// Buckets the lane-tier vertices of round key rk by sub-round (A3).
+void lp_bucket(tp_graph *g, LpWork &w, uint64_t rk, int32_t S, const tp_params &p,
+               cudaStream_t stream);
 void lp_rounds(tp_graph *g, const LpState &st, LpWork &w, uint64_t seed, uint64_t tag, uint64_t a,
                uint64_t b0, int32_t rounds, int32_t S, const tp_params &p, cudaStream_t stream);
 // ev_begin / ev_end (nullable) are recorded around the LP rounds alone.
