@@ -212,6 +212,24 @@ tp_status tp_rebalance(const tp_graph *g, int32_t k, int64_t l_max, int32_t *d_p
 tp_status tp_metrics(const tp_graph *g, const int32_t *d_part, int32_t k, int64_t *cut,
                      int64_t *h_block_weights, void *stream);
 
+/* tp_metrics without device allocation: the same cut and block weights,
+ * with the scratch (cut accumulator and k block sums) in a fixed array
+ * inside the library instead of memory from the allocator. For callers that
+ * cannot allocate device memory when they need the metrics: code running
+ * under CUDA stream capture (cudaMalloc cannot be captured), services with a
+ * device-memory footprint fixed up front, callers without an allocator of
+ * their own. The paper has no counterpart; this is an interface convenience.
+ *  - k must be <= 16383 (scratch of 128 KiB, kept by every GPU that loads
+ *    the library until the process exits); larger k returns TP_ERR_BUDGET.
+ *  - The first call on a device looks up the array's device address; make
+ *    that first call before any stream capture begins.
+ *  - Every call uses the same array: calls whose work overlaps on the GPU
+ *    (concurrent streams, other host threads) race and give wrong sums.
+ *  - Synchronises stream; cut and h_block_weights (nullable, k entries) are
+ *    host outputs. */
+tp_status tp_metrics_static(const tp_graph *g, const int32_t *d_part, int32_t k, int64_t *cut,
+                            int64_t *h_block_weights, void *stream);
+
 /* The full multilevel partitioner (Section "The Multilevel Scheme"):
  * coarsen with LP clustering + contraction until n <= c_lim * k (or a level
  * shrinks by less than 5%, or max_levels), partition the coarsest graph,

@@ -61,6 +61,7 @@ SIGNATURES = {
     "tp_lp_refine": (ctypes.c_int, [vp, i32, i64, P(Params), i32, vp, vp]),
     "tp_rebalance": (ctypes.c_int, [vp, i32, i64, vp, P(ctypes.c_int), vp]),
     "tp_metrics": (ctypes.c_int, [vp, vp, i32, P(i64), vp, vp]),
+    "tp_metrics_static": (ctypes.c_int, [vp, vp, i32, P(i64), vp, vp]),
     "tp_partition": (ctypes.c_int, [vp, i32, ctypes.c_double, P(Params), vp, P(Stats), vp]),
     "tp_launch_count": (u64, []),
     "tp_profile_enable": (None, [ctypes.c_int]),
