@@ -37,6 +37,9 @@ WORKLOADS = {
     "rgg24": dict(gen="rgg2d", n=1 << 24, deg=16.0, k=64, seed=1,
                   desc="2D random geometric graph n=2^24, expected degree 16, unit weights, "
                        "k=64, eps=0.03, seed 1; gap+VarInt compressed and int32 CSR"),
+    "rgg23": dict(gen="rgg2d", n=1 << 23, deg=16.0, k=64, seed=1,
+                  desc="2D random geometric graph n=2^23 (half-size profiling case), expected "
+                       "degree 16, unit weights, k=64, eps=0.03, seed 1"),
     "gnm14": dict(gen="gnm", n=1 << 14, m=1 << 17, k=8, seed=1,
                   desc="G(n,m) n=2^14 m=2^17, unit weights, k=8, eps=0.03, seed 1"),
     "rmat26": dict(gen="rmat", scale=26, ef=16, k=256, seed=1,
@@ -69,12 +72,17 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def library_hash():
+KERNEL_SOURCES = {  # files that define each profiled kernel family
+    "rate": ("lp.cu", "decode.cuh", "tp_internal.cuh"),
+}
+
+
+def kernel_source_hash(family="rate"):
     import hashlib
 
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2410_19119_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in KERNEL_SOURCES[family]:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
@@ -91,7 +99,7 @@ def ncu_traffic(kernel_tag, workload):
                 if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
                     fields[k.strip()] = v.strip()
-        if fields.get("source_hash") != library_hash():
+        if fields.get("source_hash") != kernel_source_hash("rate"):
             return None
         return float(fields["dram_bytes_per_launch"])
     except Exception:
@@ -221,6 +229,21 @@ def run_reference(args, w):
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_lp_only(args, w):
+    """Level-0 clustering of the compressed graph only (for profiler captures)."""
+    import torch
+
+    import paper_2410_19119_gb300 as tp
+
+    xadj, adj = make_graph(w)
+    g = tp.graph_from_csr(xadj, adj).compress()
+    n = len(xadj) - 1
+    U = max(1, (30000 * n) // (1000000 * w["k"]))
+    tp.lp_cluster(g, U, tp.default_params(seed=w["seed"]), 0)
+    torch.cuda.synchronize()
+    print(json.dumps({"lp_only": w["desc"], "n": n, "m2": len(adj)}))
 
 
 def run_native(args, w):
@@ -391,9 +414,13 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="rgg24")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lp-only", action="store_true",
+                    help="run only the level-0 clustering once (profiler captures)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
-    if args.impl == "reference":
+    if args.lp_only:
+        run_lp_only(args, w)
+    elif args.impl == "reference":
         run_reference(args, w)
     else:
         run_native(args, w)

@@ -50,6 +50,7 @@ def _load():
             "orc_encode": (i64, [i64, vp, vp, vp, vp]),
             "orc_decode": (ctypes.c_int, [i64, vp, i64, vp, vp, vp, i64]),
             "orc_rate_vertex": (ctypes.c_int, [vp, i64, vp, vp, i64, vp, ctypes.c_int, u64, vp, vp]),
+            "orc_rate_vertex_sorted": (ctypes.c_int, [vp, i64, vp, vp, i64, vp, ctypes.c_int, u64, vp, vp]),
             "orc_lp_subround": (i64, [vp, vp, vp, i64, i64, vp, u64, i32, i32]),
             "orc_lp_rounds": (i64, [vp, vp, vp, i64, i64, vp, u64, u64, u64, u64, i32, i32]),
             "orc_two_hop": (None, [vp, vp, vp, i64, u64, i64]),
@@ -81,12 +82,16 @@ def _p(a):
 class Graph:
     """CSR graph held in numpy arrays (int64 xadj, int32 adj, int64 weights)."""
 
-    def __init__(self, xadj, adj, vw=None, ew=None):
+    def __init__(self, xadj, adj, vw=None, ew=None, implicit_unit=False):
+        """implicit_unit: no weight arrays at all (only rate_vertex_sorted accepts that)."""
         self.xadj = np.ascontiguousarray(xadj, dtype=np.int64)
         self.adj = np.ascontiguousarray(adj, dtype=np.int32)
         n = len(self.xadj) - 1
-        self.vw = np.ones(n, np.int64) if vw is None else np.ascontiguousarray(vw, dtype=np.int64)
-        self.ew = np.ones(len(self.adj), np.int64) if ew is None else np.ascontiguousarray(ew, dtype=np.int64)
+        if implicit_unit:
+            self.vw = self.ew = None
+        else:
+            self.vw = np.ones(n, np.int64) if vw is None else np.ascontiguousarray(vw, dtype=np.int64)
+            self.ew = np.ones(len(self.adj), np.int64) if ew is None else np.ascontiguousarray(ew, dtype=np.int64)
         self._c = _CGraph(n, len(self.adj), _p(self.xadj), _p(self.adj), _p(self.vw), _p(self.ew))
 
     @property
@@ -186,6 +191,22 @@ def rate_vertex(g: Graph, u, label, lw, cap_uniform, cap=None, ignore_cap=False,
     moved = _load().orc_rate_vertex(g.c, u, label.ctypes.data, lw.ctypes.data, cap_uniform,
                                     _p(cap), int(ignore_cap), hv, ctypes.byref(t), ctypes.byref(gain))
     return bool(moved), t.value, gain.value
+
+
+def rate_vertex_sorted(g: Graph, u, label, lw, cap_uniform, cap=None, ignore_cap=False, hv=0):
+    """rate_vertex for one vertex of a large graph (sort-based ratings)."""
+    t = ctypes.c_int32(0)
+    gain = ctypes.c_int64(0)
+    moved = _load().orc_rate_vertex_sorted(g.c, u, label.ctypes.data, lw.ctypes.data, cap_uniform,
+                                           _p(cap), int(ignore_cap), hv, ctypes.byref(t),
+                                           ctypes.byref(gain))
+    return bool(moved), t.value, gain.value
+
+
+def vertex_hashes(rk, u):
+    """(sub-round hash, tie key) of vertex u under round key rk."""
+    hu = step(rk, u)
+    return hu, step(hu, tag(TAG_TIE))
 
 
 def lp_subround(g: Graph, label, lw, nlabels, cap_uniform, cap, rk, S, s):

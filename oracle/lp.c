@@ -107,6 +107,57 @@ int orc_rate_vertex(const orc_graph *g, int64_t u, const int32_t *label, const i
 }
 
 typedef struct {
+  int32_t x;
+  int64_t w;
+} label_weight;
+
+static int cmp_label_weight(const void *pa, const void *pb) {
+  const label_weight *a = (const label_weight *)pa, *b = (const label_weight *)pb;
+  return a->x < b->x ? -1 : (a->x > b->x);
+}
+
+/* The same decision as orc_rate_vertex, with the ratings formed by sorting
+ * the (label, weight) pairs of N(u) and summing runs of equal labels, so a
+ * single vertex costs O(deg log deg) on graphs of any size. Null vw / ew
+ * arrays mean unit weights (large graphs need not carry arrays of ones). */
+int orc_rate_vertex_sorted(const orc_graph *g, int64_t u, const int32_t *label, const int64_t *lw,
+                           int64_t cap_uniform, const int64_t *cap, int ignore_cap, uint64_t hv,
+                           int32_t *target, int64_t *gain) {
+  int64_t d = g->xadj[u + 1] - g->xadj[u];
+  label_weight *p = (label_weight *)malloc(sizeof(label_weight) * (size_t)(d + 1));
+  for (int64_t i = 0; i < d; ++i) {
+    p[i].x = label[g->adj[g->xadj[u] + i]];
+    p[i].w = g->ew ? g->ew[g->xadj[u] + i] : 1;
+  }
+  qsort(p, (size_t)d, sizeof(label_weight), cmp_label_weight);
+  int32_t own = label[u];
+  int64_t r_own = 0, best = -1, best_r = 0;
+  uint32_t best_t = 0;
+  for (int64_t i = 0; i < d;) {
+    int64_t j = i, r = 0;
+    while (j < d && p[j].x == p[i].x) r += p[j++].w;
+    int32_t x = p[i].x;
+    i = j;
+    if (x == own) {
+      r_own = r;
+      continue;
+    }
+    if (!ignore_cap && lw[x] + (g->vw ? g->vw[u] : 1) > cap_of(cap_uniform, cap, x)) continue;
+    uint32_t t = tie_hash(hv, x);
+    if (best < 0 || better(r, t, x, best_r, best_t, best)) {
+      best = x;
+      best_r = r;
+      best_t = t;
+    }
+  }
+  free(p);
+  if (best < 0 || best_r <= r_own) return 0;
+  *target = (int32_t)best;
+  *gain = best_r - r_own;
+  return 1;
+}
+
+typedef struct {
   int64_t u;
   int64_t gain;
   int64_t w;

@@ -90,6 +90,10 @@ int orc_decode(int64_t n, const uint8_t *bytes, int64_t nbytes, const uint64_t *
 int orc_rate_vertex(const orc_graph *g, int64_t u, const int32_t *label, const int64_t *lw,
                     int64_t cap_uniform, const int64_t *cap, int ignore_cap, uint64_t hv,
                     int32_t *target, int64_t *gain);
+/* Same decision, ratings formed by sorting N(u) (no n-sized scratch). */
+int orc_rate_vertex_sorted(const orc_graph *g, int64_t u, const int32_t *label, const int64_t *lw,
+                           int64_t cap_uniform, const int64_t *cap, int ignore_cap, uint64_t hv,
+                           int32_t *target, int64_t *gain);
 /* One sub-round s of round key rk. Returns the number of applied moves.
  */
 int64_t orc_lp_subround(const orc_graph *g, int32_t *label, int64_t *lw, int64_t nlabels,

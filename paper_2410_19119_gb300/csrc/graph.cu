@@ -351,13 +351,58 @@ __device__ __forceinline__ uint64_t first_code(int64_t v0, int64_t u) {
   return v0 >= u ? 2ull * (uint64_t)(v0 - u) : 2ull * (uint64_t)(u - v0) + 1ull;
 }
 
-// Encoded size of every neighbourhood (warp per vertex).
+constexpr int64_t kZipLaneMax = 256;  // thread per vertex up to this degree
+
+// Encoded size of every neighbourhood of degree <= kZipLaneMax, one thread
+// per vertex (the warp kernel below takes the rest).
+__global__ void k_zip_size_lane(GView g, int64_t *size) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < g.n;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = g.xadj[u], d = g.xadj[u + 1] - b;
+    if (d > kZipLaneMax) continue;
+    int64_t acc = vlen((uint64_t)b);
+    int32_t prev = 0;
+    for (int64_t i = 0; i < d; ++i) {
+      const int32_t v = g.adj[b + i];
+      acc += i == 0 ? vlen(first_code(v, u)) : vlen((uint64_t)(v - prev));
+      prev = v;
+    }
+    size[u] = acc;
+  }
+}
+
+// Writes every neighbourhood of degree <= kZipLaneMax, one thread per vertex.
+__global__ void k_zip_write_lane(GView g, const int64_t *off, uint8_t *out) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < g.n;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = g.xadj[u], d = g.xadj[u + 1] - b;
+    if (d > kZipLaneMax) continue;
+    uint64_t p = (uint64_t)off[u];
+    auto put = [&](uint64_t x) {
+      while (x >= 128) {
+        out[p++] = (uint8_t)(0x80u | (x & 0x7fu));
+        x >>= 7;
+      }
+      out[p++] = (uint8_t)x;
+    };
+    put((uint64_t)b);
+    int32_t prev = 0;
+    for (int64_t i = 0; i < d; ++i) {
+      const int32_t v = g.adj[b + i];
+      put(i == 0 ? first_code(v, u) : (uint64_t)(v - prev));
+      prev = v;
+    }
+  }
+}
+
+// Encoded size of every neighbourhood above kZipLaneMax (warp per vertex).
 __global__ void k_zip_size(GView g, int64_t *size) {
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   int lane = lane_id();
   for (int64_t u = warp; u < g.n; u += nw) {
     int64_t b = g.xadj[u], d = g.xadj[u + 1] - b;
+    if (d <= kZipLaneMax) continue;
     int64_t nch = d > kChunkThreshold ? (d + kChunkSize - 1) / kChunkSize : 1;
     int64_t csz = nch > 1 ? kChunkSize : d;
     int64_t acc = 0;
@@ -370,13 +415,14 @@ __global__ void k_zip_size(GView g, int64_t *size) {
   }
 }
 
-// Writes every neighbourhood at its offset (warp per vertex).
+// Writes every neighbourhood above kZipLaneMax at its offset (warp per vertex).
 __global__ void k_zip_write(GView g, const int64_t *off, uint8_t *out) {
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   int lane = lane_id();
   for (int64_t u = warp; u < g.n; u += nw) {
     int64_t b = g.xadj[u], d = g.xadj[u + 1] - b;
+    if (d <= kZipLaneMax) continue;
     uint64_t pos = (uint64_t)off[u];
     int hl = vlen((uint64_t)b);
     if (lane == 0) {
@@ -511,7 +557,8 @@ tp_graph *compress(const tp_graph *c, cudaStream_t s) {
     int64_t n = c->n;
     Buf<int64_t> off(n + 1, s);
     if (n) {
-      launch(k_zip_size, grid_for(n * 32, 256), 256, 0, s, v, off.get());
+      launch(k_zip_size_lane, grid_for(n, 256), 256, 0, s, v, off.get());
+      if (c->max_deg > kZipLaneMax || c->max_deg == 0) launch(k_zip_size, grid_for(n * 32, 256), 256, 0, s, v, off.get());
       TP_LAUNCH_CHECK();
     }
     exclusive_scan_i64(off.get(), off.get(), n, s);
@@ -522,7 +569,9 @@ tp_graph *compress(const tp_graph *c, cudaStream_t s) {
     z->bytes.alloc(z->nbytes + kBytePad, s);
     TP_CUDA(cudaMemsetAsync(z->bytes.get(), 0, z->nbytes + kBytePad, s));
     if (n) {
-      launch(k_zip_write, grid_for(n * 32, 256), 256, 0, s, v, off.get(), z->bytes.get());
+      launch(k_zip_write_lane, grid_for(n, 256), 256, 0, s, v, off.get(), z->bytes.get());
+      if (c->max_deg > kZipLaneMax || c->max_deg == 0)
+        launch(k_zip_write, grid_for(n * 32, 256), 256, 0, s, v, off.get(), z->bytes.get());
       TP_LAUNCH_CHECK();
     }
     launch(k_zip_terminal, 1, 1, 0, s, (uint64_t)body, c->m2, z->bytes.get());

@@ -1034,7 +1034,8 @@ void lp_bucket(tp_graph *g, LpWork &w, uint64_t rk, int32_t S, const tp_params &
     w.bucket_cnt.alloc(64, stream);
   }
   TP_CUDA(cudaMemsetAsync(w.bucket_cnt.get(), 0, 64 * sizeof(unsigned long long), stream));
-  const unsigned blocks = grid_for(g->n, 2048, (int64_t)num_sms() * 4);
+  // 2048 vertices per block: enough blocks to overlap the tier loads
+  const unsigned blocks = grid_for(g->n, 2048, (int64_t)1 << 20);
   launch(k_bucket, blocks, 256, 0, stream, g->tiers.tier.get(), g->n, rk, S, false,
          w.bucket_cnt.get(), w.bucket.get());
   launch(k_bucket, blocks, 256, 0, stream, g->tiers.tier.get(), g->n, rk, S, true,

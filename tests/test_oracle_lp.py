@@ -49,11 +49,12 @@ def test_rating_argmax_by_enumeration(seed):
     for u in range(n):
         for ignore in (False, True):
             hv = int(rng.integers(0, 2**63))
-            got = oracle.rate_vertex(g, u, label, lw, 0, cap, ignore, hv)
             want = bf.rate(xadj, adj, ew, vw, u, label, lw, nlabels, cap, ignore, hv)
-            assert got[0] == want[0], (u, got, want)
-            if want[0]:
-                assert got[1:] == want[1:], (u, got, want)
+            for rate in (oracle.rate_vertex, oracle.rate_vertex_sorted):
+                got = rate(g, u, label, lw, 0, cap, ignore, hv)
+                assert got[0] == want[0], (u, got, want)
+                if want[0]:
+                    assert got[1:] == want[1:], (u, got, want)
 
 
 @pytest.mark.parametrize("seed", range(16))
