@@ -32,12 +32,29 @@ __global__ void k_map(const int32_t *C, const int64_t *rank, const int64_t *vw, 
   }
 }
 
-// Per-vertex count of inter-cluster entries (hubs are counted per chunk).
+__device__ __forceinline__ bool thread_tier(uint8_t t) { return t == TIER_LANE || t == TIER_SMALL; }
+
+// Per-vertex count of inter-cluster entries, one thread per low-degree vertex.
+template <bool COMP>
+__global__ void k_count_thread(GView g, const uint8_t *tier, const int32_t *map, int64_t *cnt) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < g.n;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    if (!thread_tier(tier[u])) continue;
+    const int32_t a = map[u];
+    int64_t c = 0;
+    thread_neighbours<COMP>(g, u, [&](int32_t v, int64_t) { c += map[v] != a; });
+    cnt[u] = c;
+  }
+}
+
+// Per-vertex count of inter-cluster entries, one warp per medium vertex
+// (hubs are counted per chunk below).
 template <bool COMP>
 __global__ void k_count(GView g, const uint8_t *tier, const int32_t *map, int64_t *cnt) {
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t u = warp; u < g.n; u += nw) {
+    if (thread_tier(tier[u])) continue;
     int64_t c = 0;
     if (tier[u] != TIER_HUGE) {
       int32_t a = map[u];
@@ -95,12 +112,31 @@ __device__ __forceinline__ void emit(const GView &g, int64_t u, int64_t chunk, c
 }
 
 template <bool COMP>
+__global__ void k_emit_thread(GView g, const uint8_t *tier, const int32_t *map, int64_t nc,
+                              const int64_t *off, uint64_t *keys, uint64_t *vals) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < g.n;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    if (!thread_tier(tier[u])) continue;
+    const int32_t a = map[u];
+    int64_t pos = off[u];
+    thread_neighbours<COMP>(g, u, [&](int32_t v, int64_t w) {
+      const int32_t b = map[v];
+      if (b == a) return;
+      keys[pos] = (uint64_t)a * (uint64_t)nc + (uint64_t)b;
+      if (vals) vals[pos] = (uint64_t)w;
+      ++pos;
+    });
+  }
+}
+
+template <bool COMP>
 __global__ void k_emit(GView g, const uint8_t *tier, const int32_t *map, int64_t nc,
                        const int64_t *off, uint64_t *keys, uint64_t *vals) {
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t u = warp; u < g.n; u += nw)
-    if (tier[u] != TIER_HUGE) emit<COMP>(g, u, -1, map, nc, off[u], keys, vals);
+    if (!thread_tier(tier[u]) && tier[u] != TIER_HUGE)
+      emit<COMP>(g, u, -1, map, nc, off[u], keys, vals);
 }
 
 template <bool COMP>
@@ -183,8 +219,14 @@ tp_graph *contract(const tp_graph *g, const int32_t *C, int32_t *d_map, cudaStre
     const bool comp = g->compressed;
     Buf<int64_t> off(n + 1, s);
     unsigned wb = grid_for(n * 32, 256);
-    if (comp) launch(k_count<true>, wb, 256, 0, s, v, T.tier.get(), map, off.get());
-    else launch(k_count<false>, wb, 256, 0, s, v, T.tier.get(), map, off.get());
+    unsigned tb = grid_for(n, 256);
+    const bool warp_work = T.n_mid + T.n_big > 0;
+    if (comp) launch(k_count_thread<true>, tb, 256, 0, s, v, T.tier.get(), map, off.get());
+    else launch(k_count_thread<false>, tb, 256, 0, s, v, T.tier.get(), map, off.get());
+    if (warp_work || T.n_huge) {  // the warp kernel also zeroes the hub entries
+      if (comp) launch(k_count<true>, wb, 256, 0, s, v, T.tier.get(), map, off.get());
+      else launch(k_count<false>, wb, 256, 0, s, v, T.tier.get(), map, off.get());
+    }
     TP_LAUNCH_CHECK();
     exclusive_scan_i64(off.get(), off.get(), n, s);
     int64_t m_small = read_scalar(off.get() + n, s);
@@ -207,8 +249,14 @@ tp_graph *contract(const tp_graph *g, const int32_t *C, int32_t *d_map, cudaStre
     const bool weighted = !g->unit_ew;
     Buf<uint64_t> keys(std::max<int64_t>(m, 1), s), vals;
     if (weighted) vals.alloc(std::max<int64_t>(m, 1), s);
-    if (comp) launch(k_emit<true>, wb, 256, 0, s, v, T.tier.get(), map, nc, off.get(), keys.get(), vals.get());
-    else launch(k_emit<false>, wb, 256, 0, s, v, T.tier.get(), map, nc, off.get(), keys.get(), vals.get());
+    if (comp)
+      launch(k_emit_thread<true>, tb, 256, 0, s, v, T.tier.get(), map, nc, off.get(), keys.get(), vals.get());
+    else
+      launch(k_emit_thread<false>, tb, 256, 0, s, v, T.tier.get(), map, nc, off.get(), keys.get(), vals.get());
+    if (warp_work) {
+      if (comp) launch(k_emit<true>, wb, 256, 0, s, v, T.tier.get(), map, nc, off.get(), keys.get(), vals.get());
+      else launch(k_emit<false>, wb, 256, 0, s, v, T.tier.get(), map, nc, off.get(), keys.get(), vals.get());
+    }
     TP_LAUNCH_CHECK();
     if (T.n_huge) {
       unsigned hb = grid_for(T.n_huge_chunks * 32, 256);
@@ -247,8 +295,7 @@ tp_graph *contract(const tp_graph *g, const int32_t *C, int32_t *d_map, cudaStre
       TP_LAUNCH_CHECK();
     }
     exclusive_scan_i64(cg->xadj.get(), cg->xadj.get(), nc, s);
-    // max degree (host needs it for nothing but info); keep stats consistent
-    TP_CUDA(cudaStreamSynchronize(s));
+    cg->max_ew = max_i64(cg->ew.get(), m2, s);  // synchronises
   } catch (...) {
     delete cg;
     throw;

@@ -175,4 +175,57 @@ __device__ __forceinline__ void warp_neighbours(const GView &g, int64_t u, int64
   }
 }
 
+// Visits the neighbours of u with a single thread: f(int32_t v, int64_t w).
+// Only for vertices that are not chunked (degree <= 10000 in the compressed
+// format). The adjacency is read with evict-first loads (it is streamed once
+// per pass); compressed streams were validated when the graph was created,
+// so ids are only clamped into [0, n) to keep later accesses in bounds.
+// Returns the degree.
+template <bool COMP, class F>
+__device__ __forceinline__ int64_t thread_neighbours(const GView &g, int64_t u, F &&f) {
+  if (!COMP) {
+    const int64_t b = __ldcs(g.xadj + u), e = __ldcs(g.xadj + u + 1);
+    for (int64_t k = b; k < e; ++k) f(__ldcs(g.adj + k), g.ew ? __ldcs(g.ew + k) : (int64_t)1);
+    return e - b;
+  }
+  const uint64_t b = g.off32 ? (uint64_t)__ldcs(g.off32 + u) : __ldcs(g.off64 + u);
+  const uint64_t e = g.off32 ? (uint64_t)__ldcs(g.off32 + u + 1) : __ldcs(g.off64 + u + 1);
+  const int32_t nmax = (int32_t)(g.n - 1);
+  const uint32_t *wp = reinterpret_cast<const uint32_t *>(g.bytes + (b & ~(uint64_t)3));
+  uint32_t word = __ldcs(wp) >> (8 * (b & 3));
+  uint32_t nextw = __ldcs(wp + 1);
+  int left = 4 - (int)(b & 3);     // bytes still unread in `word`
+  int remaining = (int)(e - b);    // one record (degree <= 10000) is far below 2^31 bytes
+  while (remaining > 0) {  // header (first edge id): skip to its last byte
+    const uint32_t byte = word & 255u;
+    word >>= 8;
+    --remaining;
+    if (--left == 0) word = nextw, nextw = __ldcs(++wp + 1), left = 4;
+    if (!(byte & 0x80u)) break;
+  }
+  uint32_t val = 0;
+  int shift = 0, cnt = 0;
+  int32_t prev = (int32_t)u;
+  bool first = true;
+  while (remaining > 0) {
+    const uint32_t byte = word & 255u;
+    word >>= 8;
+    --remaining;
+    if (--left == 0) word = nextw, nextw = __ldcs(++wp + 1), left = 4;  // padded stream
+    val |= (byte & 0x7fu) << shift;
+    shift += 7;
+    if (byte & 0x80u) continue;
+    int32_t v = first ? ((val & 1u) ? prev - (int32_t)(val >> 1) : prev + (int32_t)(val >> 1))
+                      : prev + (int32_t)val;
+    v = min(max(v, 0), nmax);
+    first = false;
+    prev = v;
+    f(v, (int64_t)1);
+    ++cnt;
+    val = 0;
+    shift = 0;
+  }
+  return cnt;
+}
+
 }  // namespace tp

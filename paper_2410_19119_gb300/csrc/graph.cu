@@ -263,7 +263,8 @@ __global__ void k_fill_table(int32_t *keys, int64_t *vals, int64_t n) {
 void build_tiers(tp_graph *g, const tp_params &p, cudaStream_t s) {
   TierCache &T = g->tiers;
   // the lane tier rates with one lane per vertex and needs unit edge weights
-  int32_t lane_max = g->unit_ew ? std::max(0, std::min(p.tier_lane, kLaneMaxDeg)) : 0;
+  const bool lane_ok = g->unit_ew || g->max_ew < kLaneMaxEdgeWeight;
+  int32_t lane_max = lane_ok ? std::max(0, std::min(p.tier_lane, kLaneMaxDeg)) : 0;
   int32_t small_max = std::max(lane_max, std::min(p.tier_small, 64));
   int32_t mid_max = std::max(small_max, std::min(p.tier_mid, 1024));
   if (T.built && T.small_max == small_max && T.mid_max == mid_max && T.lane_max == lane_max) return;
@@ -541,6 +542,7 @@ static void finish_graph_stats(tp_graph *g, cudaStream_t s) {
   TP_CUDA(cudaStreamSynchronize(s));
   g->total_vw = h[0];
   if (!g->compressed) g->max_deg = h[1];
+  g->max_ew = g->unit_ew ? 1 : max_i64(g->ew.get(), g->m2, s);
 }
 
 tp_graph *compress(const tp_graph *c, cudaStream_t s) {

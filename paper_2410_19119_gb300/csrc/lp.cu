@@ -326,64 +326,23 @@ __device__ __forceinline__ bool lane_better(const LaneCand &a, const LaneCand &b
   return better(a.r, a.t, a.x, b.r, b.t, b.x);
 }
 
-// Decodes the record of u into col[i * 32] (compressed); returns the degree.
-// A rolled loop over aligned 32-bit words keeps the code small; the stream
-// and offsets are read with evict-first loads so label arrays stay in L2.
-// Streams are validated when a graph is created, so the hot loop only
-// clamps ids into [0, n) to keep every later access in bounds.
-__device__ __forceinline__ int lane_decode_zip(const GView &g, int64_t u, int32_t *col) {
-  const uint64_t b = g.off32 ? (uint64_t)__ldcs(g.off32 + u) : __ldcs(g.off64 + u);
-  const uint64_t e = g.off32 ? (uint64_t)__ldcs(g.off32 + u + 1) : __ldcs(g.off64 + u + 1);
-  const int32_t nmax = (int32_t)(g.n - 1);
-  const uint32_t *wp = reinterpret_cast<const uint32_t *>(g.bytes + (b & ~(uint64_t)3));
-  uint32_t word = __ldcs(wp) >> (8 * (b & 3));
-  uint32_t nextw = __ldcs(wp + 1);
-  int left = 4 - (int)(b & 3);  // bytes still unread in `word`
-  int remaining = (int)(e - b);
-  // header (first edge id): skip to its last byte
-  while (remaining > 0) {
-    uint32_t byte = word & 255u;
-    word >>= 8;
-    --remaining;
-    if (--left == 0) word = nextw, nextw = __ldcs(++wp + 1), left = 4;
-    if (!(byte & 0x80u)) break;
-  }
-  uint32_t val = 0;
-  int shift = 0, cntv = 0;
-  int32_t prev = (int32_t)u;
-  bool first = true;
-  while (remaining > 0) {
-    uint32_t byte = word & 255u;
-    word >>= 8;
-    --remaining;
-    if (--left == 0) word = nextw, nextw = __ldcs(++wp + 1), left = 4;
-    val |= (byte & 0x7fu) << shift;
-    shift += 7;
-    if (byte & 0x80u) continue;
-    int32_t v = first ? ((val & 1u) ? prev - (int32_t)(val >> 1) : prev + (int32_t)(val >> 1))
-                      : prev + (int32_t)val;
-    v = min(max(v, 0), nmax);
-    first = false;
-    prev = v;
-    col[min(cntv, kLaneMaxDeg - 1) * 32] = v;
-    ++cntv;
-    val = 0;
-    shift = 0;
-  }
-  return min(cntv, kLaneMaxDeg);
-}
-
-// Loads the adjacency of u into col[i * 32] (CSR); returns the degree.
-__device__ __forceinline__ int lane_load_csr(const GView &g, int64_t u, int32_t *col) {
-  const int64_t b = __ldcs(g.xadj + u), e = __ldcs(g.xadj + u + 1);
-#pragma unroll 4
-  for (int64_t k = b; k < e; ++k) col[(k - b) * 32] = __ldcs(g.adj + k);
-  return (int)(e - b);
+// Loads the neighbour ids of u into col[i * 32] (and, weighted, the edge
+// weights into wcol[i * 32]); returns the degree.
+template <bool COMP, bool W>
+__device__ __forceinline__ int lane_load(const GView &g, int64_t u, int32_t *col, uint32_t *wcol) {
+  int i = 0;
+  thread_neighbours<COMP>(g, u, [&](int32_t v, int64_t w) {
+    const int k = min(i, kLaneMaxDeg - 1);
+    col[k * 32] = v;
+    if (W) wcol[k * 32] = (uint32_t)w;
+    ++i;
+  });
+  return min(i, kLaneMaxDeg);
 }
 
 // Sorts a[0..N) ascending with a bitonic network (registers only).
-template <int N>
-__device__ __forceinline__ void bitonic_sort(int32_t (&a)[kLaneMaxDeg]) {
+template <int N, class T>
+__device__ __forceinline__ void bitonic_sort(T (&a)[kLaneMaxDeg]) {
 #pragma unroll
   for (int k = 2; k <= N; k <<= 1) {
 #pragma unroll
@@ -392,7 +351,7 @@ __device__ __forceinline__ void bitonic_sort(int32_t (&a)[kLaneMaxDeg]) {
       for (int i = 0; i < N; ++i) {
         const int l = i ^ jd;
         if (l > i) {
-          const int32_t lo = min(a[i], a[l]), hi = max(a[i], a[l]);
+          const T lo = min(a[i], a[l]), hi = max(a[i], a[l]);
           if ((i & k) == 0) a[i] = lo, a[l] = hi;
           else a[i] = hi, a[l] = lo;
         }
@@ -401,32 +360,67 @@ __device__ __forceinline__ void bitonic_sort(int32_t (&a)[kLaneMaxDeg]) {
   }
 }
 
-// Sorted labels -> (label, run length) pairs compacted to the front of the
-// column; returns the number of distinct labels (padding excluded).
-template <int N>
-__device__ __forceinline__ int runs_to_column(const int32_t (&a)[kLaneMaxDeg], int32_t *col,
-                                              uint8_t *cnt) {
-  int k = 0, run = 1;
+// Sorted labels -> (label, rating) pairs compacted to the front of the
+// columns; returns the number of distinct labels (padding excluded).
+// Unit weights: a[i] is a label, the rating is the run length. Weighted:
+// a[i] = label << 32 | weight, the rating is the sum of the run's weights.
+template <int N, bool W, class T>
+__device__ __forceinline__ int runs_to_column(const T (&a)[kLaneMaxDeg], int32_t *col,
+                                              uint8_t *cnt, uint32_t *rcol) {
+  int k = 0;
+  uint32_t run = 0;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
-    const bool last = i + 1 == N || a[i + 1] != a[i];
-    if (last && a[i] != INT32_MAX) {
-      col[k * 32] = a[i];
-      cnt[k * 32] = (uint8_t)run;
-      ++k;
+    const int32_t x = W ? (int32_t)((uint64_t)a[i] >> 32) : (int32_t)a[i];
+    run += W ? (uint32_t)((uint64_t)a[i] & 0xffffffffu) : 1u;
+    const int32_t nx = i + 1 == N ? INT32_MAX
+                                  : (W ? (int32_t)((uint64_t)a[i + 1] >> 32) : (int32_t)a[i + 1]);
+    if (nx != x) {
+      if (x != INT32_MAX) {
+        col[k * 32] = x;
+        if (W) rcol[k * 32] = run;
+        else cnt[k * 32] = (uint8_t)run;
+        ++k;
+      }
+      run = 0;
     }
-    run = last ? 1 : run + 1;
   }
   return k;
 }
 
-template <bool COMP, int MODE>
-__global__ void __launch_bounds__(kLaneWarps * 32) k_rate_lane(RateCtx c) {
-  __shared__ int32_t lab_all[kLaneWarps][kLaneMaxDeg][32];
-  __shared__ uint8_t cnt_all[kLaneWarps][kLaneMaxDeg][32];
-  __shared__ int32_t queue_all[kLaneWarps][64];
+template <int N, bool W>
+__device__ __forceinline__ int sort_runs(int deg, int32_t *col, uint8_t *cnt, uint32_t *wcol) {
+  if constexpr (W) {
+    // padding: label INT32_MAX, weight 0 (sorts last, skipped as a run)
+    constexpr uint64_t kPad = (uint64_t)INT32_MAX << 32;
+    uint64_t a[kLaneMaxDeg];
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      a[i] = i < deg ? ((uint64_t)(uint32_t)col[i * 32] << 32) | wcol[i * 32] : kPad;
+    bitonic_sort<N>(a);
+    return runs_to_column<N, true>(a, col, cnt, wcol);
+  } else {
+    int32_t a[kLaneMaxDeg];
+#pragma unroll
+    for (int i = 0; i < N; ++i) a[i] = i < deg ? col[i * 32] : INT32_MAX;
+    bitonic_sort<N>(a);
+    return runs_to_column<N, false>(a, col, cnt, wcol);
+  }
+}
+
+template <bool W>
+__host__ __device__ constexpr int lane_warps() { return W ? 4 : kLaneWarps; }
+
+template <bool COMP, int MODE, bool W>
+__global__ void __launch_bounds__(lane_warps<W>() * 32, W ? 1 : 4) k_rate_lane(RateCtx c) {
+  constexpr int WARPS = lane_warps<W>();
+  __shared__ int32_t lab_all[WARPS][kLaneMaxDeg][32];
+  __shared__ uint32_t aux_all[WARPS][W ? kLaneMaxDeg : 1][32];  // weights, then ratings
+  __shared__ uint8_t cnt_all[WARPS][W ? 1 : kLaneMaxDeg][32];   // ratings (unit weights)
+  __shared__ int32_t queue_all[WARPS][64];
   const int lane = lane_id(), w = threadIdx.x >> 5;
   int32_t *col = &lab_all[w][0][lane];
+  uint32_t *wcol = &aux_all[w][0][lane];
   uint8_t *cnt = &cnt_all[w][0][lane];
   int32_t *queue = queue_all[w];
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -444,12 +438,11 @@ __global__ void __launch_bounds__(kLaneWarps * 32) k_rate_lane(RateCtx c) {
   for (;;) {
     if (MODE == M_LP && c.bucket && pending == 0 && bnext < bcount) {
       int64_t i = bnext + lane;
-      bool act = i < bcount;
-      if (act) queue[lane] = c.bucket[bstart + i];
+      if (i < bcount) queue[lane] = c.bucket[bstart + i];
       pending = (int)(bcount - bnext < 32 ? bcount - bnext : 32);
       bnext += nw * 32;
     }
-    // fill the queue, 32 vertices of the current 256-vertex slab at a time
+    // otherwise fill the queue, 32 vertices of the current 256-vertex slab at a time
     while (pending < 32 && base < c.g.n) {
       int64_t v = base + 32 * j + lane;
       bool act = v < c.g.n && c.tier[v] == TIER_LANE && active<MODE>(c, v);
@@ -469,25 +462,14 @@ __global__ void __launch_bounds__(kLaneWarps * 32) k_rate_lane(RateCtx c) {
     __syncwarp();
     pending -= take;
     int deg = 0;
-    if (has) deg = COMP ? lane_decode_zip(c.g, u, col) : lane_load_csr(c.g, u, col);
+    if (has) deg = lane_load<COMP, W>(c.g, u, col, wcol);
     // label gathers, independent loads
 #pragma unroll 4
     for (int i = 0; i < deg; ++i) col[i * 32] = __ldg(c.label + col[i * 32]);
-    // ratings: sort the labels; runs of equal labels are the ratings
-    int32_t a[kLaneMaxDeg];
-    int ncand;
+    // ratings: sort the labels; runs of equal labels give the ratings
     const int maxdeg = __reduce_max_sync(kFull, (unsigned)deg);
-    if (maxdeg <= 16) {
-#pragma unroll
-      for (int i = 0; i < 16; ++i) a[i] = i < deg ? col[i * 32] : INT32_MAX;
-      bitonic_sort<16>(a);
-      ncand = runs_to_column<16>(a, col, cnt);
-    } else {
-#pragma unroll
-      for (int i = 0; i < kLaneMaxDeg; ++i) a[i] = i < deg ? col[i * 32] : INT32_MAX;
-      bitonic_sort<kLaneMaxDeg>(a);
-      ncand = runs_to_column<kLaneMaxDeg>(a, col, cnt);
-    }
+    const int ncand = maxdeg <= 16 ? sort_runs<16, W>(deg, col, cnt, wcol)
+                                   : sort_runs<kLaneMaxDeg, W>(deg, col, cnt, wcol);
     // own rating and the two best candidates
     const int32_t own = has ? c.label[u] : -1;
     const int64_t cu = has ? node_w(c.g, u) : 1;
@@ -496,7 +478,7 @@ __global__ void __launch_bounds__(kLaneWarps * 32) k_rate_lane(RateCtx c) {
     int32_t rown = 0;
     for (int k = 0; k < ncand; ++k) {
       const int32_t x = col[k * 32];
-      const int r = cnt[k * 32];
+      const int32_t r = W ? (int32_t)wcol[k * 32] : (int32_t)cnt[k * 32];
       if (x == own) {
         rown = r;
         continue;
@@ -520,7 +502,8 @@ __global__ void __launch_bounds__(kLaneWarps * 32) k_rate_lane(RateCtx c) {
         for (int k = 0; k < ncand; ++k) {
           const int32_t x = col[k * 32];
           if (x == own || x == b1.x || x == b2.x) continue;
-          LaneCand cand{cnt[k * 32], tie_hash(hv, x), x};
+          const int32_t r = W ? (int32_t)wcol[k * 32] : (int32_t)cnt[k * 32];
+          LaneCand cand{r, tie_hash(hv, x), x};
           if (lane_better(cand, best) && c.lw[x] + cu <= c.cap) best = cand;
         }
       }
@@ -851,10 +834,18 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
   const int64_t n_small = T.count[TIER_SMALL] + (MODE == M_REBAL ? T.count[TIER_LANE] : 0);
   if (n_lane > 0) {
     if (prof) prof_begin(PF_RATE_LANE, s);
-    unsigned blocks = (unsigned)std::min<int64_t>((g->n + 256 * kLaneWarps - 1) / (256 * kLaneWarps),
-                                                  (int64_t)sms * 8);
-    if (comp) launch(k_rate_lane<true, MODE == M_REBAL ? M_LP : MODE>, blocks, 32 * kLaneWarps, 0, s, c);
-    else launch(k_rate_lane<false, MODE == M_REBAL ? M_LP : MODE>, blocks, 32 * kLaneWarps, 0, s, c);
+    constexpr int LM = MODE == M_REBAL ? M_LP : MODE;
+    if (g->unit_ew) {
+      unsigned blocks = (unsigned)std::min<int64_t>(
+          (g->n + 256 * kLaneWarps - 1) / (256 * kLaneWarps), (int64_t)sms * 8);
+      if (comp) launch(k_rate_lane<true, LM, false>, blocks, 32 * kLaneWarps, 0, s, c);
+      else launch(k_rate_lane<false, LM, false>, blocks, 32 * kLaneWarps, 0, s, c);
+    } else {  // weighted levels are CSR
+      constexpr int WW = lane_warps<true>();
+      unsigned blocks =
+          (unsigned)std::min<int64_t>((g->n + 256 * WW - 1) / (256 * WW), (int64_t)sms * 16);
+      launch(k_rate_lane<false, LM, true>, blocks, 32 * WW, 0, s, c);
+    }
     TP_LAUNCH_CHECK();
     if (prof) prof_end(PF_RATE_LANE, s, per_launch * tier_round_bytes(g, n_lane, T.edges[TIER_LANE]));
   }

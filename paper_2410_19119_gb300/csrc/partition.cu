@@ -42,12 +42,32 @@ __global__ void k_block_weights(const int32_t *part, const int64_t *vw, int64_t 
       if (hist[b]) atomicAdd((unsigned long long *)&B[b], (unsigned long long)hist[b]);
 }
 
+// Edge cut contributions of low-degree vertices, one thread per vertex.
 template <bool COMP>
-__global__ void k_cut(GView g, const int32_t *part, unsigned long long *out) {
+__global__ void k_cut_thread(GView g, const uint8_t *tier, const int32_t *part,
+                             unsigned long long *out) {
+  int64_t acc = 0;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < g.n;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t t = tier[u];
+    if (t != TIER_LANE && t != TIER_SMALL) continue;
+    const int32_t pu = part[u];
+    thread_neighbours<COMP>(g, u, [&](int32_t v, int64_t w) {
+      if (part[v] != pu) acc += w;
+    });
+  }
+  acc = warp_sum(acc);
+  if (lane_id() == 0 && acc) atomicAdd(out, (unsigned long long)acc);
+}
+
+// Edge cut contributions of the other vertices, one warp per vertex.
+template <bool COMP>
+__global__ void k_cut(GView g, const uint8_t *tier, const int32_t *part, unsigned long long *out) {
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   int64_t acc = 0;
   for (int64_t u = warp; u < g.n; u += nw) {
+    if (tier[u] == TIER_LANE || tier[u] == TIER_SMALL) continue;
     int32_t pu = part[u];
     warp_neighbours<COMP>(g, u, -1, [&](bool has, int32_t v, int64_t w) {
       if (has && part[v] != pu) acc += w;
@@ -78,9 +98,21 @@ int64_t edge_cut(const tp_graph *g, const int32_t *part, cudaStream_t s) {
   Buf<unsigned long long> acc(1, s);
   TP_CUDA(cudaMemsetAsync(acc.get(), 0, sizeof(unsigned long long), s));
   if (g->n) {
-    unsigned b = grid_for(g->n * 32, 256);
-    if (g->compressed) launch(k_cut<true>, b, 256, 0, s, view(g), part, acc.get());
-    else launch(k_cut<false>, b, 256, 0, s, view(g), part, acc.get());
+    if (!g->tiers.built) {
+      tp_params dp;
+      tp_params_default(&dp);
+      build_tiers(const_cast<tp_graph *>(g), dp, s);
+    }
+    const TierCache &T = g->tiers;
+    const uint8_t *tier = T.tier.get();
+    unsigned tb = grid_for(g->n, 256);
+    if (g->compressed) launch(k_cut_thread<true>, tb, 256, 0, s, view(g), tier, part, acc.get());
+    else launch(k_cut_thread<false>, tb, 256, 0, s, view(g), tier, part, acc.get());
+    if (T.n_mid + T.n_big + T.n_huge > 0) {
+      unsigned b = grid_for(g->n * 32, 256);
+      if (g->compressed) launch(k_cut<true>, b, 256, 0, s, view(g), tier, part, acc.get());
+      else launch(k_cut<false>, b, 256, 0, s, view(g), tier, part, acc.get());
+    }
     TP_LAUNCH_CHECK();
   }
   return (int64_t)(read_scalar(acc.get(), s) / 2);

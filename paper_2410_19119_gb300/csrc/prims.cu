@@ -1,6 +1,8 @@
 // Device-wide primitives: prefix scans and a stable LSD radix sort.
 // Hand-written for sm_103a; used by contraction, two-hop packing, tier lists
 // and initial partitioning.
+#include <climits>
+
 #include "tp_internal.cuh"
 
 namespace tp {
@@ -190,7 +192,26 @@ __global__ void k_sort_scatter(const uint64_t *keys, const uint64_t *vals, uint6
   }
 }
 
+__global__ void k_max_i64(const int64_t *d, int64_t n, unsigned long long *out) {
+  long long m = LLONG_MIN;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = d[i] > m ? d[i] : m;
+  m = warp_max(m);
+  if (lane_id() == 0) atomicMax((long long *)out, m);
+}
+
 }  // namespace
+
+int64_t max_i64(const int64_t *d, int64_t n, cudaStream_t s) {
+  if (n <= 0) return 0;
+  Buf<unsigned long long> out(1, s);
+  long long init = LLONG_MIN;
+  TP_CUDA(cudaMemcpyAsync(out.get(), &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  launch(k_max_i64, grid_for(n, 256, (int64_t)num_sms() * 8), 256, 0, s, d, n, out.get());
+  TP_LAUNCH_CHECK();
+  return (int64_t)read_scalar(out.get(), s);
+}
 
 void exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s) {
   scan<int64_t, int64_t, SumOp>(in, out, n, true, out + n, s);

@@ -88,7 +88,8 @@ struct Buf {
 // Degree tiers used by the rating kernels (performance only; the result of
 // a rating never depends on its tier).
 enum : uint8_t { TIER_SMALL = 0, TIER_MID = 1, TIER_BIG = 2, TIER_HUGE = 3, TIER_LANE = 4 };
-constexpr int kLaneMaxDeg = 32;  // lane tier: one lane per vertex, unit edge weights
+constexpr int kLaneMaxDeg = 32;  // lane tier: one lane per vertex
+constexpr int64_t kLaneMaxEdgeWeight = (int64_t)1 << 26;  // weighted lane tier: ratings fit 32 bits
 constexpr int64_t kChunkThreshold = 10000;  // compressed format: chunked above this degree
 constexpr int64_t kChunkSize = 1000;        // neighbours per chunk
 
@@ -117,6 +118,7 @@ struct tp_graph {
   int unit_vw = 1, unit_ew = 1;
   int64_t total_vw = 0;
   int64_t max_deg = 0;
+  int64_t max_ew = 1;  // largest edge weight (1 for unit weights)
   // CSR
   tp::Buf<int64_t> xadj;
   tp::Buf<int32_t> adj;
@@ -296,6 +298,7 @@ T read_scalar(const T *d, cudaStream_t s) {
   return h;
 }
 int bits_for(uint64_t max_value);  // bits needed to represent values <= max_value
+int64_t max_i64(const int64_t *d, int64_t n, cudaStream_t s);  // 0 for n == 0; synchronises
 
 // ---------------------------------------------------------------- graph helpers (graph.cu)
 tp_graph *new_graph();
