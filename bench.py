@@ -246,6 +246,22 @@ def run_lp_only(args, w):
     print(json.dumps({"lp_only": w["desc"], "n": n, "m2": len(adj)}))
 
 
+def run_partition_only(args, w):
+    """One compressed partition of the workload (for profiler captures)."""
+    import torch
+
+    import paper_2410_19119_gb300 as tp
+
+    xadj, adj = make_graph(w)
+    z = tp.graph_from_csr(xadj, adj).compress()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, st = tp.partition(z, w["k"], EPS, tp.default_params(seed=w["seed"]))
+    torch.cuda.synchronize()
+    st["wall_ms"] = (time.perf_counter() - t0) * 1e3
+    print(json.dumps({"partition_only": w["desc"], **st}))
+
+
 def run_native(args, w):
     import torch
 
@@ -416,10 +432,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lp-only", action="store_true",
                     help="run only the level-0 clustering once (profiler captures)")
+    ap.add_argument("--partition-only", action="store_true",
+                    help="compress and partition once, print the stats (profiler captures)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.lp_only:
         run_lp_only(args, w)
+    elif args.partition_only:
+        run_partition_only(args, w)
     elif args.impl == "reference":
         run_reference(args, w)
     else:

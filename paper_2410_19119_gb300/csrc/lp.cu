@@ -68,9 +68,11 @@ struct RateCtx {
   int64_t tbase;  // slot offset of this tier's tables inside tkeys/tvals
   const int64_t *chunk_start;
   int64_t n_chunks;
-  // lane tier in LP mode: this sub-round's bucket (null: filter every vertex)
+  // lane tier in LP mode: this round's buckets (null: hash every vertex);
+  // sub-round s holds bucket[bucket_off[s * nb] .. bucket_off[(s + 1) * nb])
   const int32_t *bucket;
-  const unsigned long long *bucket_cnt;  // [0..S) counts
+  const int64_t *bucket_off;
+  int64_t bucket_nb;
 };
 
 __device__ __forceinline__ int64_t node_w(const GView &g, int64_t u) { return g.vw ? g.vw[u] : 1; }
@@ -429,15 +431,16 @@ __global__ void __launch_bounds__(lane_warps<W>() * 32, W ? 1 : 4) k_rate_lane(R
   int64_t base = gw * 256;
   int j = 0;
   // bucket mode: this sub-round's lane-tier vertices come as a list
+  const bool list_mode = MODE == M_LP && c.bucket != nullptr;
   int64_t bstart = 0, bcount = 0, bnext = gw * 32;
-  if (MODE == M_LP && c.bucket) {
-    for (int k = 0; k < c.s; ++k) bstart += (int64_t)c.bucket_cnt[k];
-    bcount = (int64_t)c.bucket_cnt[c.s];
+  if (list_mode) {
+    bstart = c.bucket_off[(int64_t)c.s * c.bucket_nb];
+    bcount = c.bucket_off[(int64_t)(c.s + 1) * c.bucket_nb] - bstart;
     base = c.g.n;  // no slab scan
   }
   for (;;) {
-    if (MODE == M_LP && c.bucket && pending == 0 && bnext < bcount) {
-      int64_t i = bnext + lane;
+    if (list_mode && pending == 0 && bnext < bcount) {
+      const int64_t i = bnext + lane;
       if (i < bcount) queue[lane] = c.bucket[bstart + i];
       pending = (int)(bcount - bnext < 32 ? bcount - bnext : 32);
       bnext += nw * 32;
@@ -963,54 +966,64 @@ ApproveCtx approve_ctx(tp_graph *g, const LpState &st, LpWork &w) {
   return a;
 }
 
-// A3: lane-tier vertices of one round grouped by sub-round. Every block
-// owns a contiguous range of vertices and counts per sub-round in shared
-// memory, so there is one global atomic per (block, sub-round); inside a
-// bucket, ids stay in runs of nearby vertices (the order inside a bucket does
-// not affect results). Pass 0 counts, pass 1 writes.
-__global__ void k_bucket(const uint8_t *tier, int64_t n, uint64_t rk, int32_t S, bool fill,
-                         unsigned long long *cnt, int32_t *bucket) {
-  __shared__ unsigned long long local[32], base[32];
-  const int lane = lane_id();
-  const int64_t per_block = ((n + gridDim.x - 1) / gridDim.x + 31) & ~(int64_t)31;
-  const int64_t lo = (int64_t)blockIdx.x * per_block;
-  const int64_t hi = lo + per_block < n ? lo + per_block : n;
-  for (int k = threadIdx.x; k < 32; k += blockDim.x) local[k] = 0;
-  __syncthreads();
-  auto sweep = [&](bool write) {
-    for (int64_t b0 = lo + (threadIdx.x & ~31); b0 < hi; b0 += blockDim.x) {
-      const int64_t u = b0 + lane;
-      const bool lt = u < hi && tier[u] == TIER_LANE;
-      const int32_t sub = lt ? sub_round_of(hstep(rk, (uint64_t)u), S) : -1;
-      for (int32_t k = 0; k < S; ++k) {
-        const unsigned m = __ballot_sync(kFull, sub == k);
-        if (!m) continue;
-        unsigned long long at = 0;
-        if (lane == 0) at = atomicAdd(&local[k], (unsigned long long)__popc(m));
-        if (write) {
-          at = __shfl_sync(kFull, at, 0);
-          if (sub == k) bucket[base[k] + at + __popc(m & lanemask_lt())] = (int32_t)u;
-        }
-      }
+// A3: the lane-tier vertices of one round grouped by sub-round, in ascending
+// vertex order inside every sub-round. Block b owns vertices
+// [b * kBucketSpan, (b + 1) * kBucketSpan); pass 0 writes its count per
+// sub-round to cnt[s * nblocks + b], an exclusive scan turns the counts into
+// offsets, pass 1 writes every vertex at its offset plus its rank inside the
+// block (chunks of 32 vertices in order, ballot ranks inside a chunk).
+constexpr int kBucketSpan = 2048;
+constexpr int kBucketChunks = kBucketSpan / 32;
+
+__global__ void __launch_bounds__(256) k_bucket(const uint8_t *tier, int64_t n, uint64_t rk,
+                                                int32_t S, bool fill, int64_t *cnt,
+                                                int32_t *bucket) {
+  __shared__ int32_t chunk_cnt[kBucketChunks][32];  // [chunk][sub-round], S <= 32
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  const int64_t nblocks = gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * kBucketSpan;
+  int32_t sub_of[kBucketChunks / 8];
+  for (int q = 0; q < kBucketChunks / 8; ++q) {
+    const int chunk = w + 8 * q;
+    const int64_t u = lo + 32 * chunk + lane;
+    const bool lt = u < n && tier[u] == TIER_LANE;
+    const int32_t sub = lt ? sub_round_of(hstep(rk, (uint64_t)u), S) : -1;
+    sub_of[q] = sub;
+    for (int32_t k = 0; k < S; ++k) {
+      const unsigned m = __ballot_sync(kFull, sub == k);
+      if (lane == 0) chunk_cnt[chunk][k] = __popc(m);
     }
-  };
-  sweep(false);
+  }
   __syncthreads();
   if (!fill) {
-    for (int k = threadIdx.x; k < S; k += blockDim.x)
-      if (local[k]) atomicAdd(&cnt[k], local[k]);
+    for (int32_t k = threadIdx.x; k < S; k += blockDim.x) {
+      int64_t t = 0;
+      for (int ch = 0; ch < kBucketChunks; ++ch) t += chunk_cnt[ch][k];
+      cnt[(int64_t)k * nblocks + blockIdx.x] = t;
+    }
     return;
   }
-  if (threadIdx.x == 0) {
-    unsigned long long run = 0;
-    for (int32_t k = 0; k < S; ++k) {
-      base[k] = run + atomicAdd(&cnt[S + k], local[k]);  // bucket start + this block's slot
-      run += cnt[k];
-      local[k] = 0;
+  // exclusive prefix over the chunks of this block, per sub-round
+  if (threadIdx.x < S) {
+    const int k = threadIdx.x;
+    int32_t run = 0;
+    for (int ch = 0; ch < kBucketChunks; ++ch) {
+      const int32_t c = chunk_cnt[ch][k];
+      chunk_cnt[ch][k] = run;
+      run += c;
     }
   }
   __syncthreads();
-  sweep(true);
+  for (int q = 0; q < kBucketChunks / 8; ++q) {
+    const int chunk = w + 8 * q;
+    const int32_t sub = sub_of[q];
+    for (int32_t k = 0; k < S; ++k) {
+      const unsigned m = __ballot_sync(kFull, sub == k);
+      if (sub == k)
+        bucket[cnt[(int64_t)k * nblocks + blockIdx.x] + chunk_cnt[chunk][k] +
+               __popc(m & lanemask_lt())] = (int32_t)(lo + 32 * chunk + lane);
+    }
+  }
 }
 
 }  // namespace
@@ -1020,19 +1033,17 @@ void lp_bucket(tp_graph *g, LpWork &w, uint64_t rk, int32_t S, const tp_params &
   build_tiers(g, p, stream);
   w.bucket_S = 0;
   if (S > 32 || g->tiers.count[TIER_LANE] == 0) return;
-  if (!w.bucket.get()) {
-    w.bucket.alloc(std::max<int64_t>(w.n, 1), stream);
-    w.bucket_cnt.alloc(64, stream);
-  }
-  TP_CUDA(cudaMemsetAsync(w.bucket_cnt.get(), 0, 64 * sizeof(unsigned long long), stream));
-  // 2048 vertices per block: enough blocks to overlap the tier loads
-  const unsigned blocks = grid_for(g->n, 2048, (int64_t)1 << 20);
-  launch(k_bucket, blocks, 256, 0, stream, g->tiers.tier.get(), g->n, rk, S, false,
-         w.bucket_cnt.get(), w.bucket.get());
-  launch(k_bucket, blocks, 256, 0, stream, g->tiers.tier.get(), g->n, rk, S, true,
-         w.bucket_cnt.get(), w.bucket.get());
+  const int64_t nblocks = (g->n + kBucketSpan - 1) / kBucketSpan;
+  if (!w.bucket.get()) w.bucket.alloc(std::max<int64_t>(w.n, 1), stream);
+  if ((int64_t)w.bucket_off.n < S * nblocks + 1) w.bucket_off.alloc(S * nblocks + 1, stream);
+  launch(k_bucket, (unsigned)nblocks, 256, 0, stream, g->tiers.tier.get(), g->n, rk, S, false,
+         w.bucket_off.get(), w.bucket.get());
+  exclusive_scan_i64(w.bucket_off.get(), w.bucket_off.get(), S * nblocks, stream);
+  launch(k_bucket, (unsigned)nblocks, 256, 0, stream, g->tiers.tier.get(), g->n, rk, S, true,
+         w.bucket_off.get(), w.bucket.get());
   TP_LAUNCH_CHECK();
   w.bucket_S = S;
+  w.bucket_nblocks = nblocks;
 }
 
 void LpWork::init(int64_t n_vertices, int64_t n_labels, cudaStream_t s) {
@@ -1074,7 +1085,8 @@ void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t
   c.counters = (unsigned long long *)w.counters.get();
   if (w.bucket_S == S) {
     c.bucket = w.bucket.get();
-    c.bucket_cnt = w.bucket_cnt.get();
+    c.bucket_off = w.bucket_off.get();
+    c.bucket_nb = w.bucket_nblocks;
   }
   rate_tiers<M_LP>(g, c, p, stream);
   ApproveCtx a = approve_ctx(g, st, w);

@@ -325,10 +325,11 @@ struct LpWork {
   Buf<int32_t> cseg;        // n (contested mover indices grouped by target)
   Buf<int32_t> ctarget;     // nlabels (contested targets)
   Buf<int64_t> counters;    // [0] movers, [1] contested targets, [2] contested pool
-  // sub-round buckets of the lane tier for the current round (A3)
-  Buf<int32_t> bucket;               // n
-  Buf<unsigned long long> bucket_cnt;  // [0..S) counts, [S..2S) fill pointers
-  int32_t bucket_S = 0;              // S of the current buckets (0: none)
+  // lane-tier vertices of the current round grouped by sub-round (A3)
+  Buf<int32_t> bucket;       // n
+  Buf<int64_t> bucket_off;   // S * nblocks + 1 offsets (sub-round major)
+  int64_t bucket_nblocks = 0;
+  int32_t bucket_S = 0;      // S of the current buckets (0: none)
   void init(int64_t n_vertices, int64_t n_labels, cudaStream_t s);
 };
 void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t S, int32_t s,
