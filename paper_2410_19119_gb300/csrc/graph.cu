@@ -203,14 +203,22 @@ void compute_degrees(const tp_graph *g, int64_t *d_deg, cudaStream_t s) {
 // ---------------------------------------------------------------- tiers
 namespace {
 
+// Compressed graphs (off32 or off64 set) keep records longer than
+// kLaneMaxRecord bytes out of the lane tier.
 __global__ void k_classify(const int64_t *deg, int64_t n, int32_t lane_max, int32_t small_max,
-                           int32_t mid_max, uint8_t *tier, int32_t *flag_small, int32_t *flag_mid,
+                           int32_t mid_max, const uint32_t *off32, const uint64_t *off64,
+                           uint8_t *tier, int32_t *flag_small, int32_t *flag_mid,
                            int32_t *flag_big, int32_t *flag_huge, unsigned long long *stats) {
   int64_t e[5] = {0, 0, 0, 0, 0}, c[5] = {0, 0, 0, 0, 0};
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
        u += (int64_t)gridDim.x * blockDim.x) {
     int64_t d = deg[u];
-    uint8_t t = (lane_max > 0 && d <= lane_max) ? TIER_LANE
+    bool lane = lane_max > 0 && d <= lane_max;
+    if (lane && (off32 || off64)) {
+      const uint64_t len = off32 ? (uint64_t)(off32[u + 1] - off32[u]) : off64[u + 1] - off64[u];
+      lane = len <= (uint64_t)kLaneMaxRecord;
+    }
+    uint8_t t = lane ? TIER_LANE
                 : d <= small_max ? TIER_SMALL
                 : d <= mid_max ? TIER_MID
                 : d <= kChunkThreshold ? TIER_BIG
@@ -283,8 +291,10 @@ void build_tiers(tp_graph *g, const tp_params &p, cudaStream_t s) {
   Buf<int32_t> fs(n, s), fm(n, s), fb(n, s), fh(n, s);
   Buf<unsigned long long> te(10, s);
   TP_CUDA(cudaMemsetAsync(te.get(), 0, 10 * sizeof(unsigned long long), s));
+  const uint32_t *o32 = g->compressed && !g->off_is64 ? g->off32.get() : nullptr;
+  const uint64_t *o64 = g->compressed && g->off_is64 ? g->off64.get() : nullptr;
   launch(k_classify, grid_for(n, 256), 256, 0, s, deg.get(), n, lane_max, small_max, mid_max,
-         T.tier.get(), fs.get(), fm.get(), fb.get(), fh.get(), te.get());
+         o32, o64, T.tier.get(), fs.get(), fm.get(), fb.get(), fh.get(), te.get());
   TP_LAUNCH_CHECK();
   unsigned long long hte[10];
   TP_CUDA(cudaMemcpyAsync(hte, te.get(), sizeof(hte), cudaMemcpyDeviceToHost, s));

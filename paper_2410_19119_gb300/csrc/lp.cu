@@ -73,6 +73,8 @@ struct RateCtx {
   const int32_t *bucket;
   const int64_t *bucket_off;
   int64_t bucket_nb;
+  // lane tier: work-class thresholds (degree for CSR, record bytes compressed)
+  int64_t lane_cls[3];
 };
 
 __device__ __forceinline__ int64_t node_w(const GView &g, int64_t u) { return g.vw ? g.vw[u] : 1; }
@@ -302,21 +304,29 @@ __global__ void k_rate_small(RateCtx c) {
 }
 
 // ---------------------------------------------------------------- lane tier
-// Low-degree vertices of unit-edge-weight graphs, one lane per vertex, so a
-// warp keeps 32 neighbourhoods in flight:
-//   1. the active vertices of a 256-vertex slab are compacted onto lanes;
-//   2. each lane loads its offsets, then its whole record with 16-byte
-//      loads, and decodes header, first neighbour and gaps in registers
-//      (CSR: the adjacency words directly) into a per-lane column of shared
-//      memory;
-//   3. label gathers for all neighbours are issued back to back;
-//   4. the labels are sorted in registers (bitonic network of 32) so equal
-//      labels form runs whose lengths are the ratings (unit edge weights);
-//   5. runs are scanned for the own rating and the two best candidates by
-//      the rating order; the cap is checked lazily (a label-weight gather only
-//      for the winner, falling back to a full feasible scan if both top
-//      candidates are full).
+// Low-degree vertices, one lane per vertex, so a warp keeps 32
+// neighbourhoods in flight. Each warp step:
+//   1. fetches a window of up to 128 active vertices (this sub-round's
+//      bucket list, or a scan of 256-vertex slabs) and partitions it stably
+//      into four work classes (degree; compressed: record length), so each
+//      batch of 32 that follows has lanes of similar degree;
+//   2. per batch, every lane stages its compressed record in its own
+//      shared-memory column with independent 16-byte loads (the next batch's
+//      records are prefetched to L2 meanwhile), reads its degree from the
+//      record's and the next record's headers, and decodes its neighbours
+//      one VarInt at a time straight into label gathers held in registers
+//      (CSR: the adjacency entries directly), so every gather is in flight
+//      before the first one is used;
+//   3. the labels are sorted with Batcher's odd-even merge network of 16 or
+//      32 elements (picked per batch), so equal labels form runs whose
+//      lengths (summed weights) are the ratings;
+//   4. only the candidates tied at the top rating are hashed for the tie
+//      order; the cap is checked for the winner only, with a scan over all
+//      admissible candidates when the winner is full.
 constexpr int kLaneWarps = 8;
+constexpr int kLaneBlocksPerSM = 3;
+constexpr int kLaneWin = 128;             // vertices per warp step
+constexpr int kLaneQueue = kLaneWin + 32;  // slab scans append 32 at a time
 
 struct LaneCand {
   int32_t r;
@@ -328,85 +338,247 @@ __device__ __forceinline__ bool lane_better(const LaneCand &a, const LaneCand &b
   return better(a.r, a.t, a.x, b.r, b.t, b.x);
 }
 
-// Loads the neighbour ids of u into col[i * 32] (and, weighted, the edge
-// weights into wcol[i * 32]); returns the degree.
-template <bool COMP, bool W>
-__device__ __forceinline__ int lane_load(const GView &g, int64_t u, int32_t *col, uint32_t *wcol) {
-  int i = 0;
-  thread_neighbours<COMP>(g, u, [&](int32_t v, int64_t w) {
-    const int k = min(i, kLaneMaxDeg - 1);
-    col[k * 32] = v;
-    if (W) wcol[k * 32] = (uint32_t)w;
-    ++i;
-  });
-  return min(i, kLaneMaxDeg);
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-// Sorts a[0..N) ascending with a bitonic network (registers only).
+// Decodes u's compressed record into its shared-memory column: the raw
+// values (first the signed first neighbour, then the gaps) go to
+// col[i * 32]; returns the degree. The record (<= kLaneMaxRecord bytes) is
+// loaded at once as five 16-byte groups from its 16-byte aligned start, so
+// no load waits on another, and consumed a 32-bit word at a time. Bytes
+// before the record are turned into value ends and, like the header, are
+// written to slot 0, which the first neighbour then overwrites; bytes after
+// it are turned into continuation bytes, so they end no value.
+__device__ __forceinline__ int lane_decode(const GView &g, int32_t u, uint32_t *col) {
+  constexpr int G = 5;  // 80-byte window
+  const uint64_t b = off_at(g, u), e = off_at(g, u + 1);
+  const uint64_t ws = b & ~(uint64_t)15;
+  const int p0 = (int)(b - ws), endp = (int)(e - ws);
+  const uint4 *src = reinterpret_cast<const uint4 *>(g.bytes + ws);
+  uint4 q[G];
+#pragma unroll
+  for (int j = 0; j < G; ++j) q[j] = 16 * j < endp ? __ldcs(src + j) : make_uint4(0, 0, 0, 0);
+  int fi = 0;  // words of q[0] already taken
+  auto pop = [&]() -> uint32_t {
+    const uint32_t w = fi == 0 ? q[0].x : fi == 1 ? q[0].y : fi == 2 ? q[0].z : q[0].w;
+    if (++fi == 4) {
+#pragma unroll
+      for (int j = 0; j + 1 < G; ++j) q[j] = q[j + 1];
+      fi = 0;
+    }
+    return w;
+  };
+  int wi = p0 >> 2;
+  for (int j = 0; j < wi; ++j) pop();
+  // leading bytes of the first word: forced value ends
+  uint32_t lead = 0x80808080u & ((1u << (8 * (p0 & 3))) - 1u);
+  int idx = -1 - (p0 & 3);  // value index; < 0 for the leading bytes and the header
+  uint32_t acc = 0;
+  int accb = 0;
+  for (; 4 * wi < endp; ++wi) {
+    uint32_t w = pop() & ~lead;
+    lead = 0;
+    const int vhi = endp - 4 * wi;  // bytes of this word inside the record
+    if (vhi < 4) w |= 0x80808080u & ~((1u << (8 * vhi)) - 1u);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t by = (w >> (8 * j)) & 0xffu;
+      acc |= (by & 0x7fu) << accb;
+      accb += 7;
+      if (!(by & 0x80u)) {
+        col[max(idx, 0) * 32] = acc;
+        ++idx;
+        acc = 0;
+        accb = 0;
+      }
+    }
+  }
+  return min(max(idx, 0), kLaneMaxDeg);
+}
+
+// Work class 0..3 of a lane-tier vertex: its degree (CSR) or record length
+// in bytes (compressed) against three ascending thresholds.
+template <bool COMP>
+__device__ __forceinline__ int lane_class(const RateCtx &c, int64_t u) {
+  const int64_t len = COMP ? (int64_t)(off_at(c.g, u + 1) - off_at(c.g, u))
+                           : c.g.xadj[u + 1] - c.g.xadj[u];
+  return (len > c.lane_cls[0]) + (len > c.lane_cls[1]) + (len > c.lane_cls[2]);
+}
+
+template <bool COMP>
+__device__ __forceinline__ void lane_prefetch(const GView &g, int64_t u) {
+  if (COMP) {
+    const uint64_t b = off_at(g, u), e = off_at(g, u + 1);
+    prefetch_l2(g.bytes + b);
+    prefetch_l2(g.bytes + e);
+  } else {
+    const int64_t b = g.xadj[u], e = g.xadj[u + 1];
+    if (e > b) {
+      prefetch_l2(g.adj + b);
+      prefetch_l2(g.adj + e - 1);
+    }
+  }
+}
+
+// Batcher's odd-even merge sort of a[0..N), ascending (N a power of two;
+// 63 comparators for 16 elements, 191 for 32), registers only. The network
+// is generated by template recursion so every index is a constant.
+template <class T>
+__device__ __forceinline__ void cmp_swap(T &x, T &y) {
+  const T lo = min(x, y), hi = max(x, y);
+  x = lo;
+  y = hi;
+}
+
+// Merges the two sorted halves of the subsequence a[LO], a[LO + R], ...
+template <int LO, int N, int R, class T>
+__device__ __forceinline__ void oem_merge(T (&a)[kLaneMaxDeg]) {
+  constexpr int M = 2 * R;
+  if constexpr (M < N) {
+    oem_merge<LO, N, M>(a);
+    oem_merge<LO + R, N, M>(a);
+#pragma unroll
+    for (int i = LO + R; i + R < LO + N; i += M) cmp_swap(a[i], a[i + R]);
+  } else {
+    cmp_swap(a[LO], a[LO + R]);
+  }
+}
+
+template <int LO, int N, class T>
+__device__ __forceinline__ void oem_sort_range(T (&a)[kLaneMaxDeg]) {
+  if constexpr (N > 1) {
+    oem_sort_range<LO, N / 2>(a);
+    oem_sort_range<LO + N / 2, N / 2>(a);
+    oem_merge<LO, N, 1>(a);
+  }
+}
+
 template <int N, class T>
-__device__ __forceinline__ void bitonic_sort(T (&a)[kLaneMaxDeg]) {
-#pragma unroll
-  for (int k = 2; k <= N; k <<= 1) {
-#pragma unroll
-    for (int jd = k >> 1; jd > 0; jd >>= 1) {
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        const int l = i ^ jd;
-        if (l > i) {
-          const T lo = min(a[i], a[l]), hi = max(a[i], a[l]);
-          if ((i & k) == 0) a[i] = lo, a[l] = hi;
-          else a[i] = hi, a[l] = lo;
-        }
-      }
-    }
-  }
+__device__ __forceinline__ void oem_sort(T (&a)[kLaneMaxDeg]) {
+  oem_sort_range<0, N>(a);
 }
 
-// Sorted labels -> (label, rating) pairs compacted to the front of the
-// columns; returns the number of distinct labels (padding excluded).
-// Unit weights: a[i] is a label, the rating is the run length. Weighted:
-// a[i] = label << 32 | weight, the rating is the sum of the run's weights.
-template <int N, bool W, class T>
-__device__ __forceinline__ int runs_to_column(const T (&a)[kLaneMaxDeg], int32_t *col,
-                                              uint8_t *cnt, uint32_t *rcol) {
-  int k = 0;
-  uint32_t run = 0;
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    const int32_t x = W ? (int32_t)((uint64_t)a[i] >> 32) : (int32_t)a[i];
-    run += W ? (uint32_t)((uint64_t)a[i] & 0xffffffffu) : 1u;
-    const int32_t nx = i + 1 == N ? INT32_MAX
-                                  : (W ? (int32_t)((uint64_t)a[i + 1] >> 32) : (int32_t)a[i + 1]);
-    if (nx != x) {
-      if (x != INT32_MAX) {
-        col[k * 32] = x;
-        if (W) rcol[k * 32] = run;
-        else cnt[k * 32] = (uint8_t)run;
-        ++k;
-      }
-      run = 0;
-    }
-  }
-  return k;
-}
-
-template <int N, bool W>
-__device__ __forceinline__ int sort_runs(int deg, int32_t *col, uint8_t *cnt, uint32_t *wcol) {
-  if constexpr (W) {
-    // padding: label INT32_MAX, weight 0 (sorts last, skipped as a run)
+// Rates one batch: this lane's vertex u with deg neighbours (compressed:
+// already decoded into the column; CSR: adjacency from xadj[u]) and emits
+// the move or favourite. N >= the largest degree of the batch.
+template <bool COMP, int MODE, bool W, int N>
+__device__ __forceinline__ void lane_batch(const RateCtx &c, bool has, int32_t u, int deg,
+                                           uint32_t *col, uint32_t *wcol, uint8_t *cnt) {
+  const int32_t own = has ? c.label[u] : -1;
+  int32_t rown = 0, rmax = 0;
+  int ncand = 0;
+  int32_t *ccol = reinterpret_cast<int32_t *>(col);
+  // gather, sort, and turn runs into (label, rating) pairs without own
+  if constexpr (W) {  // weighted levels are CSR
+    // label << 32 | weight; padding: label INT32_MAX, weight 0
     constexpr uint64_t kPad = (uint64_t)INT32_MAX << 32;
+    const int64_t b = has ? c.g.xadj[u] : 0;
     uint64_t a[kLaneMaxDeg];
 #pragma unroll
     for (int i = 0; i < N; ++i)
-      a[i] = i < deg ? ((uint64_t)(uint32_t)col[i * 32] << 32) | wcol[i * 32] : kPad;
-    bitonic_sort<N>(a);
-    return runs_to_column<N, true>(a, col, cnt, wcol);
+      a[i] = i < deg ? ((uint64_t)(uint32_t)__ldg(c.label + __ldcs(c.g.adj + b + i)) << 32) |
+                           (uint32_t)__ldcs(c.g.ew + b + i)
+                     : kPad;
+    oem_sort<N>(a);
+    uint32_t run = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int32_t x = (int32_t)(a[i] >> 32);
+      run += (uint32_t)a[i];
+      const bool end = i + 1 == N || (int32_t)(a[i + 1] >> 32) != x;
+      const bool real = end && x != INT32_MAX;
+      const bool cand = real && x != own;
+      ccol[ncand * 32] = x;
+      wcol[ncand * 32] = run;
+      rown = real && !cand ? (int32_t)run : rown;
+      rmax = cand ? max(rmax, (int32_t)run) : rmax;
+      ncand += cand;
+      run = end ? 0u : run;
+    }
   } else {
     int32_t a[kLaneMaxDeg];
+    if constexpr (COMP) {
+      // raw values -> neighbour ids (first: signed offset from u, then gaps)
+      const uint32_t nmax = (uint32_t)(c.g.n - 1);
+      int32_t prev = u;
 #pragma unroll
-    for (int i = 0; i < N; ++i) a[i] = i < deg ? col[i * 32] : INT32_MAX;
-    bitonic_sort<N>(a);
-    return runs_to_column<N, false>(a, col, cnt, wcol);
+      for (int i = 0; i < N; ++i) {
+        const uint32_t v = col[i * 32];
+        int32_t x = i == 0 ? ((v & 1u) ? u - (int32_t)(v >> 1) : u + (int32_t)(v >> 1))
+                           : prev + (int32_t)v;
+        // streams are validated on creation; the clamp only keeps a
+        // corrupted one from reading out of bounds
+        x = (int32_t)min((uint32_t)x, nmax);
+        prev = x;
+        a[i] = i < deg ? __ldg(c.label + x) : INT32_MAX;
+      }
+    } else {
+      const int64_t b = has ? c.g.xadj[u] : 0;
+#pragma unroll
+      for (int i = 0; i < N; ++i) a[i] = i < deg ? __ldg(c.label + __ldcs(c.g.adj + b + i)) : INT32_MAX;
+    }
+    oem_sort<N>(a);
+    // branch-free run scan: every position writes slot ncand, which only
+    // advances past a candidate (later writes overwrite the others)
+    int start = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const bool end = i + 1 == N || a[i + 1] != a[i];
+      const int32_t run = i + 1 - start;
+      const bool real = end && a[i] != INT32_MAX;
+      const bool cand = real && a[i] != own;
+      ccol[ncand * 32] = a[i];
+      cnt[ncand * 32] = (uint8_t)run;
+      rown = real && !cand ? run : rown;
+      rmax = cand ? max(rmax, run) : rmax;
+      ncand += cand;
+      start = end ? i + 1 : start;
+    }
+  }
+  auto rating = [&](int k) -> int32_t { return W ? (int32_t)wcol[k * 32] : (int32_t)cnt[k * 32]; };
+  const int64_t cu = has ? node_w(c.g, u) : 1;
+  LaneCand best{-1, 0xffffffffu, INT32_MAX};
+  if (MODE == M_FAV ? rmax > 0 : rmax > rown) {
+    const uint64_t hv = tie_key<MODE>(c, u);
+    // the best candidate overall is tied at the top rating
+    LaneCand b1{-1, 0xffffffffu, INT32_MAX};
+    for (int k = 0; k < ncand; ++k) {
+      if (rating(k) != rmax) continue;
+      const int32_t x = ccol[k * 32];
+      const LaneCand cand{rmax, tie_hash(hv, x), x};
+      if (lane_better(cand, b1)) b1 = cand;
+    }
+    if (MODE == M_FAV || c.lw[b1.x] + cu <= c.cap) {
+      best = b1;
+    } else {
+      // the winner is full: the best admissible candidate that improves
+      for (int k = 0; k < ncand; ++k) {
+        const int32_t r = rating(k);
+        const int32_t x = ccol[k * 32];
+        if (r <= rown || x == b1.x) continue;
+        const LaneCand cand{r, tie_hash(hv, x), x};
+        if (lane_better(cand, best) && c.lw[x] + cu <= c.cap) best = cand;
+      }
+    }
+  }
+  if (MODE == M_FAV) {
+    if (has) c.fav[u] = best.r > 0 ? best.x : (int32_t)c.g.n;
+  } else {
+    const bool mv = has && best.r > rown;
+    const unsigned mm = __ballot_sync(kFull, mv);
+    if (mm) {
+      unsigned long long basep = 0;
+      if (lane_id() == 0) basep = atomicAdd(c.counters, (unsigned long long)__popc(mm));
+      basep = __shfl_sync(kFull, basep, 0);
+      if (mv) {
+        const unsigned long long at = basep + __popc(mm & lanemask_lt());
+        c.mv_u[at] = u;
+        c.mv_t[at] = best.x;
+        c.mv_g[at] = best.r - rown;
+        atomicAdd((unsigned long long *)&c.in_w[best.x], (unsigned long long)cu);
+      }
+    }
   }
 }
 
@@ -414,122 +586,106 @@ template <bool W>
 __host__ __device__ constexpr int lane_warps() { return W ? 4 : kLaneWarps; }
 
 template <bool COMP, int MODE, bool W>
-__global__ void __launch_bounds__(lane_warps<W>() * 32, W ? 1 : 4) k_rate_lane(RateCtx c) {
+__global__ void __launch_bounds__(lane_warps<W>() * 32, W ? 1 : kLaneBlocksPerSM)
+    k_rate_lane(RateCtx c) {
+  static_assert(!(COMP && W), "weighted levels are CSR");
   constexpr int WARPS = lane_warps<W>();
-  __shared__ int32_t lab_all[WARPS][kLaneMaxDeg][32];
-  __shared__ uint32_t aux_all[WARPS][W ? kLaneMaxDeg : 1][32];  // weights, then ratings
-  __shared__ uint8_t cnt_all[WARPS][W ? 1 : kLaneMaxDeg][32];   // ratings (unit weights)
-  __shared__ int32_t queue_all[WARPS][64];
+  // per lane: staged record words, then candidate labels
+  __shared__ uint32_t lab_all[WARPS][kLaneMaxDeg][32];
+  __shared__ uint32_t aux_all[WARPS][W ? kLaneMaxDeg : 1][32];  // candidate ratings (weighted)
+  __shared__ uint8_t cnt_all[WARPS][W ? 1 : kLaneMaxDeg][32];   // candidate ratings (unit)
+  __shared__ int32_t queue_all[WARPS][kLaneQueue];
   const int lane = lane_id(), w = threadIdx.x >> 5;
-  int32_t *col = &lab_all[w][0][lane];
+  uint32_t *col = &lab_all[w][0][lane];
   uint32_t *wcol = &aux_all[w][0][lane];
   uint8_t *cnt = &cnt_all[w][0][lane];
   int32_t *queue = queue_all[w];
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  int pending = 0;  // active vertices queued for this warp (warp-uniform)
-  int64_t base = gw * 256;
-  int j = 0;
+  // warps and list positions fit 32 bits (lists hold < 2^31 vertex ids)
+  const int32_t gw = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int32_t nw = (int32_t)((gridDim.x * blockDim.x) >> 5);
   // bucket mode: this sub-round's lane-tier vertices come as a list
   const bool list_mode = MODE == M_LP && c.bucket != nullptr;
-  int64_t bstart = 0, bcount = 0, bnext = gw * 32;
+  int32_t bcount = 0, bnext = gw * kLaneWin;
+  const int32_t *blist = c.bucket;
+  int64_t base = (int64_t)gw * 256;
+  int j8 = 0, pending = 0;  // slab scan position; queued vertices (warp-uniform)
   if (list_mode) {
-    bstart = c.bucket_off[(int64_t)c.s * c.bucket_nb];
-    bcount = c.bucket_off[(int64_t)(c.s + 1) * c.bucket_nb] - bstart;
+    const int64_t bstart = c.bucket_off[(int64_t)c.s * c.bucket_nb];
+    bcount = (int32_t)(c.bucket_off[(int64_t)(c.s + 1) * c.bucket_nb] - bstart);
+    blist += bstart;
     base = c.g.n;  // no slab scan
   }
   for (;;) {
-    if (list_mode && pending == 0 && bnext < bcount) {
-      const int64_t i = bnext + lane;
-      if (i < bcount) queue[lane] = c.bucket[bstart + i];
-      pending = (int)(bcount - bnext < 32 ? bcount - bnext : 32);
-      bnext += nw * 32;
-    }
-    // otherwise fill the queue, 32 vertices of the current 256-vertex slab at a time
-    while (pending < 32 && base < c.g.n) {
-      int64_t v = base + 32 * j + lane;
-      bool act = v < c.g.n && c.tier[v] == TIER_LANE && active<MODE>(c, v);
-      unsigned m = __ballot_sync(kFull, act);
-      if (act) queue[pending + __popc(m & lanemask_lt())] = (int32_t)v;
-      pending += __popc(m);
-      if (++j == 8) j = 0, base += nw * 256;
-    }
-    if (pending == 0) break;
-    __syncwarp();
-    // one batch: up to 32 queued vertices, one per lane
-    const int take = pending < 32 ? pending : 32;
-    const bool has = lane < take;
-    const int64_t u = has ? queue[lane] : 0;
-    __syncwarp();
-    if (pending > 32 && lane < pending - 32) queue[lane] = queue[32 + lane];
-    __syncwarp();
-    pending -= take;
-    int deg = 0;
-    if (has) deg = lane_load<COMP, W>(c.g, u, col, wcol);
-    // label gathers, independent loads
-#pragma unroll 4
-    for (int i = 0; i < deg; ++i) col[i * 32] = __ldg(c.label + col[i * 32]);
-    // ratings: sort the labels; runs of equal labels give the ratings
-    const int maxdeg = __reduce_max_sync(kFull, (unsigned)deg);
-    const int ncand = maxdeg <= 16 ? sort_runs<16, W>(deg, col, cnt, wcol)
-                                   : sort_runs<kLaneMaxDeg, W>(deg, col, cnt, wcol);
-    // own rating and the two best candidates
-    const int32_t own = has ? c.label[u] : -1;
-    const int64_t cu = has ? node_w(c.g, u) : 1;
-    const uint64_t hv = has ? tie_key<MODE>(c, u) : 0;
-    LaneCand b1{-1, 0xffffffffu, INT32_MAX}, b2{-1, 0xffffffffu, INT32_MAX};
-    int32_t rown = 0;
-    for (int k = 0; k < ncand; ++k) {
-      const int32_t x = col[k * 32];
-      const int32_t r = W ? (int32_t)wcol[k * 32] : (int32_t)cnt[k * 32];
-      if (x == own) {
-        rown = r;
-        continue;
+    int take;
+    int32_t e[4];
+    if (list_mode) {
+      if (bnext >= bcount) break;
+      take = bcount - bnext < kLaneWin ? bcount - bnext : kLaneWin;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int i = lane + 32 * j;
+        e[j] = i < take ? blist[bnext + i] : -1;
       }
-      if (r < b2.r) continue;  // cannot enter the top two
-      LaneCand cand{r, tie_hash(hv, x), x};
-      if (lane_better(cand, b1)) b2 = b1, b1 = cand;
-      else if (lane_better(cand, b2)) b2 = cand;
-    }
-    // lazy cap check
-    LaneCand best{-1, 0xffffffffu, INT32_MAX};
-    if (MODE == M_FAV) {
-      best = b1;
-    } else if (b1.r > 0) {
-      if (c.lw[b1.x] + cu <= c.cap) {
-        best = b1;
-      } else if (b2.r > 0 && c.lw[b2.x] + cu <= c.cap) {
-        best = b2;
-      } else if (b2.r > 0) {
-        // both leaders are full: the best admissible among the rest
-        for (int k = 0; k < ncand; ++k) {
-          const int32_t x = col[k * 32];
-          if (x == own || x == b1.x || x == b2.x) continue;
-          const int32_t r = W ? (int32_t)wcol[k * 32] : (int32_t)cnt[k * 32];
-          LaneCand cand{r, tie_hash(hv, x), x};
-          if (lane_better(cand, best) && c.lw[x] + cu <= c.cap) best = cand;
-        }
-      }
-    }
-    if (MODE == M_FAV) {
-      if (has) c.fav[u] = best.r > 0 ? best.x : (int32_t)c.g.n;
+      // never step past the end (keeps bnext below 2^31)
+      bnext = bcount - bnext > nw * kLaneWin ? bnext + nw * kLaneWin : bcount;
     } else {
-      bool mv = has && best.r > rown;
-      unsigned mm = __ballot_sync(kFull, mv);
-      if (mm) {
-        unsigned long long basep = 0;
-        if (lane == 0) basep = atomicAdd(c.counters, (unsigned long long)__popc(mm));
-        basep = __shfl_sync(kFull, basep, 0);
-        if (mv) {
-          unsigned long long at = basep + __popc(mm & lanemask_lt());
-          c.mv_u[at] = (int32_t)u;
-          c.mv_t[at] = best.x;
-          c.mv_g[at] = best.r - rown;
-          atomicAdd((unsigned long long *)&c.in_w[best.x], (unsigned long long)cu);
-        }
+      // fill the queue, 32 vertices of the current 256-vertex slab at a time
+      while (pending < kLaneWin && base < c.g.n) {
+        const int64_t v = base + 32 * j8 + lane;
+        const bool act = v < c.g.n && c.tier[v] == TIER_LANE && active<MODE>(c, v);
+        const unsigned m = __ballot_sync(kFull, act);
+        if (act) queue[pending + __popc(m & lanemask_lt())] = (int32_t)v;
+        pending += __popc(m);
+        if (++j8 == 8) j8 = 0, base += (int64_t)nw * 256;
+      }
+      if (pending == 0) break;
+      __syncwarp();
+      take = pending < kLaneWin ? pending : kLaneWin;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int i = lane + 32 * j;
+        e[j] = i < take ? queue[i] : -1;
+      }
+      __syncwarp();
+    }
+    // stable partition of the window into work classes
+    int cls[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) cls[j] = e[j] >= 0 ? lane_class<COMP>(c, e[j]) : 4;
+    int cursor = 0;
+#pragma unroll
+    for (int cl = 0; cl < 4; ++cl) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool m = cls[j] == cl;
+        const unsigned b = __ballot_sync(kFull, m);
+        if (m) queue[cursor + __popc(b & lanemask_lt())] = e[j];
+        cursor += __popc(b);
       }
     }
     __syncwarp();
+    for (int q = 0; q < take; q += 32) {
+      const bool has = q + lane < take;
+      const int32_t u = has ? queue[q + lane] : 0;
+      if (q + 32 + lane < take) lane_prefetch<COMP>(c.g, queue[q + 32 + lane]);
+      int deg = 0;
+      if (has) {
+        if (COMP) deg = lane_decode(c.g, u, col);
+        else deg = min((int)(c.g.xadj[u + 1] - c.g.xadj[u]), kLaneMaxDeg);
+      }
+      const unsigned maxdeg = __reduce_max_sync(kFull, (unsigned)deg);
+      if (maxdeg <= 16) lane_batch<COMP, MODE, W, 16>(c, has, u, deg, col, wcol, cnt);
+      else lane_batch<COMP, MODE, W, kLaneMaxDeg>(c, has, u, deg, col, wcol, cnt);
+    }
+    __syncwarp();
+    if (!list_mode) {  // slab scans: move the vertices beyond the window to the front
+      const int left = pending - take;
+      const int32_t t = lane < left ? queue[take + lane] : 0;
+      __syncwarp();
+      if (lane < left) queue[lane] = t;
+      __syncwarp();
+      pending = left;
+    }
   }
 }
 
@@ -838,9 +994,17 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
   if (n_lane > 0) {
     if (prof) prof_begin(PF_RATE_LANE, s);
     constexpr int LM = MODE == M_REBAL ? M_LP : MODE;
+    // work classes: degree <= 8, 16, 24 (compressed: the record length those
+    // degrees take at this stream's bytes per adjacency entry)
+    for (int i = 0; i < 3; ++i) {
+      const int64_t d = 8 * (i + 1);
+      c.lane_cls[i] = comp && g->m2 > 0
+                          ? (int64_t)((double)d * (double)g->nbytes / (double)g->m2 + 0.5)
+                          : d;
+    }
     if (g->unit_ew) {
       unsigned blocks = (unsigned)std::min<int64_t>(
-          (g->n + 256 * kLaneWarps - 1) / (256 * kLaneWarps), (int64_t)sms * 8);
+          (g->n + 256 * kLaneWarps - 1) / (256 * kLaneWarps), (int64_t)sms * kLaneBlocksPerSM);
       if (comp) launch(k_rate_lane<true, LM, false>, blocks, 32 * kLaneWarps, 0, s, c);
       else launch(k_rate_lane<false, LM, false>, blocks, 32 * kLaneWarps, 0, s, c);
     } else {  // weighted levels are CSR

@@ -89,6 +89,9 @@ struct Buf {
 // a rating never depends on its tier).
 enum : uint8_t { TIER_SMALL = 0, TIER_MID = 1, TIER_BIG = 2, TIER_HUGE = 3, TIER_LANE = 4 };
 constexpr int kLaneMaxDeg = 32;  // lane tier: one lane per vertex
+// Compressed lane tier: records of at most this many bytes, so a record fits
+// an 80-byte window from its 16-byte aligned start.
+constexpr int kLaneMaxRecord = 65;
 constexpr int64_t kLaneMaxEdgeWeight = (int64_t)1 << 26;  // weighted lane tier: ratings fit 32 bits
 constexpr int64_t kChunkThreshold = 10000;  // compressed format: chunked above this degree
 constexpr int64_t kChunkSize = 1000;        // neighbours per chunk
