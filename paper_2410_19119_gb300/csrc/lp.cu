@@ -322,7 +322,9 @@ __global__ void k_rate_small(RateCtx c) {
 //      lengths (summed weights) are the ratings;
 //   4. only the candidates tied at the top rating are hashed for the tie
 //      order; the cap is checked for the winner only, with a scan over all
-//      admissible candidates when the winner is full.
+//      admissible candidates when the winner is full;
+//   5. the window's movers are collected in shared memory and written out
+//      with one atomic per window.
 constexpr int kLaneWarps = 8;
 constexpr int kLaneBlocksPerSM = 3;
 constexpr int kLaneWin = 128;             // vertices per warp step
@@ -459,12 +461,19 @@ __device__ __forceinline__ void oem_sort(T (&a)[kLaneMaxDeg]) {
   oem_sort_range<0, N>(a);
 }
 
+// Mover records of one warp's window, written out with one atomic per window.
+struct LaneMovers {
+  int32_t u[kLaneWin], t[kLaneWin], g[kLaneWin];
+};
+
 // Rates one batch: this lane's vertex u with deg neighbours (compressed:
 // already decoded into the column; CSR: adjacency from xadj[u]) and emits
-// the move or favourite. N >= the largest degree of the batch.
+// the favourite, or queues the move in the warp's window buffer (nmv
+// records so far, warp-uniform). N >= the largest degree of the batch.
 template <bool COMP, int MODE, bool W, int N>
 __device__ __forceinline__ void lane_batch(const RateCtx &c, bool has, int32_t u, int deg,
-                                           uint32_t *col, uint32_t *wcol, uint8_t *cnt) {
+                                           uint32_t *col, uint32_t *wcol, uint8_t *cnt,
+                                           LaneMovers &mb, int &nmv) {
   const int32_t own = has ? c.label[u] : -1;
   int32_t rown = 0, rmax = 0;
   int ncand = 0;
@@ -567,18 +576,14 @@ __device__ __forceinline__ void lane_batch(const RateCtx &c, bool has, int32_t u
   } else {
     const bool mv = has && best.r > rown;
     const unsigned mm = __ballot_sync(kFull, mv);
-    if (mm) {
-      unsigned long long basep = 0;
-      if (lane_id() == 0) basep = atomicAdd(c.counters, (unsigned long long)__popc(mm));
-      basep = __shfl_sync(kFull, basep, 0);
-      if (mv) {
-        const unsigned long long at = basep + __popc(mm & lanemask_lt());
-        c.mv_u[at] = u;
-        c.mv_t[at] = best.x;
-        c.mv_g[at] = best.r - rown;
-        atomicAdd((unsigned long long *)&c.in_w[best.x], (unsigned long long)cu);
-      }
+    if (mv) {
+      const int at = nmv + __popc(mm & lanemask_lt());
+      mb.u[at] = u;
+      mb.t[at] = best.x;
+      mb.g[at] = best.r - rown;
+      atomicAdd((unsigned long long *)&c.in_w[best.x], (unsigned long long)cu);
     }
+    nmv += __popc(mm);
   }
 }
 
@@ -595,11 +600,13 @@ __global__ void __launch_bounds__(lane_warps<W>() * 32, W ? 1 : kLaneBlocksPerSM
   __shared__ uint32_t aux_all[WARPS][W ? kLaneMaxDeg : 1][32];  // candidate ratings (weighted)
   __shared__ uint8_t cnt_all[WARPS][W ? 1 : kLaneMaxDeg][32];   // candidate ratings (unit)
   __shared__ int32_t queue_all[WARPS][kLaneQueue];
+  __shared__ LaneMovers movers_all[WARPS];
   const int lane = lane_id(), w = threadIdx.x >> 5;
   uint32_t *col = &lab_all[w][0][lane];
   uint32_t *wcol = &aux_all[w][0][lane];
   uint8_t *cnt = &cnt_all[w][0][lane];
   int32_t *queue = queue_all[w];
+  LaneMovers &mb = movers_all[w];
   // warps and list positions fit 32 bits (lists hold < 2^31 vertex ids)
   const int32_t gw = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int32_t nw = (int32_t)((gridDim.x * blockDim.x) >> 5);
@@ -664,6 +671,7 @@ __global__ void __launch_bounds__(lane_warps<W>() * 32, W ? 1 : kLaneBlocksPerSM
       }
     }
     __syncwarp();
+    int nmv = 0;  // movers of this window so far (warp-uniform)
     for (int q = 0; q < take; q += 32) {
       const bool has = q + lane < take;
       const int32_t u = has ? queue[q + lane] : 0;
@@ -674,10 +682,21 @@ __global__ void __launch_bounds__(lane_warps<W>() * 32, W ? 1 : kLaneBlocksPerSM
         else deg = min((int)(c.g.xadj[u + 1] - c.g.xadj[u]), kLaneMaxDeg);
       }
       const unsigned maxdeg = __reduce_max_sync(kFull, (unsigned)deg);
-      if (maxdeg <= 16) lane_batch<COMP, MODE, W, 16>(c, has, u, deg, col, wcol, cnt);
-      else lane_batch<COMP, MODE, W, kLaneMaxDeg>(c, has, u, deg, col, wcol, cnt);
+      if (maxdeg <= 16) lane_batch<COMP, MODE, W, 16>(c, has, u, deg, col, wcol, cnt, mb, nmv);
+      else lane_batch<COMP, MODE, W, kLaneMaxDeg>(c, has, u, deg, col, wcol, cnt, mb, nmv);
     }
     __syncwarp();
+    if (nmv) {  // the window's movers, coalesced
+      unsigned long long basep = 0;
+      if (lane == 0) basep = atomicAdd(c.counters, (unsigned long long)nmv);
+      basep = __shfl_sync(kFull, basep, 0);
+      for (int i = lane; i < nmv; i += 32) {
+        c.mv_u[basep + i] = mb.u[i];
+        c.mv_t[basep + i] = mb.t[i];
+        c.mv_g[basep + i] = mb.g[i];
+      }
+      __syncwarp();
+    }
     if (!list_mode) {  // slab scans: move the vertices beyond the window to the front
       const int left = pending - take;
       const int32_t t = lane < left ? queue[take + lane] : 0;
