@@ -45,6 +45,10 @@ WORKLOADS = {
     "rmat26": dict(gen="rmat", scale=26, ef=16, k=256, seed=1,
                    desc="R-MAT scale 26 edge factor 16 (0.57,0.19,0.19,0.05), symmetrised, "
                         "deduplicated, k=256, eps=0.03, seed 1; compressed with chunking and CSR"),
+    "batch4096": dict(gen="batch", count=4096, seed=1,
+                      desc="batched: 4096 independent graphs, n log-uniform in [2^8, 2^16], "
+                           "G(n,m) deg 8 / RGG-2D deg 12 / RHG deg 16 gamma 2.8 in turn, k in "
+                           "{2,4,8,16,32} per graph, eps=0.03, seed 1; int32 CSR"),
 }
 EPS = 0.03
 FALLBACK_HBM_GBS = 6800.0
@@ -246,6 +250,115 @@ def run_lp_only(args, w):
     print(json.dumps({"lp_only": w["desc"], "n": n, "m2": len(adj)}))
 
 
+def run_batch(args, w):
+    """Batched mode: the whole batch per step through tp_partition_batch with
+    autotuned knobs and stream count, against the plain single-graph path
+    (the same graphs partitioned one after another on one stream)."""
+    import torch
+
+    import paper_2410_19119_gb300 as tp
+    import synth
+    from paper_2410_19119_gb300 import autotune
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    recipe = synth.batch_recipe(w["count"], seed=w["seed"])
+    t0 = time.perf_counter()
+    csr = [synth.batch_graph(s) for s in recipe]
+    gen_s = time.perf_counter() - t0
+    graphs = [tp.graph_from_csr(x, a) for x, a in csr]
+    ks = [s["k"] for s in recipe]
+    total_n = sum(len(x) - 1 for x, _ in csr)
+    total_m2 = sum(len(a) for _, a in csr)
+    t0 = time.perf_counter()
+    params, conc, table = autotune.autotune(graphs, ks, EPS, seed=w["seed"])
+    tune_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        tp.partition_batch(graphs, ks, EPS, params, concurrency=conc)
+    torch.cuda.synchronize()
+    l0 = tp.launch_count()
+    times = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = tp.partition_batch(graphs, ks, EPS, params, concurrency=conc)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    launches = tp.launch_count() - l0
+    batch_s = statistics.median(times)
+    # the plain single-graph path, default knobs, one stream
+    p0 = tp.default_params(seed=w["seed"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = [tp.partition(g, k, EPS, p0) for g, k in zip(graphs, ks)]
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    same = all(bool(torch.equal(a[0], b[0])) for a, b in zip(out, plain))
+    if rank != 0:
+        return
+    knobs = {f: getattr(params, f) for f in ("tier_lane", "tier_small", "tier_mid",
+                                             "warps_per_block")}
+    line = {
+        "metric": METRIC, "value": len(graphs) * ws / batch_s, "unit": "graphs/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_s * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": w["desc"], "graphs": len(graphs), "total_n": total_n,
+                   "total_m2": total_m2, "timing": "host clock around the blocking batch call"},
+        "batch_ms": batch_s * 1e3, "plain_single_graph_ms": plain_s * 1e3,
+        "speedup_vs_plain": plain_s / batch_s, "identical_to_plain": same,
+        "lp_level0_edges_per_s": 5.0 * total_m2 / batch_s,
+        "autotune": {"knobs": knobs, "concurrency": conc, "seconds": tune_s,
+                     "trials": len(table)},
+        "generate_s": gen_s, "gpu_launches": launches // max(args.steps, 1),
+        "sum_cut": sum(st["cut"] for _, st in out),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_batch_reference(args, w):
+    """The oracle on a bounded sample of the batch: every step partitions the
+    next 16 graphs of the recipe on one host thread."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import synth
+
+    recipe = synth.batch_recipe(w["count"], seed=w["seed"])
+    per_step = 16
+    need = (args.warmup + args.steps) * per_step
+    csr = [synth.batch_graph(s) for s in recipe[:need]]
+    pos = 0
+
+    def one_step():
+        nonlocal pos
+        for j in range(per_step):
+            xadj, adj = csr[pos + j]
+            oracle.partition(oracle.Graph(xadj, adj), recipe[pos + j]["k"], EPS,
+                             oracle.Params(seed=w["seed"]))
+        pos += per_step
+
+    for _ in range(args.warmup):
+        one_step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one_step()
+    dt = time.perf_counter() - t0
+    value = args.steps * per_step / dt
+    sample = f"{per_step} graphs of the recipe (in recipe order) per step, one thread"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "graphs/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": w["desc"]},
+            "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_partition_only(args, w):
     """One compressed partition of the workload (for profiler captures)."""
     import torch
@@ -436,7 +549,12 @@ def main():
                     help="compress and partition once, print the stats (profiler captures)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
-    if args.lp_only:
+    if w["gen"] == "batch":
+        if args.impl == "reference":
+            run_batch_reference(args, w)
+        else:
+            run_batch(args, w)
+    elif args.lp_only:
         run_lp_only(args, w)
     elif args.partition_only:
         run_partition_only(args, w)

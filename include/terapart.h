@@ -240,6 +240,26 @@ tp_status tp_metrics_static(const tp_graph *g, const int32_t *d_part, int32_t k,
 tp_status tp_partition(const tp_graph *g, int32_t k, double eps, const tp_params *p,
                        int32_t *d_part, tp_stats *stats, void *stream);
 
+/* Batched mode: partitions count independent graphs, graph i into k[i]
+ * blocks written to the device buffer d_part[i] (graphs[i]->n entries),
+ * with the shared eps and params p (NULL: defaults). Each graph runs the
+ * tp_partition path unchanged, so every result equals tp_partition of that
+ * graph alone; the call only overlaps the graphs on the device, using
+ * `concurrency` host threads that each create, use and destroy one CUDA
+ * stream on the calling thread's device (graphs are handed out largest
+ * first). The paper partitions one graph at a time; this is the serving
+ * side of the method (many small graphs keep the GPU busy only together).
+ *  - stats (nullable, count entries) and status (nullable, count entries)
+ *    receive each graph's stats and status.
+ *  - A handle may appear only once (graphs cache per-level state while they
+ *    are partitioned); every graph must live on the calling thread's device.
+ *  - Blocks until all graphs are done; returns TP_OK or the first failing
+ *    graph's status (in graph order); TP_ERR_INVALID for bad arguments
+ *    before any work starts. */
+tp_status tp_partition_batch(int32_t count, tp_graph *const *graphs, const int32_t *k, double eps,
+                             const tp_params *p, int32_t *const *d_part, tp_stats *stats,
+                             tp_status *status, int32_t concurrency);
+
 /* ---- tracing ---- */
 
 /* Number of kernels the library has launched in this process so far. */

@@ -16,7 +16,7 @@ from ._lib import ProfileEntry, Params, Stats, TpError, check, lib
 __all__ = ["Graph", "Params", "Stats", "TpError", "default_params", "graph_from_csr",
            "graph_from_compressed", "partition", "lp_cluster", "lp_subround", "contract",
            "initial_partition", "lp_refine", "rebalance", "metrics", "launch_count",
-           "profile_enable", "profile_read", "PROFILE_FAMILIES"]
+           "profile_enable", "profile_read", "PROFILE_FAMILIES", "partition_batch"]
 
 PROFILE_FAMILIES = ("rate_small", "rate_mid", "rate_big", "rate_huge", "approve", "rate_lane")
 
@@ -232,6 +232,31 @@ def partition(g: Graph, k, eps=0.03, params=None, out=None, stream=None):
                              _stream(stream)), "tp_partition")
     return part[:n], stats_dict(st)
 
+
+
+def partition_batch(graphs, ks, eps=0.03, params=None, concurrency=16, outs=None):
+    """Batched mode: partitions independent graphs concurrently (tp_partition_batch).
+
+    Each result equals partition(graphs[i], ks[i], eps, params). Returns a list
+    of (part int32 CUDA tensor, stats dict) in input order; raises on the first
+    failing graph.
+    """
+    torch = _torch()
+    p = params or default_params()
+    cnt = len(graphs)
+    if len(ks) != cnt:
+        raise ValueError("one k per graph")
+    parts = outs if outs is not None else [
+        torch.empty(max(g.n, 1), dtype=torch.int32, device="cuda") for g in graphs]
+    handles = (ctypes.c_void_p * max(cnt, 1))(*[g.handle for g in graphs])
+    karr = (ctypes.c_int32 * max(cnt, 1))(*[int(k) for k in ks])
+    parr = (ctypes.c_void_p * max(cnt, 1))(*[_ptr(t) for t in parts])
+    st = (Stats * max(cnt, 1))()
+    status = (ctypes.c_int * max(cnt, 1))()
+    torch.cuda.synchronize()  # inputs written on other streams are complete
+    check(lib().tp_partition_batch(cnt, handles, karr, eps, ctypes.byref(p), parr, st, status,
+                                   concurrency), "tp_partition_batch")
+    return [(parts[i][: graphs[i].n], stats_dict(st[i])) for i in range(cnt)]
 
 
 def launch_count() -> int:

@@ -63,6 +63,8 @@ SIGNATURES = {
     "tp_metrics": (ctypes.c_int, [vp, vp, i32, P(i64), vp, vp]),
     "tp_metrics_static": (ctypes.c_int, [vp, vp, i32, P(i64), vp, vp]),
     "tp_partition": (ctypes.c_int, [vp, i32, ctypes.c_double, P(Params), vp, P(Stats), vp]),
+    "tp_partition_batch": (ctypes.c_int, [i32, P(vp), P(i32), ctypes.c_double, P(Params), P(vp),
+                                          P(Stats), P(ctypes.c_int), i32]),
     "tp_launch_count": (u64, []),
     "tp_profile_enable": (None, [ctypes.c_int]),
     "tp_profile_read": (ctypes.c_int, [P(ProfileEntry), ctypes.c_int, vp]),

@@ -1,0 +1,66 @@
+"""Autotuner for the performance knobs of batched partitioning.
+
+The knobs only decide which kernel rates a vertex and how work is laid out:
+the degree bounds of the lane and warp tiers (tier_lane, tier_small,
+tier_mid), the warps per block of the warp-per-vertex kernels
+(warps_per_block, which also sets how many 128-slot shared hash tables a
+block holds) and the number of concurrent streams of tp_partition_batch.
+None of them changes a result (integer sums commute and the rating order is
+total), so the tuner may pick any of them by time alone. It times
+partition_batch on a sample of the batch that spans its size range, for each
+candidate, and keeps the fastest: first the stream count with the default
+knobs, then every knob combination at that stream count.
+"""
+import itertools
+import time
+
+from . import default_params, partition_batch
+
+TIER_LANE = (0, 16, 32)
+TIER_SMALL = (32, 64)
+TIER_MID = (256, 1024)
+WARPS_PER_BLOCK = (4, 8)
+CONCURRENCY = (8, 16, 32)
+
+
+def candidates():
+    """Every knob combination the tuner tries."""
+    for lane, small, mid, wpb in itertools.product(TIER_LANE, TIER_SMALL, TIER_MID,
+                                                   WARPS_PER_BLOCK):
+        yield {"tier_lane": lane, "tier_small": small, "tier_mid": mid, "warps_per_block": wpb}
+
+
+def sample_indices(graphs, size):
+    """size graphs spread evenly over the batch sorted by n + 2m."""
+    order = sorted(range(len(graphs)), key=lambda i: graphs[i].n + graphs[i].info()["m2"])
+    if size >= len(order):
+        return order
+    step = len(order) / size
+    return [order[int(j * step)] for j in range(size)]
+
+
+def autotune(graphs, ks, eps=0.03, seed=1, sample=96, repeats=1, concurrency=CONCURRENCY):
+    """Returns (params, concurrency, table): the fastest knob set on the sample,
+    the matching stream count, and every (knobs, concurrency, seconds) timed."""
+    import torch
+
+    idx = sample_indices(graphs, sample)
+    gs, kk = [graphs[i] for i in idx], [ks[i] for i in idx]
+    table = []
+
+    def timed(knobs, conc):
+        p = default_params(seed=seed, **knobs)
+        partition_batch(gs, kk, eps, p, concurrency=conc)  # warm-up (allocations)
+        dt = float("inf")
+        for _ in range(repeats):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            partition_batch(gs, kk, eps, p, concurrency=conc)
+            torch.cuda.synchronize()
+            dt = min(dt, time.perf_counter() - t0)
+        table.append((dict(knobs), conc, dt))
+        return dt
+
+    conc = min(concurrency, key=lambda c: timed({}, c))
+    knobs = min(candidates(), key=lambda kn: timed(kn, conc))
+    return default_params(seed=seed, **knobs), conc, table

@@ -2,6 +2,10 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <thread>
+#include <vector>
 
 #include "tp_internal.cuh"
 
@@ -19,9 +23,7 @@ void partition(tp_graph *g0, int32_t k, int64_t eps_ppm, const tp_params &p, int
                tp_stats *st, cudaStream_t s);
 
 namespace {
-void pool_setup() {
-  static bool done = false;
-  if (done) return;
+void pool_setup_once() {
   int dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) {
     cudaMemPool_t pool;
@@ -30,7 +32,11 @@ void pool_setup() {
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
   }
-  done = true;
+}
+
+void pool_setup() {
+  static std::once_flag once;
+  std::call_once(once, pool_setup_once);
 }
 
 bool params_ok(const tp_params &p) {
@@ -163,7 +169,12 @@ tp_status tp_graph_check(const tp_graph *g, void *stream) {
   return r != TP_OK ? r : st;
 }
 
-void tp_graph_destroy(tp_graph *g) { delete g; }
+void tp_graph_destroy(tp_graph *g) {
+  if (!g) return;
+  cudaDeviceSynchronize();  // nothing may still run on g, on any stream
+  g->rehome();
+  delete g;
+}
 
 tp_status tp_lp_subround(const tp_graph *g, int32_t *d_label, int64_t *d_lw, int64_t nlabels,
                          int64_t cap, uint64_t round_key, int32_t S, int32_t s, void *stream) {
@@ -258,6 +269,72 @@ tp_status tp_partition(const tp_graph *g, int32_t k, double eps, const tp_params
     partition(const_cast<tp_graph *>(g), k, eps_ppm_of(eps), q, d_part, stats,
               (cudaStream_t)stream);
   });
+}
+
+// Batched mode: many independent graphs overlap on the device. Every graph
+// runs exactly the tp_partition path on a stream of its worker, so each
+// result is bit-identical to partitioning that graph alone; only the
+// scheduling differs. `concurrency` host workers each own a CUDA stream and
+// take the next graph from a shared counter, largest graphs first so the
+// batch does not end on one big straggler.
+tp_status tp_partition_batch(int32_t count, tp_graph *const *graphs, const int32_t *k, double eps,
+                             const tp_params *p, int32_t *const *d_part, tp_stats *stats,
+                             tp_status *status, int32_t concurrency) {
+  if (count < 0 || concurrency < 1 || !(eps >= 0.0 && eps < 1.0)) return TP_ERR_INVALID;
+  if (count == 0) return TP_OK;
+  if (!graphs || !k || !d_part) return TP_ERR_INVALID;
+  for (int32_t i = 0; i < count; ++i)
+    if (!graphs[i] || k[i] < 1 || (graphs[i]->n && !d_part[i])) return TP_ERR_INVALID;
+  {  // a graph caches per-level state while it is partitioned: no handle twice
+    std::vector<tp_graph *> sorted(graphs, graphs + count);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return TP_ERR_INVALID;
+  }
+  tp_params q;
+  try {
+    q = resolve(p);
+  } catch (const Error &e) {
+    return e.code;
+  }
+  const int64_t eps_ppm = eps_ppm_of(eps);
+  std::vector<int32_t> order((size_t)count);
+  for (int32_t i = 0; i < count; ++i) order[(size_t)i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return graphs[a]->n + graphs[a]->m2 > graphs[b]->n + graphs[b]->m2;
+  });
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TP_ERR_CUDA;
+  std::vector<tp_status> st((size_t)count, TP_OK);
+  std::atomic<int32_t> next{0};
+  auto worker = [&] {
+    cudaStream_t s = nullptr;
+    if (cudaSetDevice(dev) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      (void)cudaGetLastError();
+      for (int32_t i; (i = next.fetch_add(1)) < count;) st[(size_t)order[(size_t)i]] = TP_ERR_CUDA;
+      return;
+    }
+    for (int32_t i; (i = next.fetch_add(1)) < count;) {
+      const int32_t g = order[(size_t)i];
+      st[(size_t)g] = guard([&] {
+        partition(graphs[g], k[g], eps_ppm, q, d_part[g], stats ? &stats[g] : nullptr, s);
+      });
+    }
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  };
+  const int32_t nthreads = std::min(concurrency, std::min(count, 256));
+  std::vector<std::thread> pool;
+  pool.reserve((size_t)nthreads - 1);
+  for (int32_t t = 1; t < nthreads; ++t) pool.emplace_back(worker);
+  worker();
+  for (std::thread &t : pool) t.join();
+  tp_status first = TP_OK;
+  for (int32_t i = 0; i < count; ++i) {
+    if (status) status[i] = st[(size_t)i];
+    if (first == TP_OK) first = st[(size_t)i];
+  }
+  return first;
 }
 
 }  // extern "C"

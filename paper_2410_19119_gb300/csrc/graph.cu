@@ -15,7 +15,7 @@ namespace {
 void *(*g_alloc)(size_t, void *, void *) = nullptr;
 void (*g_free)(void *, size_t, void *, void *) = nullptr;
 void *g_ctx = nullptr;
-int g_sms = 0;
+std::atomic<int> g_sms{0};
 }  // namespace
 
 void *dev_alloc(size_t bytes, cudaStream_t s) {
@@ -51,8 +51,11 @@ struct ProfRecord {
   cudaEvent_t a, b;
   double bytes;
 };
+// The profiler serves one host thread at a time (benchmarks); the scope flag
+// is per thread so concurrent partitions (tp_partition_batch) never record.
+thread_local bool t_prof_scope = false;
 struct Profiler {
-  bool enabled = false, scope = false;
+  bool enabled = false;
   std::vector<ProfRecord> recs;
   std::vector<cudaEvent_t> pool;
   cudaEvent_t open[PF_COUNT] = {};
@@ -70,8 +73,8 @@ struct Profiler {
 }  // namespace
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
-bool prof_active() { return g_prof.enabled && g_prof.scope; }
-void prof_scope(bool on) { g_prof.scope = on; }
+bool prof_active() { return t_prof_scope && g_prof.enabled; }
+void prof_scope(bool on) { t_prof_scope = on; }
 void prof_begin(int family, cudaStream_t s) {
   if (!prof_active()) return;
   cudaEvent_t e = g_prof.get();
@@ -87,13 +90,15 @@ void prof_end(int family, cudaStream_t s, double alg_bytes) {
 }
 
 int num_sms() {
-  if (!g_sms) {
+  int v = g_sms.load(std::memory_order_relaxed);
+  if (!v) {
     int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sms <= 0) g_sms = 1;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (v <= 0) v = 1;
+    g_sms.store(v, std::memory_order_relaxed);  // every thread computes the same value
   }
-  return g_sms;
+  return v;
 }
 
 GView view(const tp_graph *g) {
@@ -276,6 +281,9 @@ void build_tiers(tp_graph *g, const tp_params &p, cudaStream_t s) {
   int32_t small_max = std::max(lane_max, std::min(p.tier_small, 64));
   int32_t mid_max = std::max(small_max, std::min(p.tier_mid, 1024));
   if (T.built && T.small_max == small_max && T.mid_max == mid_max && T.lane_max == lane_max) return;
+  // the old cache is freed on this call's stream: the stream it was built on
+  // may be gone (calls on one graph are ordered by the caller)
+  T.rehome(s);
   T = TierCache();
   T.lane_max = lane_max;
   T.small_max = small_max;
@@ -781,7 +789,6 @@ extern "C" uint64_t tp_launch_count(void) { return tp::g_launches.load(); }
 
 extern "C" void tp_profile_enable(int on) {
   tp::g_prof.enabled = on != 0;
-  if (!on) tp::g_prof.scope = false;
 }
 
 extern "C" int tp_profile_read(tp_profile_entry *out, int max, void *stream) {

@@ -23,6 +23,7 @@
 // per target runs a weighted radix select over the key (gain desc, vertex
 // asc) and approves exactly the longest fitting prefix.
 #include <algorithm>
+#include <mutex>
 
 #include "decode.cuh"
 
@@ -1109,9 +1110,7 @@ void set_smem_limits(K kernel, size_t bytes) {
   TP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
 }
 
-void configure_kernels() {
-  static bool done = false;
-  if (done) return;
+void configure_kernels_once() {
   size_t small16 = sizeof(WarpSmem<kSmallLog>) * 16;
   size_t mid = sizeof(WarpSmem<kMidLog>) * kMidWarps;
   size_t huge = sizeof(WarpSmem<kMidLog>) * kHugeWarps;
@@ -1126,7 +1125,11 @@ void configure_kernels() {
   TP_CFG_MODE(M_FAV)
   TP_CFG_MODE(M_REBAL)
 #undef TP_CFG_MODE
-  done = true;
+}
+
+void configure_kernels() {
+  static std::once_flag once;
+  std::call_once(once, configure_kernels_once);
 }
 
 ApproveCtx approve_ctx(tp_graph *g, const LpState &st, LpWork &w) {

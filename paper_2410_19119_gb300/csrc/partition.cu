@@ -2,6 +2,7 @@
 // balance constraint and metrics of the problem statement (Section
 // "Introduction"), and projection between levels.
 #include <algorithm>
+#include <memory>
 #include <vector>
 
 #include "decode.cuh"
@@ -195,7 +196,10 @@ void partition(tp_graph *g0, int32_t k, int64_t eps_ppm, const tp_params &p, int
   Buf<int64_t> B(std::max(k, 1), s);
   Buf<int32_t> cur(std::max<int64_t>(levels[L]->n, 1), s);
   t_phase.start();
-  initial_partition(levels[L], k, l_max, p, cur.get(), s);
+  // a compressed input that is not coarsened at all is partitioned as CSR
+  std::unique_ptr<tp_graph> ip_csr(levels[L]->compressed ? decompress(levels[L], s) : nullptr);
+  initial_partition(ip_csr ? ip_csr.get() : levels[L], k, l_max, p, cur.get(), s);
+  ip_csr.reset();
   t_phase.stop();
   S.ms_initial = t_phase.ms();
   t_phase.start();

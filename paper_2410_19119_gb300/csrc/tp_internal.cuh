@@ -111,6 +111,13 @@ struct TierCache {
   int64_t n_huge_chunks = 0;
   Buf<int32_t> tkeys;  // global rating tables (big + huge), EMPTY = -1
   Buf<int64_t> tvals;
+  // Later frees go to stream s (the cache may have been built on a stream
+  // that no longer exists; see tp_graph::rehome).
+  void rehome(cudaStream_t s) {
+    tier.s = small.s = mid.s = big.s = huge.s = s;
+    big_toff.s = huge_toff.s = big_tcap.s = huge_tcap.s = s;
+    huge_chunk_start.s = tkeys.s = tvals.s = s;
+  }
 };
 
 }  // namespace tp
@@ -135,6 +142,15 @@ struct tp_graph {
   // per-graph error word (device)
   tp::Buf<int32_t> err;
   tp::TierCache tiers;
+  // Buffers remember the stream they were allocated on and are freed on it.
+  // A graph outlives those streams (its tier cache may have been built by a
+  // partition on a batch worker's stream), so once the device is idle its
+  // buffers are freed on the legacy stream instead.
+  void rehome() {
+    xadj.s = adj.s = vw.s = ew.s = err.s = nullptr;
+    bytes.s = off32.s = off64.s = nullptr;
+    tiers.rehome(nullptr);
+  }
 };
 
 namespace tp {
@@ -357,6 +373,7 @@ void rebalance_moves(tp_graph *g, int32_t k, int64_t l_max, int32_t *d_part, int
 
 // ---------------------------------------------------------------- contraction / IP / metrics
 tp_graph *contract(const tp_graph *g, const int32_t *C, int32_t *d_map, cudaStream_t s);
+tp_graph *decompress(const tp_graph *z, cudaStream_t s);
 void initial_partition(const tp_graph *g, int32_t k, int64_t l_max, const tp_params &p,
                        int32_t *d_part, cudaStream_t s);
 void block_weights(const tp_graph *g, const int32_t *part, int32_t k, int64_t *d_B,

@@ -269,6 +269,225 @@ syn_graph *syn_rmat(int32_t scale, int64_t edge_factor, double a, double b, doub
   return g;
 }
 
+/* ------------------------------------------------------------------- RHG */
+/* Threshold random hyperbolic graph (Krioukov, Papadopoulos, Kitsak, Vahdat,
+ * Boguna, Phys. Rev. E 82, 2010): n points in a hyperbolic disk of radius R.
+ * Point i takes draws 2i (angle, uniform in [0, 2 pi)) and 2i + 1 (radius,
+ * density alpha sinh(alpha r) / (cosh(alpha R) - 1) on [0, R], sampled by
+ * its inverse CDF r = acosh(1 + (cosh(alpha R) - 1) U) / alpha), with
+ * alpha = (gamma - 1) / 2 for the power-law exponent gamma. Two points are
+ * adjacent iff their hyperbolic distance is <= R:
+ *   cosh r1 cosh r2 - sinh r1 sinh r2 cos(t1 - t2) <= cosh R.
+ * R = 2 ln n + C. C starts from the asymptotic average degree
+ * 2 alpha^2 e^{-C/2} / (pi (alpha - 1/2)^2) (Gugelmann, Panagiotou, Peter,
+ * ICALP 2012) and is then bisected on the measured average degree of these
+ * points (the radii are redrawn from the same uniforms for every trial C).
+ * Vertex ids follow the angle order, so neighbour ids are close.
+ * Candidates come from radial bands (the band idea of von Looz, Meyerhenke,
+ * Prutkin, ISAAC 2015): points of each band are kept in angle order, and for
+ * u and a band whose lower radius is b > 0 only angles within
+ * acos((cosh r_u cosh b - cosh R) / (sinh r_u sinh b)) of u's can be close
+ * enough (that bound only tightens as r grows). Windows are widened by 1e-9
+ * and every pair is tested with one expression in canonical order, so the
+ * adjacency is symmetric. */
+typedef struct {
+  int64_t n, nb;
+  double R, coshR;
+  double *th, *ch, *sh; /* angle, cosh r, sinh r per vertex (angle order) */
+  double *r;
+  int64_t *bstart;      /* band b holds vertices bidx[bstart[b] .. bstart[b+1]) */
+  int32_t *bidx;        /* vertex ids, angle order within a band */
+  double *bth;          /* their angles */
+  double *blo;          /* lower radius of each band */
+} rhg_pts;
+
+static int cmp_dbl_idx(const void *a, const void *b) {
+  const double *x = (const double *)a, *y = (const double *)b;
+  return x[0] < y[0] ? -1 : x[0] > y[0] ? 1 : (x[1] < y[1] ? -1 : x[1] > y[1]);
+}
+
+static int rhg_adjacent(const rhg_pts *P, int32_t u, int32_t v) {
+  int32_t a = u < v ? u : v, b = u < v ? v : u;
+  double lhs = P->ch[a] * P->ch[b] - P->sh[a] * P->sh[b] * cos(P->th[a] - P->th[b]);
+  return lhs <= P->coshR;
+}
+
+/* radii and bands for disk radius R (angles and uniforms fixed) */
+static void rhg_place(rhg_pts *P, const double *ur, double alpha, double R) {
+  int64_t n = P->n;
+  P->R = R;
+  P->coshR = cosh(R);
+  double ca = cosh(alpha * R) - 1.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double r = acosh(1.0 + ca * ur[i]) / alpha;
+    if (r > R) r = R;
+    P->r[i] = r;
+    P->ch[i] = cosh(r);
+    P->sh[i] = sinh(r);
+  }
+  int64_t nb = P->nb;
+  for (int64_t b = 0; b <= nb; ++b) P->bstart[b] = 0;
+  for (int64_t b = 0; b < nb; ++b) P->blo[b] = R * (double)b / (double)nb;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t b = (int64_t)(P->r[i] / R * (double)nb);
+    if (b >= nb) b = nb - 1;
+    P->bstart[b + 1]++;
+  }
+  for (int64_t b = 0; b < nb; ++b) P->bstart[b + 1] += P->bstart[b];
+  int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)nb);
+  for (int64_t b = 0; b < nb; ++b) fill[b] = P->bstart[b];
+  for (int64_t i = 0; i < n; ++i) { /* ids ascend with angle, so bands stay angle-sorted */
+    int64_t b = (int64_t)(P->r[i] / R * (double)nb);
+    if (b >= nb) b = nb - 1;
+    P->bidx[fill[b]] = (int32_t)i;
+    P->bth[fill[b]] = P->th[i];
+    fill[b]++;
+  }
+  free(fill);
+}
+
+/* first position in band [lo, hi) of bth with angle >= t */
+static int64_t lower_angle(const double *bth, int64_t lo, int64_t hi, double t) {
+  while (lo < hi) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if (bth[mid] < t) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+/* Visits every v != u adjacent to u (emit != NULL) or counts them; brute:
+ * test every other point instead of the band windows (for tests). */
+static int64_t rhg_scan(const rhg_pts *P, int32_t u, int32_t *emit, int brute) {
+  const double TWO_PI = 6.283185307179586;
+  int64_t cnt = 0;
+  if (brute) {
+    for (int32_t v = 0; v < (int32_t)P->n; ++v) {
+      if (v == u || !rhg_adjacent(P, u, v)) continue;
+      if (emit) emit[cnt] = v;
+      ++cnt;
+    }
+    return cnt;
+  }
+  for (int64_t b = 0; b < P->nb; ++b) {
+    int64_t lo = P->bstart[b], hi = P->bstart[b + 1];
+    if (lo == hi) continue;
+    double lb = P->blo[b], w = 4.0; /* > pi: the whole band */
+    if (lb > 0.0 && P->sh[u] > 0.0) {
+      double q = (P->ch[u] * cosh(lb) - P->coshR) / (P->sh[u] * sinh(lb));
+      if (q > 1.0) continue;
+      if (q > -1.0) w = acos(q) + 1e-9;
+    }
+    /* angle ranges [t0, t1] intersected with [0, 2 pi), up to two pieces */
+    double t0 = P->th[u] - w, t1 = P->th[u] + w;
+    double seg[4];
+    int ns = 0;
+    if (w >= 3.14159265358979) {
+      seg[0] = 0.0, seg[1] = TWO_PI, ns = 1;
+    } else {
+      if (t0 < 0.0) {
+        seg[0] = t0 + TWO_PI, seg[1] = TWO_PI, seg[2] = 0.0, seg[3] = t1, ns = 2;
+      } else if (t1 >= TWO_PI) {
+        seg[0] = t0, seg[1] = TWO_PI, seg[2] = 0.0, seg[3] = t1 - TWO_PI, ns = 2;
+      } else {
+        seg[0] = t0, seg[1] = t1, ns = 1;
+      }
+    }
+    for (int sgi = 0; sgi < ns; ++sgi) {
+      int64_t i = lower_angle(P->bth, lo, hi, seg[2 * sgi]);
+      for (; i < hi && P->bth[i] <= seg[2 * sgi + 1]; ++i) {
+        int32_t v = P->bidx[i];
+        if (v == u || !rhg_adjacent(P, u, v)) continue;
+        if (emit) emit[cnt] = v;
+        ++cnt;
+      }
+    }
+  }
+  return cnt;
+}
+
+static int64_t rhg_count(const rhg_pts *P) {
+  int64_t total = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : total)
+  for (int64_t u = 0; u < P->n; ++u) total += rhg_scan(P, (int32_t)u, NULL, 0);
+  return total;
+}
+
+static syn_graph *rhg_build(int64_t n, double avg_deg, double gamma, uint64_t seed, int brute) {
+  const double TWO_PI = 6.283185307179586;
+  double alpha = (gamma - 1.0) / 2.0;
+  rhg_pts P;
+  memset(&P, 0, sizeof(P));
+  P.n = n;
+  P.nb = n > 1 ? (int64_t)ceil(log((double)n)) : 1;
+  P.th = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+  P.ch = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+  P.sh = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+  P.r = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+  P.bidx = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n + 1));
+  P.bth = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+  P.bstart = (int64_t *)malloc(sizeof(int64_t) * (size_t)(P.nb + 1));
+  P.blo = (double *)malloc(sizeof(double) * (size_t)P.nb);
+  /* angles sorted (ids follow angle order); each point keeps its radius draw */
+  double *pair = (double *)malloc(sizeof(double) * 2 * (size_t)(n + 1));
+  for (int64_t i = 0; i < n; ++i) {
+    pair[2 * i] = unit01(sm64(seed, 2 * (uint64_t)i)) * TWO_PI;
+    pair[2 * i + 1] = unit01(sm64(seed, 2 * (uint64_t)i + 1));
+  }
+  qsort(pair, (size_t)n, 2 * sizeof(double), cmp_dbl_idx);
+  double *ur = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+  for (int64_t i = 0; i < n; ++i) {
+    P.th[i] = pair[2 * i];
+    ur[i] = pair[2 * i + 1];
+  }
+  free(pair);
+  double am = alpha - 0.5;
+  double C = -2.0 * log(avg_deg * 3.141592653589793 * am * am / (2.0 * alpha * alpha));
+  double lnn = log((double)(n > 1 ? n : 2));
+  if (n > 1) { /* bisection on the measured degree: larger C, sparser graph */
+    double lo = C - 1.5, hi = C + 1.5;
+    for (int it = 0; it < 8; ++it) {
+      double mid = 0.5 * (lo + hi);
+      rhg_place(&P, ur, alpha, 2.0 * lnn + mid);
+      double d = (double)rhg_count(&P) / (double)n;
+      if (d > avg_deg) lo = mid;
+      else hi = mid;
+    }
+    C = 0.5 * (lo + hi);
+  }
+  rhg_place(&P, ur, alpha, 2.0 * lnn + C);
+  syn_graph *g = (syn_graph *)malloc(sizeof(syn_graph));
+  g->n = n;
+  g->xadj = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  int64_t *deg = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t u = 0; u < n; ++u) deg[u] = rhg_scan(&P, (int32_t)u, NULL, brute);
+  g->xadj[0] = 0;
+  for (int64_t u = 0; u < n; ++u) g->xadj[u + 1] = g->xadj[u] + deg[u];
+  g->m2 = g->xadj[n];
+  g->adj = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g->m2 + 1));
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t u = 0; u < n; ++u) {
+    int32_t *a = g->adj + g->xadj[u];
+    rhg_scan(&P, (int32_t)u, a, brute);
+    qsort(a, (size_t)deg[u], sizeof(int32_t), cmp_i32);
+  }
+  free(deg);
+  free(ur);
+  free(P.th), free(P.ch), free(P.sh), free(P.r), free(P.bidx), free(P.bth), free(P.bstart),
+      free(P.blo);
+  return g;
+}
+
+syn_graph *syn_rhg(int64_t n, double avg_deg, double gamma, uint64_t seed) {
+  return rhg_build(n, avg_deg, gamma, seed, 0);
+}
+
+/* The same graph with every pair tested directly (small n, for tests). */
+syn_graph *syn_rhg_brute(int64_t n, double avg_deg, double gamma, uint64_t seed) {
+  return rhg_build(n, avg_deg, gamma, seed, 1);
+}
+
 /* ---------------------------------------------------------------- access */
 int64_t syn_n(const syn_graph *g) { return g->n; }
 int64_t syn_m2(const syn_graph *g) { return g->m2; }
