@@ -71,8 +71,8 @@ typedef struct {
   int32_t tier_small;    /* max degree rated with the small shared table (64) */
   int32_t tier_mid;      /* max degree rated with the large shared table (1000) */
   int32_t warps_per_block; /* warps per block in the small tier (8) */
-  int32_t use_graphs;    /* capture LP levels below graph_n into CUDA graphs (1) */
-  int32_t graph_n;       /* see use_graphs (1 << 16) */
+  int32_t use_graphs;    /* reserved, no effect */
+  int32_t graph_n;       /* reserved, no effect */
 } tp_params;
 
 typedef struct {
@@ -87,6 +87,8 @@ typedef struct {
   int64_t level_m2[64];     /* adjacency entries (2m) per level */
   double ms_coarsen, ms_initial, ms_uncoarsen; /* device time per phase */
   double ms_lp_level0;      /* device time of the level-0 clustering rounds */
+  int64_t peak_bytes;       /* most device memory the call held at once (working
+                               set, including the caches it attaches to the graph) */
 } tp_stats;
 
 /* Fills p with the defaults listed above. */
@@ -259,6 +261,66 @@ tp_status tp_partition(const tp_graph *g, int32_t k, double eps, const tp_params
 tp_status tp_partition_batch(int32_t count, tp_graph *const *graphs, const int32_t *k, double eps,
                              const tp_params *p, int32_t *const *d_part, tp_stats *stats,
                              tp_status *status, int32_t concurrency);
+
+/* ---- serving: continuous batching under a device-memory budget ---- */
+
+/* A request server. Worker threads, each with its own CUDA stream, take
+ * submitted requests in FIFO order: the oldest waiting request starts as
+ * soon as a worker is free, its footprint fits in what is left of the
+ * budget, and (on a resident graph) no other request is using that graph.
+ * Started requests run concurrently on the device; a finished request
+ * returns its footprint to the budget, which admits the next. Every request
+ * runs the tp_partition path unchanged (after uploading and, if asked,
+ * compressing a host graph), so its result equals tp_partition of that
+ * graph alone. The paper partitions one graph per run; this is a serving
+ * layer around the method. */
+typedef struct tp_server tp_server;
+
+typedef struct {
+  const tp_graph *graph; /* resident device graph (not owned), or NULL: */
+  int64_t n;             /*   host CSR with n vertices, uploaded per request */
+  const int64_t *xadj;   /*   host, n + 1 entries; must stay valid until waited */
+  const int32_t *adj;    /*   host, xadj[n] entries, same lifetime */
+  int32_t compress;      /*   compress the uploaded graph before partitioning */
+  int32_t k;             /* blocks (>= 1) */
+  double eps;            /* imbalance, 0 <= eps < 1 */
+  int32_t *part;         /* host output, n entries, valid once waited */
+} tp_request;
+
+typedef struct {
+  double queued_ms;        /* submit -> start */
+  double run_ms;           /* start -> done */
+  double total_ms;         /* submit -> done (the request's latency) */
+  int64_t footprint_bytes; /* budget the request held (tp_footprint_bytes) */
+  int64_t peak_bytes;      /* device memory it actually held at its peak */
+} tp_request_info;
+
+/* Upper bound on the device memory one request holds: the partitioner's
+ * working set (and, with upload != 0, the uploaded CSR and, with compress,
+ * the compressed copy) for a graph of n vertices, m2 adjacency entries and
+ * k blocks. Returns -1 for invalid sizes. */
+int64_t tp_footprint_bytes(int64_t n, int64_t m2, int32_t k, int32_t upload, int32_t compress);
+
+/* Starts a server with budget_bytes of device memory for requests and
+ * `workers` worker threads (1..256) on the calling thread's device. p may be
+ * NULL (defaults); it applies to every request. */
+tp_status tp_server_create(int64_t budget_bytes, int32_t workers, const tp_params *p,
+                           tp_server **out);
+
+/* Queues a request and returns its ticket. TP_ERR_BUDGET if its footprint
+ * exceeds the whole budget; TP_ERR_INVALID for bad arguments. Never blocks
+ * on the device. */
+tp_status tp_server_submit(tp_server *sv, const tp_request *req, uint64_t *ticket);
+
+/* Blocks until the request is done, fills stats and info (both nullable)
+ * and returns its status; a ticket can be waited once. */
+tp_status tp_server_wait(tp_server *sv, uint64_t ticket, tp_stats *stats, tp_request_info *info);
+
+/* Largest sum of footprints the server has had running at once. */
+int64_t tp_server_peak_in_use(tp_server *sv);
+
+/* Runs every queued request to completion, then stops the workers. */
+void tp_server_destroy(tp_server *sv);
 
 /* ---- tracing ---- */
 

@@ -11,12 +11,13 @@ import ctypes
 
 import numpy as np
 
-from ._lib import ProfileEntry, Params, Stats, TpError, check, lib
+from ._lib import ProfileEntry, Params, Request, RequestInfo, Stats, TpError, check, lib
 
 __all__ = ["Graph", "Params", "Stats", "TpError", "default_params", "graph_from_csr",
            "graph_from_compressed", "partition", "lp_cluster", "lp_subround", "contract",
            "initial_partition", "lp_refine", "rebalance", "metrics", "launch_count",
-           "profile_enable", "profile_read", "PROFILE_FAMILIES", "partition_batch"]
+           "profile_enable", "profile_read", "PROFILE_FAMILIES", "partition_batch", "Server",
+           "footprint_bytes"]
 
 PROFILE_FAMILIES = ("rate_small", "rate_mid", "rate_big", "rate_huge", "approve", "rate_lane")
 
@@ -218,7 +219,7 @@ def stats_dict(st: Stats):
             "balanced": bool(st.balanced), "level_n": list(st.level_n[:L]),
             "level_m2": list(st.level_m2[:L]), "ms_coarsen": st.ms_coarsen,
             "ms_initial": st.ms_initial, "ms_uncoarsen": st.ms_uncoarsen,
-            "ms_lp_level0": st.ms_lp_level0}
+            "ms_lp_level0": st.ms_lp_level0, "peak_bytes": st.peak_bytes}
 
 
 def partition(g: Graph, k, eps=0.03, params=None, out=None, stream=None):
@@ -257,6 +258,75 @@ def partition_batch(graphs, ks, eps=0.03, params=None, concurrency=16, outs=None
     check(lib().tp_partition_batch(cnt, handles, karr, eps, ctypes.byref(p), parr, st, status,
                                    concurrency), "tp_partition_batch")
     return [(parts[i][: graphs[i].n], stats_dict(st[i])) for i in range(cnt)]
+
+
+def footprint_bytes(n, m2, k, upload=True, compress=False) -> int:
+    """Device memory budget one served request is charged (tp_footprint_bytes)."""
+    return lib().tp_footprint_bytes(n, m2, k, int(upload), int(compress))
+
+
+class Server:
+    """Serving with continuous batching (tp_server_*): requests are admitted in
+    FIFO order as workers and device-memory budget free up, and run
+    concurrently; each result equals partition() of that graph alone."""
+
+    def __init__(self, budget_bytes, workers=8, params=None):
+        self._p = params or default_params()
+        h = ctypes.c_void_p()
+        check(lib().tp_server_create(int(budget_bytes), workers, ctypes.byref(self._p),
+                                     ctypes.byref(h)), "tp_server_create")
+        self._h = h
+        self._pending = {}
+
+    def submit(self, k, eps=0.03, xadj=None, adj=None, graph=None, compress=False):
+        """Queues a request on a host CSR (xadj, adj numpy) or a resident Graph;
+        returns a ticket."""
+        if graph is not None:
+            n = graph.n
+            req = Request(graph.handle, 0, None, None, 0, int(k), float(eps), None)
+            keep = ()
+        else:
+            xadj = np.ascontiguousarray(xadj, dtype=np.int64)
+            adj = np.ascontiguousarray(adj, dtype=np.int32)
+            n = len(xadj) - 1
+            req = Request(None, n, xadj.ctypes.data, adj.ctypes.data, int(compress), int(k),
+                          float(eps), None)
+            keep = (xadj, adj)
+        part = np.empty(max(n, 1), dtype=np.int32)
+        req.part = part.ctypes.data
+        t = ctypes.c_uint64()
+        check(lib().tp_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)),
+              "tp_server_submit")
+        self._pending[t.value] = (part, n, keep, graph)
+        return t.value
+
+    def wait(self, ticket):
+        """(partition numpy int32, stats dict, info dict) of a submitted request."""
+        st, info = Stats(), RequestInfo()
+        code = lib().tp_server_wait(self._h, ticket, ctypes.byref(st), ctypes.byref(info))
+        part, n, _, _ = self._pending.pop(ticket)
+        check(code, "tp_server_wait")
+        return part[:n], stats_dict(st), {f: getattr(info, f) for f, _ in RequestInfo._fields_}
+
+    def peak_in_use(self):
+        return lib().tp_server_peak_in_use(self._h)
+
+    def close(self):
+        if self._h:
+            lib().tp_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def launch_count() -> int:

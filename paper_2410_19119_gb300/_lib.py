@@ -34,7 +34,18 @@ class Stats(ctypes.Structure):
                 ("imbalance", ctypes.c_double), ("levels", i32), ("balanced", i32),
                 ("level_n", i64 * 64), ("level_m2", i64 * 64), ("ms_coarsen", ctypes.c_double),
                 ("ms_initial", ctypes.c_double), ("ms_uncoarsen", ctypes.c_double),
-                ("ms_lp_level0", ctypes.c_double)]
+                ("ms_lp_level0", ctypes.c_double), ("peak_bytes", i64)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_void_p), ("n", i64), ("xadj", ctypes.c_void_p),
+                ("adj", ctypes.c_void_p), ("compress", i32), ("k", i32), ("eps", ctypes.c_double),
+                ("part", ctypes.c_void_p)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("queued_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double), ("footprint_bytes", i64), ("peak_bytes", i64)]
 
 
 class ProfileEntry(ctypes.Structure):
@@ -66,6 +77,12 @@ SIGNATURES = {
     "tp_partition_batch": (ctypes.c_int, [i32, P(vp), P(i32), ctypes.c_double, P(Params), P(vp),
                                           P(Stats), P(ctypes.c_int), i32]),
     "tp_launch_count": (u64, []),
+    "tp_footprint_bytes": (i64, [i64, i64, i32, i32, i32]),
+    "tp_server_create": (ctypes.c_int, [i64, i32, P(Params), P(vp)]),
+    "tp_server_submit": (ctypes.c_int, [vp, P(Request), P(u64)]),
+    "tp_server_wait": (ctypes.c_int, [vp, u64, P(Stats), P(RequestInfo)]),
+    "tp_server_peak_in_use": (i64, [vp]),
+    "tp_server_destroy": (None, [vp]),
     "tp_profile_enable": (None, [ctypes.c_int]),
     "tp_profile_read": (ctypes.c_int, [P(ProfileEntry), ctypes.c_int, vp]),
 }

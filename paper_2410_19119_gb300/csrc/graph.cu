@@ -18,24 +18,41 @@ void *g_ctx = nullptr;
 std::atomic<int> g_sms{0};
 }  // namespace
 
+// Device bytes this host thread holds and its high-water mark (a call runs
+// on one thread, so the peak of its working set is the mark's rise).
+thread_local int64_t t_live = 0, t_peak = 0;
+
+int64_t mem_mark() {
+  t_peak = t_live;
+  return t_live;
+}
+int64_t mem_peak_since(int64_t mark) { return t_peak - mark; }
+
+static void mem_add(int64_t b) {
+  t_live += b;
+  if (t_live > t_peak) t_peak = t_live;
+}
+
 void *dev_alloc(size_t bytes, cudaStream_t s) {
   if (bytes == 0) return nullptr;
   void *p = nullptr;
   if (g_alloc) {
     p = g_alloc(bytes, (void *)s, g_ctx);
     if (!p) throw Error{TP_ERR_OOM};
-    return p;
+  } else {
+    cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      throw Error{e == cudaErrorMemoryAllocation ? TP_ERR_OOM : TP_ERR_CUDA};
+    }
   }
-  cudaError_t e = cudaMallocAsync(&p, bytes, s);
-  if (e != cudaSuccess) {
-    (void)cudaGetLastError();
-    throw Error{e == cudaErrorMemoryAllocation ? TP_ERR_OOM : TP_ERR_CUDA};
-  }
+  mem_add((int64_t)bytes);
   return p;
 }
 
 void dev_free(void *p, size_t bytes, cudaStream_t s) {
   if (!p) return;
+  t_live -= (int64_t)bytes;
   if (g_free) {
     g_free(p, bytes, (void *)s, g_ctx);
     return;

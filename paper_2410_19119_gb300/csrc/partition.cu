@@ -152,6 +152,7 @@ void partition(tp_graph *g0, int32_t k, int64_t eps_ppm, const tp_params &p, int
   tp_stats local{};
   tp_stats &S = st ? *st : local;
   S = tp_stats{};
+  const int64_t mark = mem_mark();
   const int64_t W = g0->total_vw;
   const int64_t U = cluster_cap(W, k, eps_ppm);
   const int64_t l_max = block_cap(W, k, eps_ppm);
@@ -232,6 +233,7 @@ void partition(tp_graph *g0, int32_t k, int64_t eps_ppm, const tp_params &p, int
   S.balanced = mx <= l_max;
   int64_t perfect = (W + k - 1) / k;
   S.imbalance = perfect > 0 ? (double)mx / (double)perfect - 1.0 : 0.0;
+  S.peak_bytes = mem_peak_since(mark);
   int32_t e = read_scalar(g0->err.get(), s);
   TP_REQUIRE(e == 0, (tp_status)e);
 }

@@ -1,0 +1,230 @@
+// Serving: continuous batching of partition requests under a device-memory
+// budget.
+//
+// A server owns a pool of worker threads, each with its own CUDA stream.
+// Submitted requests wait in FIFO order; the head is admitted as soon as a
+// worker is free, its footprint (tp_footprint_bytes) fits in what is left of
+// the budget, and, for a request on a resident graph, no other request is
+// using that graph (a graph caches per-level state while it is partitioned).
+// Admitted requests run concurrently on the device; each one's memory is
+// returned to the budget when it finishes, which admits the next. Every
+// request runs the unchanged single-graph path (upload, optional
+// compression, tp_partition, copy back), so its result does not depend on
+// what else is in flight.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "tp_internal.cuh"
+
+namespace tp {
+tp_graph *from_csr(int64_t n, const int64_t *xadj, const int32_t *adj, const int64_t *vwgt,
+                   const int64_t *ewgt, int host, cudaStream_t s);
+tp_graph *compress(const tp_graph *c, cudaStream_t s);
+void partition(tp_graph *g0, int32_t k, int64_t eps_ppm, const tp_params &p, int32_t *d_part,
+               tp_stats *st, cudaStream_t s);
+}  // namespace tp
+
+using namespace tp;
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+struct Request {
+  tp_request r;
+  int64_t need = 0;  // admitted footprint (bytes)
+  int state = 0;     // 0 queued, 1 running, 2 done
+  tp_status status = TP_OK;
+  tp_stats stats{};
+  int64_t peak = 0;
+  Clock::time_point t_submit, t_start, t_done;
+};
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+}  // namespace
+
+struct tp_server {
+  int64_t budget = 0, in_use = 0, peak_in_use = 0;
+  int32_t max_running = 0, running = 0;
+  tp_params params{};
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<uint64_t> queue;
+  std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
+  std::unordered_set<const tp_graph *> busy;
+  std::vector<std::thread> workers;
+  uint64_t next_ticket = 1;
+  bool stopping = false;
+
+  // The queue head, if it can start now (caller holds mu).
+  Request *admissible() {
+    if (queue.empty() || running >= max_running) return nullptr;
+    Request *q = reqs[queue.front()].get();
+    if (in_use + q->need > budget) return nullptr;
+    if (q->r.graph && busy.count(q->r.graph)) return nullptr;
+    return q;
+  }
+
+  void run(Request *q, cudaStream_t s) {
+    const tp_request &r = q->r;
+    const int64_t mark = mem_mark();
+    q->status = guard([&] {
+      std::unique_ptr<tp_graph> up, zp;
+      const tp_graph *g = r.graph;
+      if (!g) {
+        up.reset(from_csr(r.n, r.xadj, r.adj, nullptr, nullptr, 1, s));
+        g = up.get();
+        if (r.compress) {
+          zp.reset(compress(up.get(), s));
+          up.reset();
+          g = zp.get();
+        }
+      }
+      Buf<int32_t> part(std::max<int64_t>(g->n, 1), s);
+      partition(const_cast<tp_graph *>(g), r.k, (int64_t)llround(r.eps * 1e6), params, part.get(),
+                &q->stats, s);
+      if (g->n)
+        TP_CUDA(cudaMemcpyAsync(r.part, part.get(), g->n * sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, s));
+      TP_CUDA(cudaStreamSynchronize(s));
+    });
+    q->peak = mem_peak_since(mark);
+  }
+
+  void worker() {
+    cudaStream_t s = nullptr;
+    const bool ok = cudaSetDevice(device) == cudaSuccess &&
+                    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+    std::unique_lock<std::mutex> lk(mu);
+    for (;;) {
+      Request *q = nullptr;
+      cv_work.wait(lk, [&] { return (q = admissible()) != nullptr || (stopping && queue.empty()); });
+      if (!q) break;
+      queue.pop_front();
+      q->state = 1;
+      q->t_start = Clock::now();
+      in_use += q->need;
+      peak_in_use = std::max(peak_in_use, in_use);
+      ++running;
+      if (q->r.graph) busy.insert(q->r.graph);
+      cv_work.notify_all();  // the next head may fit as well
+      lk.unlock();
+      if (ok) run(q, s);
+      else q->status = TP_ERR_CUDA;
+      lk.lock();
+      q->t_done = Clock::now();
+      in_use -= q->need;
+      --running;
+      if (q->r.graph) busy.erase(q->r.graph);
+      q->state = 2;
+      cv_done.notify_all();
+      cv_work.notify_all();
+    }
+    lk.unlock();
+    if (s) cudaStreamDestroy(s);
+  }
+};
+
+extern "C" {
+
+int64_t tp_footprint_bytes(int64_t n, int64_t m2, int32_t k, int32_t upload, int32_t compress) {
+  if (n < 0 || m2 < 0 || k < 1) return -1;
+  const int64_t csr = 8 * (n + 1) + 4 * m2 + 64;
+  int64_t b = 16 * csr + 256 * (int64_t)k + ((int64_t)8 << 20);
+  if (upload) b += csr + (compress ? 2 * csr : 0);
+  return b;
+}
+
+tp_status tp_server_create(int64_t budget_bytes, int32_t workers, const tp_params *p,
+                           tp_server **out) {
+  if (!out || budget_bytes <= 0 || workers < 1 || workers > 256) return TP_ERR_INVALID;
+  *out = nullptr;
+  tp_params q;
+  if (p) q = *p;
+  else tp_params_default(&q);
+  if (q.cluster_rounds < 0 || q.refine_rounds < 0 || q.sub_rounds < 1 || q.c_lim < 1 ||
+      q.ip_attempts < 1 || q.max_levels < 1 || q.max_levels > 64)
+    return TP_ERR_INVALID;
+  auto *sv = new tp_server();
+  sv->budget = budget_bytes;
+  sv->max_running = workers;
+  sv->params = q;
+  if (cudaGetDevice(&sv->device) != cudaSuccess) {
+    delete sv;
+    return TP_ERR_CUDA;
+  }
+  for (int32_t i = 0; i < workers; ++i) sv->workers.emplace_back([sv] { sv->worker(); });
+  *out = sv;
+  return TP_OK;
+}
+
+tp_status tp_server_submit(tp_server *sv, const tp_request *req, uint64_t *ticket) {
+  if (!sv || !req || !ticket || req->k < 1 || !(req->eps >= 0.0 && req->eps < 1.0))
+    return TP_ERR_INVALID;
+  const tp_request &r = *req;
+  int64_t n = r.graph ? r.graph->n : r.n;
+  int64_t m2 = r.graph ? r.graph->m2 : (r.xadj && r.n >= 0 ? r.xadj[r.n] : -1);
+  if (n < 0 || m2 < 0 || (n > 0 && !r.part) || (!r.graph && (!r.xadj || (m2 > 0 && !r.adj))))
+    return TP_ERR_INVALID;
+  auto q = std::make_unique<Request>();
+  q->r = r;
+  q->need = tp_footprint_bytes(n, m2, r.k, r.graph ? 0 : 1, r.graph ? 0 : r.compress);
+  if (q->need > sv->budget) return TP_ERR_BUDGET;
+  q->t_submit = Clock::now();
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (sv->stopping) return TP_ERR_INVALID;
+  *ticket = sv->next_ticket++;
+  sv->queue.push_back(*ticket);
+  sv->reqs.emplace(*ticket, std::move(q));
+  sv->cv_work.notify_all();
+  return TP_OK;
+}
+
+tp_status tp_server_wait(tp_server *sv, uint64_t ticket, tp_stats *stats, tp_request_info *info) {
+  if (!sv) return TP_ERR_INVALID;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return TP_ERR_INVALID;
+  Request *q = it->second.get();
+  sv->cv_done.wait(lk, [&] { return q->state == 2; });
+  if (stats) *stats = q->stats;
+  if (info) {
+    info->queued_ms = ms_between(q->t_submit, q->t_start);
+    info->run_ms = ms_between(q->t_start, q->t_done);
+    info->total_ms = ms_between(q->t_submit, q->t_done);
+    info->footprint_bytes = q->need;
+    info->peak_bytes = q->peak;
+  }
+  tp_status st = q->status;
+  sv->reqs.erase(it);
+  return st;
+}
+
+int64_t tp_server_peak_in_use(tp_server *sv) {
+  if (!sv) return -1;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  return sv->peak_in_use;
+}
+
+void tp_server_destroy(tp_server *sv) {
+  if (!sv) return;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stopping = true;
+    sv->cv_work.notify_all();
+  }
+  for (std::thread &t : sv->workers) t.join();
+  delete sv;
+}
+
+}  // extern "C"

@@ -51,6 +51,10 @@ tp_status guard(F &&f) {
 // ---------------------------------------------------------------- device memory
 void *dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void *p, size_t bytes, cudaStream_t s);
+// Per-thread device-memory high-water mark: mem_mark() starts a window and
+// returns the current holding; mem_peak_since(mark) is the rise since then.
+int64_t mem_mark();
+int64_t mem_peak_since(int64_t mark);
 
 // Owning, stream-ordered device buffer.
 template <class T>
