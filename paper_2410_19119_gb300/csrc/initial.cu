@@ -24,7 +24,7 @@ namespace tp {
 
 namespace {
 
-constexpr int kIPThreads = 512;
+constexpr int kIPThreads = 1024;
 
 struct IPCtx {
   int64_t n;
@@ -43,6 +43,7 @@ struct IPCtx {
   // scratch, T * n entries each
   int32_t *ord, *disc, *claimer, *cnt, *side, *mvx0, *mvx1, *ok0, *ok1;
   int64_t *mvg0, *mvg1;
+  uint8_t *sub;  // sub-round of every vertex in the current 2-way LP round
   int64_t *cut;  // nodes * T
 };
 
@@ -113,7 +114,42 @@ __device__ void ip_select(int64_t cnt, int64_t rem, Item item, uint64_t &khi, ui
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kIPThreads) k_bisect(IPCtx c) {
+// Adjacency of a node's vertex is scanned by a whole warp, lanes striding
+// over the neighbours (coalesced, and a hub does not serialise one thread);
+// helpers visit the neighbours of u inside node j as (lane-local) callbacks.
+template <class F>
+__device__ __forceinline__ void node_nbrs(const IPCtx &c, int32_t u, int32_t j, F &&f) {
+  const int64_t b = c.xadj[u], e = c.xadj[u + 1];
+  for (int64_t i0 = b; i0 < e; i0 += 32) {
+    const int64_t i = i0 + lane_id();
+    bool in = false;
+    int32_t y = 0;
+    int64_t w = 0;
+    if (i < e) {
+      const int32_t v = c.adj[i];
+      in = c.node_of[v] == j;
+      if (in) y = c.loc[v], w = c.ew ? c.ew[i] : 1;
+    }
+    f(in, y, w);
+  }
+}
+
+// Exclusive scan of x[0..len) in place, block-wide; returns the total.
+__device__ int64_t block_scan_array(int32_t *x, int64_t len) {
+  int64_t carry = 0;
+  for (int64_t q0 = 0; q0 < len; q0 += blockDim.x) {
+    const int64_t q = q0 + threadIdx.x;
+    const int64_t v = q < len ? x[q] : 0;
+    int64_t tot;
+    const int64_t ex = bscan_excl(v, tot);
+    if (q < len) x[q] = (int32_t)(carry + ex);
+    carry += tot;
+  }
+  __syncthreads();
+  return carry;
+}
+
+__global__ void __launch_bounds__(kIPThreads, 1) k_bisect(IPCtx c) {
   const int32_t j = blockIdx.x / c.T, a = blockIdx.x % c.T;
   const int64_t nb = c.nstart[j], ns = c.nstart[j + 1] - nb;
   const int64_t R = (int64_t)a * c.n + nb;  // scratch region of this attempt
@@ -121,9 +157,11 @@ __global__ void __launch_bounds__(kIPThreads) k_bisect(IPCtx c) {
   int32_t *side = c.side + R, *mvx0 = c.mvx0 + R, *mvx1 = c.mvx1 + R, *ok0 = c.ok0 + R,
           *ok1 = c.ok1 + R;
   int64_t *mvg0 = c.mvg0 + R, *mvg1 = c.mvg1 + R;
+  uint8_t *sub = c.sub + R;
   const int32_t *vs = c.vlist + nb;
   const int32_t kk = c.nkk[j], k0 = (kk + 1) / 2, k1 = kk / 2;
   const uint64_t key = ((uint64_t)(uint32_t)c.noff[j] << 32) | (uint32_t)kk;
+  const int lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   auto cw = [&](int64_t x) -> int64_t { return c.vw ? c.vw[vs[x]] : 1; };
   if (ns == 0) {
     if (threadIdx.x == 0) c.cut[blockIdx.x] = 0;
@@ -141,45 +179,32 @@ __global__ void __launch_bounds__(kIPThreads) k_bisect(IPCtx c) {
   }
   __syncthreads();
   for (;;) {
-    int64_t fb = sh_fb, fe = sh_fe, tail = sh_tail;
+    const int64_t fb = sh_fb, fe = sh_fe, tail = sh_tail;
     if (fb >= fe) break;
-    for (int64_t i = fb + threadIdx.x; i < fe; i += blockDim.x) {
-      int32_t u = vs[ord[i]];
-      for (int64_t e = c.xadj[u]; e < c.xadj[u + 1]; ++e) {
-        int32_t v = c.adj[e];
-        if (c.node_of[v] != j) continue;
-        int32_t y = c.loc[v];
-        if (!disc[y]) atomicMin(&claimer[y], (int32_t)i);
-      }
+    // every undiscovered neighbour is claimed by its earliest frontier vertex
+    for (int64_t i = fb + warp; i < fe; i += nwarps)
+      node_nbrs(c, vs[ord[i]], j, [&](bool in, int32_t y, int64_t) {
+        if (in && !disc[y]) atomicMin(&claimer[y], (int32_t)i);
+      });
+    __syncthreads();
+    for (int64_t i = fb + warp; i < fe; i += nwarps) {
+      int32_t k = 0;
+      node_nbrs(c, vs[ord[i]], j, [&](bool in, int32_t y, int64_t) {
+        k += __popc(__ballot_sync(kFull, in && !disc[y] && claimer[y] == i));
+      });
+      if (lane == 0) cnt[i - fb] = k;
     }
     __syncthreads();
-    int64_t carry = 0;
-    for (int64_t i0 = fb; i0 < fe; i0 += blockDim.x) {
-      int64_t i = i0 + threadIdx.x, k = 0;
-      if (i < fe) {
-        int32_t u = vs[ord[i]];
-        for (int64_t e = c.xadj[u]; e < c.xadj[u + 1]; ++e) {
-          int32_t v = c.adj[e];
-          if (c.node_of[v] != j) continue;
-          int32_t y = c.loc[v];
-          if (!disc[y] && claimer[y] == i) ++k;
-        }
-      }
-      int64_t tot;
-      int64_t ex = bscan_excl(k, tot);
-      if (i < fe) cnt[i - fb] = (int32_t)(carry + ex);
-      carry += tot;
-    }
-    __syncthreads();
-    for (int64_t i = fb + threadIdx.x; i < fe; i += blockDim.x) {
+    const int64_t carry = block_scan_array(cnt, fe - fb);
+    // claimed neighbours in frontier order, then adjacency order
+    for (int64_t i = fb + warp; i < fe; i += nwarps) {
       int64_t pos = tail + cnt[i - fb];
-      int32_t u = vs[ord[i]];
-      for (int64_t e = c.xadj[u]; e < c.xadj[u + 1]; ++e) {
-        int32_t v = c.adj[e];
-        if (c.node_of[v] != j) continue;
-        int32_t y = c.loc[v];
-        if (!disc[y] && claimer[y] == i) ord[pos++] = y;
-      }
+      node_nbrs(c, vs[ord[i]], j, [&](bool in, int32_t y, int64_t) {
+        const bool mine = in && !disc[y] && claimer[y] == i;
+        const unsigned m = __ballot_sync(kFull, mine);
+        if (mine) ord[pos + __popc(m & lanemask_lt())] = y;
+        pos += __popc(m);
+      });
     }
     __syncthreads();
     for (int64_t q = tail + threadIdx.x; q < tail + carry; q += blockDim.x) disc[ord[q]] = 1;
@@ -201,6 +226,7 @@ __global__ void __launch_bounds__(kIPThreads) k_bisect(IPCtx c) {
   }
   // ---------------- greedy growing: longest prefix within target0
   __shared__ int64_t lw[2], inw[2], ncnt[2];
+  __shared__ int64_t sh_nact;
   int64_t W = 0;
   for (int64_t x = threadIdx.x; x < ns; x += blockDim.x) W += cw(x);
   W = bsum(W);
@@ -227,26 +253,43 @@ __global__ void __launch_bounds__(kIPThreads) k_bisect(IPCtx c) {
   // ---------------- 2-way label propagation
   for (int32_t r = 0; r < c.rounds; ++r) {
     const uint64_t rk = round_key(c.seed, kTagIPLP, key, ((uint64_t)a << 8) + (uint64_t)r);
+    for (int64_t x = threadIdx.x; x < ns; x += blockDim.x)
+      sub[x] = (uint8_t)sub_round_of(hstep(rk, (uint64_t)x), c.S);
+    __syncthreads();
     for (int32_t s = 0; s < c.S; ++s) {
-      if (threadIdx.x == 0) inw[0] = inw[1] = 0, ncnt[0] = ncnt[1] = 0;
-      __syncthreads();
-      for (int64_t x = threadIdx.x; x < ns; x += blockDim.x) {
-        if (sub_round_of(hstep(rk, (uint64_t)x), c.S) != s) continue;
-        int32_t u = vs[x];
-        int64_t Rs[2] = {0, 0};
-        for (int64_t e = c.xadj[u]; e < c.xadj[u + 1]; ++e) {
-          int32_t v = c.adj[e];
-          if (c.node_of[v] != j) continue;
-          Rs[side[c.loc[v]]] += c.ew ? c.ew[e] : 1;
+      // this sub-round's vertices, listed in cnt (ascending)
+      {
+        int64_t carry = 0;
+        for (int64_t x0 = 0; x0 < ns; x0 += blockDim.x) {
+          const int64_t x = x0 + threadIdx.x;
+          const int64_t f = x < ns && sub[x] == s;
+          int64_t tot;
+          const int64_t ex = bscan_excl(f, tot);
+          if (f) cnt[carry + ex] = (int32_t)x;
+          carry += tot;
         }
-        int32_t own = side[x], oth = 1 - own;
-        int64_t w = cw(x);
-        if (Rs[oth] > Rs[own] && lw[oth] + w <= caps[oth]) {
-          int64_t g = Rs[oth] - Rs[own];
+        if (threadIdx.x == 0) sh_nact = carry, inw[0] = inw[1] = 0, ncnt[0] = ncnt[1] = 0;
+        __syncthreads();
+      }
+      const int64_t nact = sh_nact;
+      for (int64_t q = warp; q < nact; q += nwarps) {
+        const int32_t x = cnt[q];
+        int64_t r0 = 0, r1 = 0;
+        node_nbrs(c, vs[x], j, [&](bool in, int32_t y, int64_t w) {
+          if (in) (side[y] ? r1 : r0) += w;
+        });
+        r0 = warp_sum(r0);
+        r1 = warp_sum(r1);
+        if (lane != 0) continue;
+        const int32_t own = side[x], oth = 1 - own;
+        const int64_t Rown = own ? r1 : r0, Roth = own ? r0 : r1;
+        const int64_t w = cw(x);
+        if (Roth > Rown && lw[oth] + w <= caps[oth]) {
+          const int64_t g = Roth - Rown;
           unsigned long long p = atomicAdd((unsigned long long *)&ncnt[oth], 1ull);
           atomicAdd((unsigned long long *)&inw[oth], (unsigned long long)w);
-          if (oth == 0) mvx0[p] = (int32_t)x, mvg0[p] = g, ok0[p] = 0;
-          else mvx1[p] = (int32_t)x, mvg1[p] = g, ok1[p] = 0;
+          if (oth == 0) mvx0[p] = x, mvg0[p] = g, ok0[p] = 0;
+          else mvx1[p] = x, mvg1[p] = g, ok1[p] = 0;
         }
       }
       __syncthreads();
@@ -288,12 +331,11 @@ __global__ void __launch_bounds__(kIPThreads) k_bisect(IPCtx c) {
   }
   // ---------------- cut of the induced subgraph
   int64_t cutv = 0;
-  for (int64_t x = threadIdx.x; x < ns; x += blockDim.x) {
-    int32_t u = vs[x];
-    for (int64_t e = c.xadj[u]; e < c.xadj[u + 1]; ++e) {
-      int32_t v = c.adj[e];
-      if (c.node_of[v] == j && side[c.loc[v]] != side[x]) cutv += c.ew ? c.ew[e] : 1;
-    }
+  for (int64_t x = warp; x < ns; x += nwarps) {
+    const int32_t sx = side[x];
+    node_nbrs(c, vs[x], j, [&](bool in, int32_t y, int64_t w) {
+      if (in && side[y] != sx) cutv += w;
+    });
   }
   cutv = bsum(cutv);
   if (threadIdx.x == 0) c.cut[blockIdx.x] = cutv / 2;
@@ -364,6 +406,7 @@ void initial_partition(const tp_graph *g, int32_t k, int64_t l_max, const tp_par
   Buf<int32_t> ord(T * n, s), disc(T * n, s), claimer(T * n, s), cnt(T * n, s), side(T * n, s),
       mvx0(T * n, s), mvx1(T * n, s), ok0(T * n, s), ok1(T * n, s);
   Buf<int64_t> mvg0(T * n, s), mvg1(T * n, s);
+  Buf<uint8_t> sub(T * n, s);
   Buf<uint64_t> keys(n, s);
   std::vector<int32_t> off = {0}, kks = {k};
   while (!off.empty()) {
@@ -415,6 +458,7 @@ void initial_partition(const tp_graph *g, int32_t k, int64_t l_max, const tp_par
     c.side = side.get(), c.mvx0 = mvx0.get(), c.mvx1 = mvx1.get(), c.ok0 = ok0.get(),
     c.ok1 = ok1.get();
     c.mvg0 = mvg0.get(), c.mvg1 = mvg1.get();
+    c.sub = sub.get();
     c.cut = cut.get();
     launch(k_bisect, (unsigned)(nodes * T), kIPThreads, 0, s, c);
     TP_LAUNCH_CHECK();
