@@ -731,7 +731,12 @@ __global__ void k_rate_list(RateCtx c) {
       int64_t off = c.tbase + c.toff[i];
       rate_vertex_warp<COMP, MODE>(c, u, c.tkeys + off, c.tvals + off, c.tcap[i], false, &mb);
     } else {
-      rate_vertex_warp<COMP, MODE>(c, u, wsp->keys, wsp->vals, kMidLog, false, &mb);
+      // use (and afterwards scan and clear) only the first power of two >= 2 deg
+      // slots of the warp's table
+      const int64_t d = COMP ? zip_nbr(c.g, u).deg : c.g.xadj[u + 1] - c.g.xadj[u];
+      int lc = kSmallLog;
+      while (lc < kMidLog && ((int64_t)1 << lc) < 2 * d) ++lc;
+      rate_vertex_warp<COMP, MODE>(c, u, wsp->keys, wsp->vals, lc, false, &mb);
     }
   }
   if (MODE == M_LP) flush_movers(c, mb);
