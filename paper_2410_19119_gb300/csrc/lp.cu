@@ -48,7 +48,7 @@ struct RateCtx {
   uint64_t rk;
   int32_t S, s;
   // M_LP outputs
-  int32_t *mv_u, *mv_t;
+  int32_t *mv_u, *mv_t, *mv_o;
   int64_t *mv_g;
   int64_t *in_w;
   unsigned long long *counters;
@@ -141,7 +141,7 @@ __device__ __forceinline__ void warp_reduce_best(Best &b) {
 
 // Per-warp buffer of mover records, flushed with one atomic per 32 movers.
 struct MoverBuf {
-  int32_t *u, *t;
+  int32_t *u, *t, *o;
   int64_t *gain;
   int cnt;
 };
@@ -156,6 +156,7 @@ __device__ __forceinline__ void flush_movers(const RateCtx &c, MoverBuf &mb) {
   if (l < mb.cnt) {
     c.mv_u[base + l] = mb.u[l];
     c.mv_t[base + l] = mb.t[l];
+    c.mv_o[base + l] = mb.o[l];
     c.mv_g[base + l] = mb.gain[l];
   }
   mb.cnt = 0;
@@ -172,6 +173,7 @@ __device__ __forceinline__ void finalize_warp(const RateCtx &c, const Best &b, i
       if (lane == 0) {
         mb->u[mb->cnt] = (int32_t)u;
         mb->t[mb->cnt] = b.x;
+        mb->o[mb->cnt] = c.label[u];
         mb->gain[mb->cnt] = b.r - b.rown;
         atomicAdd((unsigned long long *)&c.in_w[b.x], (unsigned long long)cu);
       }
@@ -261,7 +263,7 @@ template <int LOG>
 struct WarpSmem {
   int32_t keys[1 << LOG];
   int64_t vals[1 << LOG];
-  int32_t mu[32], mt[32];
+  int32_t mu[32], mt[32], mo[32];
   int64_t mg[32];
 };
 
@@ -279,7 +281,7 @@ __global__ void k_rate_small(RateCtx c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem<kSmallLog> &ws = reinterpret_cast<WarpSmem<kSmallLog> *>(smem_raw)[threadIdx.x >> 5];
   init_table(ws);
-  MoverBuf mb{ws.mu, ws.mt, ws.mg, 0};
+  MoverBuf mb{ws.mu, ws.mt, ws.mo, ws.mg, 0};
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   if (c.list) {
@@ -464,7 +466,7 @@ __device__ __forceinline__ void oem_sort(T (&a)[kLaneMaxDeg]) {
 
 // Mover records of one warp's window, written out with one atomic per window.
 struct LaneMovers {
-  int32_t u[kLaneWin], t[kLaneWin], g[kLaneWin];
+  int32_t u[kLaneWin], t[kLaneWin], o[kLaneWin], g[kLaneWin];
 };
 
 // Rates one batch: this lane's vertex u with deg neighbours (compressed:
@@ -581,6 +583,7 @@ __device__ __forceinline__ void lane_batch(const RateCtx &c, bool has, int32_t u
       const int at = nmv + __popc(mm & lanemask_lt());
       mb.u[at] = u;
       mb.t[at] = best.x;
+      mb.o[at] = own;
       mb.g[at] = best.r - rown;
       atomicAdd((unsigned long long *)&c.in_w[best.x], (unsigned long long)cu);
     }
@@ -694,6 +697,7 @@ __global__ void __launch_bounds__(lane_warps<W>() * 32, W ? 1 : kLaneBlocksPerSM
       for (int i = lane; i < nmv; i += 32) {
         c.mv_u[basep + i] = mb.u[i];
         c.mv_t[basep + i] = mb.t[i];
+        c.mv_o[basep + i] = mb.o[i];
         c.mv_g[basep + i] = mb.g[i];
       }
       __syncwarp();
@@ -714,14 +718,14 @@ template <bool COMP, int MODE, bool GLOBAL>
 __global__ void k_rate_list(RateCtx c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WarpSmem<kMidLog> *wsp = nullptr;
-  __shared__ int32_t mu[kMidWarps][32], mt[kMidWarps][32];
+  __shared__ int32_t mu[kMidWarps][32], mt[kMidWarps][32], mo[kMidWarps][32];
   __shared__ int64_t mg[kMidWarps][32];
   int w = threadIdx.x >> 5;
   if (!GLOBAL) {
     wsp = &reinterpret_cast<WarpSmem<kMidLog> *>(smem_raw)[w];
     init_table(*wsp);
   }
-  MoverBuf mb{mu[w], mt[w], mg[w], 0};
+  MoverBuf mb{mu[w], mt[w], mo[w], mg[w], 0};
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = gw; i < c.list_n; i += nw) {
@@ -818,9 +822,9 @@ __global__ void k_rate_huge_decide(RateCtx c) {
     if (w == 0) {
       b = lane < (int)(blockDim.x >> 5) ? wb[lane] : Best{-1, 0xffffffffu, INT32_MAX, 0};
       warp_reduce_best(b);
-      __shared__ int32_t mu[32], mt[32];
+      __shared__ int32_t mu[32], mt[32], mo[32];
       __shared__ int64_t mg[32];
-      MoverBuf mb{mu, mt, mg, 0};
+      MoverBuf mb{mu, mt, mo, mg, 0};
       finalize_warp<MODE>(c, b, u, cu, &mb);
       if (MODE == M_LP) flush_movers(c, mb);
     }
@@ -830,7 +834,7 @@ __global__ void k_rate_huge_decide(RateCtx c) {
 
 // ---------------------------------------------------------------- approval
 struct ApproveCtx {
-  const int32_t *mv_u, *mv_t;
+  const int32_t *mv_u, *mv_t, *mv_o;
   const int64_t *mv_g;
   int8_t *mv_ok;
   int64_t *in_w;
@@ -972,7 +976,7 @@ __global__ void k_apply(ApproveCtx a) {
     if (a.mv_ok[i]) {
       int32_t u = a.mv_u[i];
       int64_t w = vwt(a, u);
-      int32_t own = a.label[u];
+      int32_t own = a.mv_o[i];  // labels change only here, so this is still u's label
       a.label[u] = t;
       atomicAdd((unsigned long long *)&a.lw[t], (unsigned long long)w);
       atomicAdd((unsigned long long *)&a.lw[own], (unsigned long long)(-w));
@@ -1140,6 +1144,7 @@ void configure_kernels() {
 ApproveCtx approve_ctx(tp_graph *g, const LpState &st, LpWork &w) {
   ApproveCtx a;
   a.mv_u = w.mv_u.get();
+  a.mv_o = w.mv_o.get();
   a.mv_t = w.mv_t.get();
   a.mv_g = w.mv_g.get();
   a.mv_ok = w.mv_ok.get();
@@ -1249,6 +1254,7 @@ void LpWork::init(int64_t n_vertices, int64_t n_labels, cudaStream_t s) {
   ctarget.alloc(L, s);
   mv_u.alloc(N, s);
   mv_t.alloc(N, s);
+  mv_o.alloc(N, s);
   mv_g.alloc(N, s);
   mv_ok.alloc(N, s);
   cseg.alloc(N, s);
@@ -1270,6 +1276,7 @@ void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t
   c.S = S;
   c.s = s;
   c.mv_u = w.mv_u.get();
+  c.mv_o = w.mv_o.get();
   c.mv_t = w.mv_t.get();
   c.mv_g = w.mv_g.get();
   c.in_w = w.in_w.get();

@@ -343,6 +343,7 @@ struct LpWork {
   Buf<int32_t> cfill;  // nlabels: fill pointer inside a contested segment
   Buf<int64_t> cbase;   // nlabels
   Buf<int32_t> mv_u, mv_t;  // n
+  Buf<int32_t> mv_o;        // n: the mover's label when it was rated (its source)
   Buf<int64_t> mv_g;        // n
   Buf<int8_t> mv_ok;        // n
   Buf<int32_t> cseg;        // n (contested mover indices grouped by target)
