@@ -89,7 +89,13 @@ struct Profiler {
 } g_prof;
 }  // namespace
 
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+// Launches recorded into a CUDA graph are counted when the graph runs.
+thread_local bool t_capturing = false;
+void count_launch() {
+  if (!t_capturing) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+void count_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+void capture_counting(bool on) { t_capturing = on; }
 bool prof_active() { return t_prof_scope && g_prof.enabled; }
 void prof_scope(bool on) { t_prof_scope = on; }
 void prof_begin(int family, cudaStream_t s) {

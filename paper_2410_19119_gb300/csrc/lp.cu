@@ -1265,8 +1265,65 @@ void LpWork::init(int64_t n_vertices, int64_t n_labels, cudaStream_t s) {
   TP_CUDA(cudaMemsetAsync(counters.get(), 0, 4 * 8, s));
 }
 
+// The approval of one sub-round: the same five kernels and counter reset on
+// every sub-round of a level (only the data differs).
+constexpr int kApproveKernels = 5;
+void launch_approval(const ApproveCtx &a, int64_t wn, int64_t *counters, cudaStream_t stream) {
+  const unsigned blocks = (unsigned)num_sms() * 4;
+  const unsigned wide = grid_for(std::max<int64_t>(wn, 1), 256, (int64_t)num_sms() * 64);
+  launch(k_approve_fit, wide, 256, 0, stream, a);
+  launch(k_approve_alloc, (unsigned)num_sms(), 256, 0, stream, a);
+  launch(k_approve_scatter, blocks, 256, 0, stream, a);
+  launch(k_approve_contested, (unsigned)num_sms() * 2, 256, 0, stream, a);
+  launch(k_apply, wide, 256, 0, stream, a);
+  TP_LAUNCH_CHECK();
+  TP_CUDA(cudaMemsetAsync(counters, 0, 4 * sizeof(int64_t), stream));
+}
+
+// Records the approval of a level's sub-rounds into a CUDA graph on a
+// private stream, so each sub-round replays it with one launch. Returns null
+// (callers then launch directly) if capturing is not possible.
+struct ApprovalGraph {
+  cudaStream_t cs = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ApprovalGraph(const ApproveCtx &a, int64_t wn, int64_t *counters) {
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+      (void)cudaGetLastError();
+      cs = nullptr;
+      return;
+    }
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return;
+    }
+    capture_counting(true);
+    bool ok = true;
+    try {
+      launch_approval(a, wn, counters, cs);
+    } catch (...) {
+      ok = false;
+    }
+    capture_counting(false);
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamEndCapture(cs, &graph) != cudaSuccess || !ok || !graph) {
+      (void)cudaGetLastError();
+      if (graph) cudaGraphDestroy(graph);
+      return;
+    }
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+      (void)cudaGetLastError();
+      exec = nullptr;
+    }
+    cudaGraphDestroy(graph);
+  }
+  ~ApprovalGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cs) cudaStreamDestroy(cs);
+  }
+};
+
 void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t S, int32_t s,
-                 const tp_params &p, cudaStream_t stream) {
+                 const tp_params &p, cudaStream_t stream, cudaGraphExec_t approval) {
   configure_kernels();
   RateCtx c{};
   c.label = st.label;
@@ -1287,27 +1344,24 @@ void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t
     c.bucket_nb = w.bucket_nblocks;
   }
   rate_tiers<M_LP>(g, c, p, stream);
-  ApproveCtx a = approve_ctx(g, st, w);
-  const unsigned blocks = (unsigned)num_sms() * 4;
   prof_begin(PF_APPROVE, stream);
-  launch(k_approve_fit, grid_for(std::max<int64_t>(w.n, 1), 256, (int64_t)num_sms() * 64), 256, 0,
-         stream, a);
-  launch(k_approve_alloc, (unsigned)num_sms(), 256, 0, stream, a);
-  launch(k_approve_scatter, blocks, 256, 0, stream, a);
-  launch(k_approve_contested, (unsigned)num_sms() * 2, 256, 0, stream, a);
-  const unsigned wide = grid_for(std::max<int64_t>(w.n, 1), 256, (int64_t)num_sms() * 64);
-  launch(k_apply, wide, 256, 0, stream, a);
-  TP_LAUNCH_CHECK();
-  TP_CUDA(cudaMemsetAsync(w.counters.get(), 0, 4 * sizeof(int64_t), stream));
+  if (approval) {
+    TP_CUDA(cudaGraphLaunch(approval, stream));
+    count_launches(kApproveKernels);
+  } else {
+    launch_approval(approve_ctx(g, st, w), w.n, w.counters.get(), stream);
+  }
   prof_end(PF_APPROVE, stream, 0.0);
 }
 
 void lp_rounds(tp_graph *g, const LpState &st, LpWork &w, uint64_t seed, uint64_t tag, uint64_t a,
                uint64_t b0, int32_t rounds, int32_t S, const tp_params &p, cudaStream_t stream) {
+  if (rounds <= 0) return;
+  ApprovalGraph ag(approve_ctx(g, st, w), w.n, w.counters.get());
   for (int32_t r = 0; r < rounds; ++r) {
     uint64_t rk = round_key(seed, tag, a, b0 + (uint64_t)r);
     lp_bucket(g, w, rk, S, p, stream);
-    for (int32_t s = 0; s < S; ++s) lp_subround(g, st, w, rk, S, s, p, stream);
+    for (int32_t s = 0; s < S; ++s) lp_subround(g, st, w, rk, S, s, p, stream, ag.exec);
     w.bucket_S = 0;
   }
 }

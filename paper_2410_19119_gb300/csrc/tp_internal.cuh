@@ -272,6 +272,8 @@ __device__ __forceinline__ void latch_error(int32_t *err, int32_t code) {
 // ---------------------------------------------------------------- launch helpers
 int num_sms();
 void count_launch();
+void count_launches(uint64_t k);  // kernels a replayed CUDA graph ran
+void capture_counting(bool on);   // launches on this thread are being captured
 
 // Every kernel of the library is launched through here (counts launches).
 template <class... KArgs, class... Args>
@@ -356,8 +358,10 @@ struct LpWork {
   int32_t bucket_S = 0;      // S of the current buckets (0: none)
   void init(int64_t n_vertices, int64_t n_labels, cudaStream_t s);
 };
+// approval (nullable): a CUDA graph of this level's approval kernels to
+// replay instead of launching them.
 void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t S, int32_t s,
-                 const tp_params &p, cudaStream_t stream);
+                 const tp_params &p, cudaStream_t stream, cudaGraphExec_t approval = nullptr);
 // Buckets the lane-tier vertices of round key rk by sub-round (A3).
 void lp_bucket(tp_graph *g, LpWork &w, uint64_t rk, int32_t S, const tp_params &p,
                cudaStream_t stream);
