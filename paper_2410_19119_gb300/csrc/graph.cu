@@ -91,11 +91,17 @@ struct Profiler {
 
 // Launches recorded into a CUDA graph are counted when the graph runs.
 thread_local bool t_capturing = false;
+thread_local uint64_t t_captured = 0;
 void count_launch() {
-  if (!t_capturing) g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (t_capturing) ++t_captured;
+  else g_launches.fetch_add(1, std::memory_order_relaxed);
 }
 void count_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
-void capture_counting(bool on) { t_capturing = on; }
+uint64_t capture_counting(bool on) {
+  t_capturing = on;
+  if (on) t_captured = 0;
+  return t_captured;
+}
 bool prof_active() { return t_prof_scope && g_prof.enabled; }
 void prof_scope(bool on) { t_prof_scope = on; }
 void prof_begin(int family, cudaStream_t s) {

@@ -46,6 +46,7 @@ struct RateCtx {
   const int64_t *lw;
   int64_t cap;
   uint64_t rk;
+  const uint64_t *rk_dev;  // if set, the round key is read here (replayed round graphs)
   int32_t S, s;
   // M_LP outputs
   int32_t *mv_u, *mv_t, *mv_o;
@@ -80,16 +81,18 @@ struct RateCtx {
 
 __device__ __forceinline__ int64_t node_w(const GView &g, int64_t u) { return g.vw ? g.vw[u] : 1; }
 
+__device__ __forceinline__ uint64_t rk_of(const RateCtx &c) { return c.rk_dev ? *c.rk_dev : c.rk; }
+
 template <int MODE>
 __device__ __forceinline__ bool active(const RateCtx &c, int64_t u) {
-  if (MODE == M_LP) return sub_round_of(hstep(c.rk, (uint64_t)u), c.S) == c.s;
+  if (MODE == M_LP) return sub_round_of(hstep(rk_of(c), (uint64_t)u), c.S) == c.s;
   if (MODE == M_FAV) return c.label[u] == u && c.lw[u] == node_w(c.g, u);
   return c.label[u] == c.blk;
 }
 
 template <int MODE>
 __device__ __forceinline__ uint64_t tie_key(const RateCtx &c, int64_t u) {
-  return MODE == M_REBAL ? 0 : hstep(hstep(c.rk, (uint64_t)u), kTagTie);
+  return MODE == M_REBAL ? 0 : hstep(hstep(rk_of(c), (uint64_t)u), kTagTie);
 }
 
 __device__ __forceinline__ uint32_t slot_of(int32_t x, int logcap) {
@@ -1171,9 +1174,10 @@ ApproveCtx approve_ctx(tp_graph *g, const LpState &st, LpWork &w) {
 constexpr int kBucketSpan = 2048;
 constexpr int kBucketChunks = kBucketSpan / 32;
 
-__global__ void __launch_bounds__(256) k_bucket(const uint8_t *tier, int64_t n, uint64_t rk,
-                                                int32_t S, bool fill, int64_t *cnt,
-                                                int32_t *bucket) {
+__global__ void __launch_bounds__(256) k_bucket(const uint8_t *tier, int64_t n, uint64_t rk_in,
+                                                const uint64_t *rk_dev, int32_t S, bool fill,
+                                                int64_t *cnt, int32_t *bucket) {
+  const uint64_t rk = rk_dev ? *rk_dev : rk_in;
   __shared__ int32_t chunk_cnt[kBucketChunks][32];  // [chunk][sub-round], S <= 32
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const int64_t nblocks = gridDim.x;
@@ -1225,18 +1229,18 @@ __global__ void __launch_bounds__(256) k_bucket(const uint8_t *tier, int64_t n, 
 }  // namespace
 
 void lp_bucket(tp_graph *g, LpWork &w, uint64_t rk, int32_t S, const tp_params &p,
-               cudaStream_t stream) {
+               cudaStream_t stream, const uint64_t *rk_dev) {
   build_tiers(g, p, stream);
   w.bucket_S = 0;
   if (S > 32 || g->tiers.count[TIER_LANE] == 0) return;
   const int64_t nblocks = (g->n + kBucketSpan - 1) / kBucketSpan;
   if (!w.bucket.get()) w.bucket.alloc(std::max<int64_t>(w.n, 1), stream);
   if ((int64_t)w.bucket_off.n < S * nblocks + 1) w.bucket_off.alloc(S * nblocks + 1, stream);
-  launch(k_bucket, (unsigned)nblocks, 256, 0, stream, g->tiers.tier.get(), g->n, rk, S, false,
-         w.bucket_off.get(), w.bucket.get());
+  launch(k_bucket, (unsigned)nblocks, 256, 0, stream, g->tiers.tier.get(), g->n, rk, rk_dev, S,
+         false, w.bucket_off.get(), w.bucket.get());
   exclusive_scan_i64(w.bucket_off.get(), w.bucket_off.get(), S * nblocks, stream);
-  launch(k_bucket, (unsigned)nblocks, 256, 0, stream, g->tiers.tier.get(), g->n, rk, S, true,
-         w.bucket_off.get(), w.bucket.get());
+  launch(k_bucket, (unsigned)nblocks, 256, 0, stream, g->tiers.tier.get(), g->n, rk, rk_dev, S,
+         true, w.bucket_off.get(), w.bucket.get());
   TP_LAUNCH_CHECK();
   w.bucket_S = S;
   w.bucket_nblocks = nblocks;
@@ -1323,13 +1327,15 @@ struct ApprovalGraph {
 };
 
 void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t S, int32_t s,
-                 const tp_params &p, cudaStream_t stream, cudaGraphExec_t approval) {
+                 const tp_params &p, cudaStream_t stream, cudaGraphExec_t approval,
+                 const uint64_t *rk_dev) {
   configure_kernels();
   RateCtx c{};
   c.label = st.label;
   c.lw = st.lw;
   c.cap = st.cap;
   c.rk = rk;
+  c.rk_dev = rk_dev;
   c.S = S;
   c.s = s;
   c.mv_u = w.mv_u.get();
@@ -1354,9 +1360,88 @@ void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t
   prof_end(PF_APPROVE, stream, 0.0);
 }
 
+// Round key of round *r (then r advances): the first node of a replayed
+// round graph.
+__global__ void k_round_key(uint64_t seed, uint64_t tag, uint64_t a, uint64_t b0, int32_t *r,
+                            uint64_t *rk) {
+  *rk = round_key(seed, tag, a, b0 + (uint64_t)*r);
+  *r += 1;
+}
+
+// Small levels: a whole LP round (round key, bucketing, every sub-round's
+// rating and approval) is recorded once as a CUDA graph on a private stream
+// and replayed once per round on the caller's stream, the round key coming
+// from device memory. Levels above this size launch directly (their kernels
+// are long enough to hide launch costs, and their bucket scan would allocate
+// inside the graph).
+constexpr int64_t kRoundGraphMaxN = (int64_t)1 << 19;
+
+bool lp_rounds_graph(tp_graph *g, const LpState &st, LpWork &w, uint64_t seed, uint64_t tag,
+                     uint64_t a, uint64_t b0, int32_t rounds, int32_t S, const tp_params &p,
+                     cudaStream_t stream) {
+  configure_kernels();
+  build_tiers(g, p, stream);  // synchronises; must not run while capturing
+  const int64_t nblocks = (g->n + kBucketSpan - 1) / kBucketSpan;
+  if (S > 32 || S * nblocks > 2048) return false;
+  if (!w.bucket.get()) w.bucket.alloc(std::max<int64_t>(w.n, 1), stream);
+  if ((int64_t)w.bucket_off.n < S * nblocks + 1) w.bucket_off.alloc(S * nblocks + 1, stream);
+  Buf<int32_t> d_r(1, stream);
+  Buf<uint64_t> d_rk(1, stream);
+  TP_CUDA(cudaMemsetAsync(d_r.get(), 0, sizeof(int32_t), stream));
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  struct StreamGuard {
+    cudaStream_t s;
+    ~StreamGuard() { cudaStreamDestroy(s); }
+  } sg{cs};
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  capture_counting(true);
+  bool ok = true;
+  try {
+    launch(k_round_key, 1u, 1u, 0, cs, seed, tag, a, b0, d_r.get(), d_rk.get());
+    lp_bucket(g, w, 0, S, p, cs, d_rk.get());
+    for (int32_t s = 0; s < S; ++s) lp_subround(g, st, w, 0, S, s, p, cs, nullptr, d_rk.get());
+    w.bucket_S = 0;
+  } catch (...) {
+    ok = false;
+  }
+  const uint64_t kernels = capture_counting(false);
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamEndCapture(cs, &graph) != cudaSuccess || !ok || !graph) {
+    (void)cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    return false;
+  }
+  cudaGraphExec_t exec = nullptr;
+  const bool inst = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+  cudaGraphDestroy(graph);
+  if (!inst) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  struct ExecGuard {
+    cudaGraphExec_t e;
+    ~ExecGuard() { cudaGraphExecDestroy(e); }
+  } eg{exec};
+  for (int32_t r = 0; r < rounds; ++r) {
+    TP_CUDA(cudaGraphLaunch(exec, stream));
+    count_launches(kernels);
+  }
+  return true;
+}
+
 void lp_rounds(tp_graph *g, const LpState &st, LpWork &w, uint64_t seed, uint64_t tag, uint64_t a,
                uint64_t b0, int32_t rounds, int32_t S, const tp_params &p, cudaStream_t stream) {
   if (rounds <= 0) return;
+  if (g->n <= kRoundGraphMaxN && !prof_active() &&
+      lp_rounds_graph(g, st, w, seed, tag, a, b0, rounds, S, p, stream))
+    return;
   ApprovalGraph ag(approve_ctx(g, st, w), w.n, w.counters.get());
   for (int32_t r = 0; r < rounds; ++r) {
     uint64_t rk = round_key(seed, tag, a, b0 + (uint64_t)r);

@@ -273,7 +273,9 @@ __device__ __forceinline__ void latch_error(int32_t *err, int32_t code) {
 int num_sms();
 void count_launch();
 void count_launches(uint64_t k);  // kernels a replayed CUDA graph ran
-void capture_counting(bool on);   // launches on this thread are being captured
+// Launches on this thread are being recorded into a CUDA graph (on) or no
+// longer (off, returning how many were recorded since on).
+uint64_t capture_counting(bool on);
 
 // Every kernel of the library is launched through here (counts launches).
 template <class... KArgs, class... Args>
@@ -361,10 +363,11 @@ struct LpWork {
 // approval (nullable): a CUDA graph of this level's approval kernels to
 // replay instead of launching them.
 void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t S, int32_t s,
-                 const tp_params &p, cudaStream_t stream, cudaGraphExec_t approval = nullptr);
+                 const tp_params &p, cudaStream_t stream, cudaGraphExec_t approval = nullptr,
+                 const uint64_t *rk_dev = nullptr);
 // Buckets the lane-tier vertices of round key rk by sub-round (A3).
 void lp_bucket(tp_graph *g, LpWork &w, uint64_t rk, int32_t S, const tp_params &p,
-               cudaStream_t stream);
+               cudaStream_t stream, const uint64_t *rk_dev = nullptr);
 void lp_rounds(tp_graph *g, const LpState &st, LpWork &w, uint64_t seed, uint64_t tag, uint64_t a,
                uint64_t b0, int32_t rounds, int32_t S, const tp_params &p, cudaStream_t stream);
 // ev_begin / ev_end (nullable) are recorded around the LP rounds alone.
