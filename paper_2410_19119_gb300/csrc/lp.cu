@@ -1174,25 +1174,35 @@ ApproveCtx approve_ctx(tp_graph *g, const LpState &st, LpWork &w) {
 constexpr int kBucketSpan = 2048;
 constexpr int kBucketChunks = kBucketSpan / 32;
 
+// Pass 0 hashes every vertex once and keeps its sub-round (+1; 0: not in the
+// lane tier) in sub[]; pass 1 reads it back. Lanes of a 32-vertex chunk with
+// the same sub-round are grouped with one match instruction.
 __global__ void __launch_bounds__(256) k_bucket(const uint8_t *tier, int64_t n, uint64_t rk_in,
                                                 const uint64_t *rk_dev, int32_t S, bool fill,
-                                                int64_t *cnt, int32_t *bucket) {
-  const uint64_t rk = rk_dev ? *rk_dev : rk_in;
+                                                int64_t *cnt, int32_t *bucket, uint8_t *sub_byte) {
   __shared__ int32_t chunk_cnt[kBucketChunks][32];  // [chunk][sub-round], S <= 32
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const int64_t nblocks = gridDim.x;
   const int64_t lo = (int64_t)blockIdx.x * kBucketSpan;
+  for (int i = threadIdx.x; i < kBucketChunks * 32; i += blockDim.x) (&chunk_cnt[0][0])[i] = 0;
+  __syncthreads();
+  const uint64_t rk = fill ? 0 : (rk_dev ? *rk_dev : rk_in);
   int32_t sub_of[kBucketChunks / 8];
   for (int q = 0; q < kBucketChunks / 8; ++q) {
     const int chunk = w + 8 * q;
     const int64_t u = lo + 32 * chunk + lane;
-    const bool lt = u < n && tier[u] == TIER_LANE;
-    const int32_t sub = lt ? sub_round_of(hstep(rk, (uint64_t)u), S) : -1;
-    sub_of[q] = sub;
-    for (int32_t k = 0; k < S; ++k) {
-      const unsigned m = __ballot_sync(kFull, sub == k);
-      if (lane == 0) chunk_cnt[chunk][k] = __popc(m);
+    int32_t sub = -1;
+    if (u < n) {
+      if (fill) {
+        sub = (int32_t)sub_byte[u] - 1;
+      } else {
+        if (tier[u] == TIER_LANE) sub = sub_round_of(hstep(rk, (uint64_t)u), S);
+        sub_byte[u] = (uint8_t)(sub + 1);
+      }
     }
+    sub_of[q] = sub;
+    const unsigned peers = __match_any_sync(kFull, sub);
+    if (sub >= 0 && (peers & lanemask_lt()) == 0) chunk_cnt[chunk][sub] = __popc(peers);
   }
   __syncthreads();
   if (!fill) {
@@ -1217,12 +1227,10 @@ __global__ void __launch_bounds__(256) k_bucket(const uint8_t *tier, int64_t n, 
   for (int q = 0; q < kBucketChunks / 8; ++q) {
     const int chunk = w + 8 * q;
     const int32_t sub = sub_of[q];
-    for (int32_t k = 0; k < S; ++k) {
-      const unsigned m = __ballot_sync(kFull, sub == k);
-      if (sub == k)
-        bucket[cnt[(int64_t)k * nblocks + blockIdx.x] + chunk_cnt[chunk][k] +
-               __popc(m & lanemask_lt())] = (int32_t)(lo + 32 * chunk + lane);
-    }
+    const unsigned peers = __match_any_sync(kFull, sub);
+    if (sub >= 0)
+      bucket[cnt[(int64_t)sub * nblocks + blockIdx.x] + chunk_cnt[chunk][sub] +
+             __popc(peers & lanemask_lt())] = (int32_t)(lo + 32 * chunk + lane);
   }
 }
 
@@ -1235,12 +1243,13 @@ void lp_bucket(tp_graph *g, LpWork &w, uint64_t rk, int32_t S, const tp_params &
   if (S > 32 || g->tiers.count[TIER_LANE] == 0) return;
   const int64_t nblocks = (g->n + kBucketSpan - 1) / kBucketSpan;
   if (!w.bucket.get()) w.bucket.alloc(std::max<int64_t>(w.n, 1), stream);
+  if (!w.bucket_sub.get()) w.bucket_sub.alloc(std::max<int64_t>(w.n, 1), stream);
   if ((int64_t)w.bucket_off.n < S * nblocks + 1) w.bucket_off.alloc(S * nblocks + 1, stream);
   launch(k_bucket, (unsigned)nblocks, 256, 0, stream, g->tiers.tier.get(), g->n, rk, rk_dev, S,
-         false, w.bucket_off.get(), w.bucket.get());
+         false, w.bucket_off.get(), w.bucket.get(), w.bucket_sub.get());
   exclusive_scan_i64(w.bucket_off.get(), w.bucket_off.get(), S * nblocks, stream);
   launch(k_bucket, (unsigned)nblocks, 256, 0, stream, g->tiers.tier.get(), g->n, rk, rk_dev, S,
-         true, w.bucket_off.get(), w.bucket.get());
+         true, w.bucket_off.get(), w.bucket.get(), w.bucket_sub.get());
   TP_LAUNCH_CHECK();
   w.bucket_S = S;
   w.bucket_nblocks = nblocks;
@@ -1384,6 +1393,7 @@ bool lp_rounds_graph(tp_graph *g, const LpState &st, LpWork &w, uint64_t seed, u
   const int64_t nblocks = (g->n + kBucketSpan - 1) / kBucketSpan;
   if (S > 32 || S * nblocks > 2048) return false;
   if (!w.bucket.get()) w.bucket.alloc(std::max<int64_t>(w.n, 1), stream);
+  if (!w.bucket_sub.get()) w.bucket_sub.alloc(std::max<int64_t>(w.n, 1), stream);
   if ((int64_t)w.bucket_off.n < S * nblocks + 1) w.bucket_off.alloc(S * nblocks + 1, stream);
   Buf<int32_t> d_r(1, stream);
   Buf<uint64_t> d_rk(1, stream);
