@@ -898,13 +898,41 @@ __device__ void block_select(int64_t cnt, int64_t rem, Item item, uint64_t &khi,
   __shared__ uint64_t fhi, mhi;
   __shared__ uint32_t flo, mlo;
   __shared__ int64_t cum;
-  if (threadIdx.x == 0) fhi = 0, mhi = 0, flo = 0, mlo = 0, cum = 0;
+  __shared__ unsigned long long and_hi, or_hi;
+  __shared__ unsigned and_lo, or_lo;
+  if (threadIdx.x == 0) {
+    fhi = 0, mhi = 0, flo = 0, mlo = 0, cum = 0;
+    and_hi = ~0ull, or_hi = 0, and_lo = ~0u, or_lo = 0;
+  }
   __syncthreads();
-  for (int pass = 0; pass < 12; ++pass) {
-    for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+  {  // bytes on which every key agrees need no histogram pass
+    unsigned long long ah = ~0ull, oh = 0;
+    unsigned al = ~0u, ol = 0;
+    for (int64_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+      uint64_t hi;
+      uint32_t lo;
+      int64_t w;
+      item(q, hi, lo, w);
+      ah &= hi, oh |= hi, al &= lo, ol |= lo;
+    }
+    atomicAnd(&and_hi, ah), atomicOr(&or_hi, oh), atomicAnd(&and_lo, al), atomicOr(&or_lo, ol);
     __syncthreads();
+  }
+  for (int pass = 0; pass < 12; ++pass) {
     const bool in_hi = pass < 8;
     const int shift = in_hi ? 56 - 8 * pass : 24 - 8 * (pass - 8);
+    const unsigned same = in_hi ? (unsigned)(((and_hi ^ or_hi) >> shift) & 255u)
+                                : ((and_lo ^ or_lo) >> shift) & 255u;
+    if (same == 0) {  // all keys carry this byte: it is the selected key's byte too
+      if (threadIdx.x == 0) {
+        if (in_hi) fhi |= ((uint64_t)and_hi >> shift & 255u) << shift, mhi |= 255ull << shift;
+        else flo |= ((and_lo >> shift) & 255u) << shift, mlo |= 255u << shift;
+      }
+      __syncthreads();
+      continue;
+    }
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
     for (int64_t q = threadIdx.x; q < cnt; q += blockDim.x) {
       uint64_t hi;
       uint32_t lo;
