@@ -73,19 +73,50 @@ __device__ __forceinline__ int64_t bsum(int64_t v) {
 
 // Weighted radix select (same contract as in lp.cu): first key in ascending
 // (hi, lo) order whose inclusive weight prefix exceeds rem.
+// Called only when the keys' total weight exceeds rem, so every pass selects
+// a byte some remaining key carries: bytes on which all keys agree are taken
+// without a histogram pass.
 template <class Item>
 __device__ void ip_select(int64_t cnt, int64_t rem, Item item, uint64_t &khi, uint32_t &klo) {
   __shared__ int64_t hist[256];
   __shared__ uint64_t fhi, mhi;
   __shared__ uint32_t flo, mlo;
   __shared__ int64_t cum;
-  if (threadIdx.x == 0) fhi = 0, mhi = 0, flo = 0, mlo = 0, cum = 0;
+  __shared__ unsigned long long and_hi, or_hi;
+  __shared__ unsigned and_lo, or_lo;
+  if (threadIdx.x == 0) {
+    fhi = 0, mhi = 0, flo = 0, mlo = 0, cum = 0;
+    and_hi = ~0ull, or_hi = 0, and_lo = ~0u, or_lo = 0;
+  }
   __syncthreads();
-  for (int pass = 0; pass < 12; ++pass) {
-    for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+  {
+    unsigned long long ah = ~0ull, oh = 0;
+    unsigned al = ~0u, ol = 0;
+    for (int64_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+      uint64_t hi;
+      uint32_t lo;
+      int64_t w;
+      item(q, hi, lo, w);
+      ah &= hi, oh |= hi, al &= lo, ol |= lo;
+    }
+    atomicAnd(&and_hi, ah), atomicOr(&or_hi, oh), atomicAnd(&and_lo, al), atomicOr(&or_lo, ol);
     __syncthreads();
+  }
+  for (int pass = 0; pass < 12; ++pass) {
     const bool in_hi = pass < 8;
     const int shift = in_hi ? 56 - 8 * pass : 24 - 8 * (pass - 8);
+    const unsigned same = in_hi ? (unsigned)(((and_hi ^ or_hi) >> shift) & 255u)
+                                : ((and_lo ^ or_lo) >> shift) & 255u;
+    if (same == 0) {
+      if (threadIdx.x == 0) {
+        if (in_hi) fhi |= ((uint64_t)and_hi >> shift & 255u) << shift, mhi |= 255ull << shift;
+        else flo |= ((and_lo >> shift) & 255u) << shift, mlo |= 255u << shift;
+      }
+      __syncthreads();
+      continue;
+    }
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
     for (int64_t q = threadIdx.x; q < cnt; q += blockDim.x) {
       uint64_t hi;
       uint32_t lo;

@@ -891,7 +891,9 @@ __global__ void k_approve_scatter(ApproveCtx a) {
 
 // Weighted radix select over 96-bit keys (hi = ~gain, lo = vertex): finds the
 // first key whose inclusive weight prefix exceeds rem and returns it in
-// (khi, klo). Every thread of the block must call it.
+// (khi, klo). Every thread of the block must call it. Called only when the
+// keys' total weight exceeds rem, so every pass selects a byte some remaining
+// key carries: bytes on which all keys agree are taken without a pass.
 template <class Item>
 __device__ void block_select(int64_t cnt, int64_t rem, Item item, uint64_t &khi, uint32_t &klo) {
   __shared__ int64_t hist[256];
