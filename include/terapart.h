@@ -69,7 +69,7 @@ typedef struct {
   /* performance only */
   int32_t tier_lane;     /* max degree rated one lane per vertex (32; 0 = off) */
   int32_t tier_small;    /* max degree rated with the small shared table (64) */
-  int32_t tier_mid;      /* max degree rated with the large shared table (1000) */
+  int32_t tier_mid;      /* max degree rated with the large shared table (512; at most 512) */
   int32_t warps_per_block; /* warps per block in the small tier (8) */
   int32_t use_graphs;    /* reserved, no effect */
   int32_t graph_n;       /* reserved, no effect */

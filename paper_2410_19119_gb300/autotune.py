@@ -18,7 +18,7 @@ from . import default_params, partition_batch
 
 TIER_LANE = (0, 16, 32)
 TIER_SMALL = (32, 64)
-TIER_MID = (256, 1024)
+TIER_MID = (128, 512)
 WARPS_PER_BLOCK = (4, 8)
 CONCURRENCY = (8, 16, 32)
 

@@ -71,7 +71,7 @@ void tp_params_default(tp_params *p) {
   p->max_levels = 64;
   p->tier_lane = 32;
   p->tier_small = 64;
-  p->tier_mid = 1000;
+  p->tier_mid = 512;
   p->warps_per_block = 8;
   p->use_graphs = 1;
   p->graph_n = 1 << 16;

@@ -308,7 +308,7 @@ void build_tiers(tp_graph *g, const tp_params &p, cudaStream_t s) {
   const bool lane_ok = g->unit_ew || g->max_ew < kLaneMaxEdgeWeight;
   int32_t lane_max = lane_ok ? std::max(0, std::min(p.tier_lane, kLaneMaxDeg)) : 0;
   int32_t small_max = std::max(lane_max, std::min(p.tier_small, 64));
-  int32_t mid_max = std::max(small_max, std::min(p.tier_mid, 1024));
+  int32_t mid_max = std::max(small_max, std::min(p.tier_mid, 512));  // tables of 1024 slots
   if (T.built && T.small_max == small_max && T.mid_max == mid_max && T.lane_max == lane_max) return;
   // the old cache is freed on this call's stream: the stream it was built on
   // may be gone (calls on one graph are ordered by the caller)

@@ -8,7 +8,7 @@
 //   small (deg <= tier_small): one warp per vertex, 128-slot shared table, and
 //          for one-window unit-weight neighbourhoods no table at all (lanes
 //          with equal labels are grouped by __match_any_sync);
-//   mid   (deg <= tier_mid):   one warp per vertex, 2048-slot shared table;
+//   mid   (deg <= tier_mid):   one warp per vertex, 1024-slot shared table;
 //   big   (deg <= 10000):      one warp per vertex, table in global memory;
 //   huge  (deg > 10000):       one warp per chunk of 1000 neighbours (the
 //          compressed format's independently decodable chunks) aggregates in
@@ -34,7 +34,8 @@ namespace {
 enum Mode { M_LP = 0, M_FAV = 1, M_REBAL = 2 };
 
 constexpr int kSmallLog = 7;   // 128 slots
-constexpr int kMidLog = 11;    // 2048 slots
+constexpr int kMidLog = 10;    // 1024 slots: mid tier, degree <= 512
+constexpr int kHugeLog = 11;   // 2048 slots: one 1000-neighbour chunk of a hub
 constexpr int kMidWarps = 4;
 constexpr int kHugeWarps = 4;  // warps per block in the chunk kernel
 constexpr int kDecideThreads = 256;
@@ -754,7 +755,7 @@ __global__ void k_rate_list(RateCtx c) {
 template <bool COMP, int MODE>
 __global__ void k_rate_huge_chunks(RateCtx c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  WarpSmem<kMidLog> &ws = reinterpret_cast<WarpSmem<kMidLog> *>(smem_raw)[threadIdx.x >> 5];
+  WarpSmem<kHugeLog> &ws = reinterpret_cast<WarpSmem<kHugeLog> *>(smem_raw)[threadIdx.x >> 5];
   init_table(ws);
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -775,16 +776,16 @@ __global__ void k_rate_huge_chunks(RateCtx c) {
       if (!c.g.ew) {
         unsigned peers = __match_any_sync(kFull, x);
         if (has && (peers & lanemask_lt()) == 0)
-          tbl_add(ws.keys, ws.vals, kMidLog, x, __popc(peers), c.g.err);
+          tbl_add(ws.keys, ws.vals, kHugeLog, x, __popc(peers), c.g.err);
       } else if (has) {
-        tbl_add(ws.keys, ws.vals, kMidLog, x, w, c.g.err);
+        tbl_add(ws.keys, ws.vals, kHugeLog, x, w, c.g.err);
       }
     });
     __syncwarp();
     __threadfence_block();
     int64_t off = c.tbase + c.toff[i];
     int lc = c.tcap[i];
-    for (int s = lane; s < (1 << kMidLog); s += 32) {
+    for (int s = lane; s < (1 << kHugeLog); s += 32) {
       int32_t x = ws.keys[s];
       if (x >= 0) {
         tbl_add(c.tkeys + off, c.tvals + off, lc, x, ws.vals[s], c.g.err);
@@ -1135,7 +1136,7 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
     m.tbase = T.big_slots;
     m.chunk_start = T.huge_chunk_start.get();
     m.n_chunks = T.n_huge_chunks;
-    size_t sm = sizeof(WarpSmem<kMidLog>) * kHugeWarps;
+    size_t sm = sizeof(WarpSmem<kHugeLog>) * kHugeWarps;
     unsigned blocks = (unsigned)std::min<int64_t>((T.n_huge_chunks + kHugeWarps - 1) / kHugeWarps, (int64_t)sms * 8);
     if (comp) launch(k_rate_huge_chunks<true, MODE>, blocks, 32 * kHugeWarps, sm, s, m);
     else launch(k_rate_huge_chunks<false, MODE>, blocks, 32 * kHugeWarps, sm, s, m);
@@ -1155,7 +1156,7 @@ void set_smem_limits(K kernel, size_t bytes) {
 void configure_kernels_once() {
   size_t small16 = sizeof(WarpSmem<kSmallLog>) * 16;
   size_t mid = sizeof(WarpSmem<kMidLog>) * kMidWarps;
-  size_t huge = sizeof(WarpSmem<kMidLog>) * kHugeWarps;
+  size_t huge = sizeof(WarpSmem<kHugeLog>) * kHugeWarps;
 #define TP_CFG_MODE(M)                                              \
   set_smem_limits(k_rate_small<true, M>, small16);                  \
   set_smem_limits(k_rate_small<false, M>, small16);                 \
