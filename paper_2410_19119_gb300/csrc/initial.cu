@@ -35,6 +35,11 @@ struct IPCtx {
   const int32_t *vlist;    // vertices sorted by (node, id)
   const int64_t *nstart;   // node start in vlist
   const int32_t *loc;      // position of a vertex inside its node
+  // the subgraph induced by every node, in local positions: vertex vlist[p]
+  // has neighbours ladj[lxadj[p] .. lxadj[p + 1]) (ascending, as in the graph)
+  const int64_t *lxadj;
+  const int32_t *ladj;
+  const int64_t *lew;  // null: unit
   const int32_t *noff, *nkk;
   int32_t T;
   uint64_t seed;
@@ -145,23 +150,56 @@ __device__ void ip_select(int64_t cnt, int64_t rem, Item item, uint64_t &khi, ui
   __syncthreads();
 }
 
-// Adjacency of a node's vertex is scanned by a whole warp, lanes striding
-// over the neighbours (coalesced, and a hub does not serialise one thread);
-// helpers visit the neighbours of u inside node j as (lane-local) callbacks.
+// Adjacency of a node's vertex (vlist position p) in the node's induced
+// subgraph is scanned by a whole warp, lanes striding over the neighbours
+// (coalesced, and a hub does not serialise one thread); f(in, y, w) is called
+// by every lane for every 32 neighbours, y a position inside the node.
 template <class F>
-__device__ __forceinline__ void node_nbrs(const IPCtx &c, int32_t u, int32_t j, F &&f) {
-  const int64_t b = c.xadj[u], e = c.xadj[u + 1];
+__device__ __forceinline__ void node_nbrs(const IPCtx &c, int64_t p, F &&f) {
+  const int64_t b = c.lxadj[p], e = c.lxadj[p + 1];
   for (int64_t i0 = b; i0 < e; i0 += 32) {
     const int64_t i = i0 + lane_id();
-    bool in = false;
-    int32_t y = 0;
-    int64_t w = 0;
-    if (i < e) {
-      const int32_t v = c.adj[i];
-      in = c.node_of[v] == j;
-      if (in) y = c.loc[v], w = c.ew ? c.ew[i] : 1;
+    const bool in = i < e;
+    f(in, in ? c.ladj[i] : 0, in ? (c.lew ? c.lew[i] : (int64_t)1) : (int64_t)0);
+  }
+}
+
+// Induced subgraphs of all nodes of a depth: neighbour counts, then (after a
+// scan into lxadj) the neighbours' positions, one warp per listed vertex.
+__global__ void k_local_deg(const int64_t *xadj, const int32_t *adj, const int32_t *node_of,
+                            const int32_t *vlist, int64_t m, int64_t *ldeg) {
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = gw; p < m; p += nw) {
+    const int32_t u = vlist[p], j = node_of[u];
+    int64_t k = 0;
+    for (int64_t i = xadj[u] + lane_id(); i < xadj[u + 1]; i += 32) k += node_of[adj[i]] == j;
+    k = warp_sum(k);
+    if (lane_id() == 0) ldeg[p] = k;
+  }
+}
+
+__global__ void k_local_fill(const int64_t *xadj, const int32_t *adj, const int64_t *ew,
+                             const int32_t *node_of, const int32_t *loc, const int32_t *vlist,
+                             int64_t m, const int64_t *lxadj, int32_t *ladj, int64_t *lew) {
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = gw; p < m; p += nw) {
+    const int32_t u = vlist[p], j = node_of[u];
+    int64_t pos = lxadj[p];
+    const int64_t b = xadj[u], e = xadj[u + 1];
+    for (int64_t i0 = b; i0 < e; i0 += 32) {
+      const int64_t i = i0 + lane_id();
+      int32_t v = 0;
+      const bool in = i < e && node_of[v = adj[i]] == j;
+      const unsigned msk = __ballot_sync(kFull, in);
+      if (in) {
+        const int64_t at = pos + __popc(msk & lanemask_lt());
+        ladj[at] = loc[v];
+        if (lew) lew[at] = ew[i];
+      }
+      pos += __popc(msk);
     }
-    f(in, y, w);
   }
 }
 
@@ -214,13 +252,13 @@ __global__ void __launch_bounds__(kIPThreads, 1) k_bisect(IPCtx c) {
     if (fb >= fe) break;
     // every undiscovered neighbour is claimed by its earliest frontier vertex
     for (int64_t i = fb + warp; i < fe; i += nwarps)
-      node_nbrs(c, vs[ord[i]], j, [&](bool in, int32_t y, int64_t) {
+      node_nbrs(c, nb + ord[i], [&](bool in, int32_t y, int64_t) {
         if (in && !disc[y]) atomicMin(&claimer[y], (int32_t)i);
       });
     __syncthreads();
     for (int64_t i = fb + warp; i < fe; i += nwarps) {
       int32_t k = 0;
-      node_nbrs(c, vs[ord[i]], j, [&](bool in, int32_t y, int64_t) {
+      node_nbrs(c, nb + ord[i], [&](bool in, int32_t y, int64_t) {
         k += __popc(__ballot_sync(kFull, in && !disc[y] && claimer[y] == i));
       });
       if (lane == 0) cnt[i - fb] = k;
@@ -230,7 +268,7 @@ __global__ void __launch_bounds__(kIPThreads, 1) k_bisect(IPCtx c) {
     // claimed neighbours in frontier order, then adjacency order
     for (int64_t i = fb + warp; i < fe; i += nwarps) {
       int64_t pos = tail + cnt[i - fb];
-      node_nbrs(c, vs[ord[i]], j, [&](bool in, int32_t y, int64_t) {
+      node_nbrs(c, nb + ord[i], [&](bool in, int32_t y, int64_t) {
         const bool mine = in && !disc[y] && claimer[y] == i;
         const unsigned m = __ballot_sync(kFull, mine);
         if (mine) ord[pos + __popc(m & lanemask_lt())] = y;
@@ -306,7 +344,7 @@ __global__ void __launch_bounds__(kIPThreads, 1) k_bisect(IPCtx c) {
       for (int64_t q = warp; q < nact; q += nwarps) {
         const int32_t x = cnt[q];
         int64_t r0 = 0, r1 = 0;
-        node_nbrs(c, vs[x], j, [&](bool in, int32_t y, int64_t w) {
+        node_nbrs(c, nb + x, [&](bool in, int32_t y, int64_t w) {
           if (in) (side[y] ? r1 : r0) += w;
         });
         r0 = warp_sum(r0);
@@ -364,7 +402,7 @@ __global__ void __launch_bounds__(kIPThreads, 1) k_bisect(IPCtx c) {
   int64_t cutv = 0;
   for (int64_t x = warp; x < ns; x += nwarps) {
     const int32_t sx = side[x];
-    node_nbrs(c, vs[x], j, [&](bool in, int32_t y, int64_t w) {
+    node_nbrs(c, nb + x, [&](bool in, int32_t y, int64_t w) {
       if (in && side[y] != sx) cutv += w;
     });
   }
@@ -454,6 +492,25 @@ void initial_partition(const tp_graph *g, int32_t k, int64_t l_max, const tp_par
       launch(k_node_lists, grid_for(m, 256), 256, 0, s, keys.get(), nstart.get(), m, vlist.get(), loc.get());
       TP_LAUNCH_CHECK();
     }
+    // induced subgraph of every node in local positions
+    const bool weighted = !g->unit_ew;
+    Buf<int64_t> lxadj(m + 1, s);
+    Buf<int32_t> ladj;
+    Buf<int64_t> lew;
+    if (m) {
+      const unsigned wg = grid_for(m * 32, 256);
+      launch(k_local_deg, wg, 256, 0, s, g->xadj.get(), g->adj.get(), node_of.get(), vlist.get(), m,
+             lxadj.get());
+      TP_LAUNCH_CHECK();
+      exclusive_scan_i64(lxadj.get(), lxadj.get(), m, s);
+      const int64_t lm = read_scalar(lxadj.get() + m, s);
+      ladj.alloc(std::max<int64_t>(lm, 1), s);
+      if (weighted) lew.alloc(std::max<int64_t>(lm, 1), s);
+      launch(k_local_fill, wg, 256, 0, s, g->xadj.get(), g->adj.get(),
+             weighted ? g->ew.get() : nullptr, node_of.get(), loc.get(), vlist.get(), m, lxadj.get(),
+             ladj.get(), weighted ? lew.get() : nullptr);
+      TP_LAUNCH_CHECK();
+    }
     // children of every node at the next depth (-1: leaf, assign the block)
     std::vector<int32_t> c0(nodes), c1(nodes), noff, nkk;
     for (int32_t jn = 0; jn < nodes; ++jn) {
@@ -478,6 +535,9 @@ void initial_partition(const tp_graph *g, int32_t k, int64_t l_max, const tp_par
     c.vlist = vlist.get();
     c.nstart = nstart.get();
     c.loc = loc.get();
+    c.lxadj = lxadj.get();
+    c.ladj = ladj.get();
+    c.lew = weighted ? lew.get() : nullptr;
     c.noff = d_off.get();
     c.nkk = d_kk.get();
     c.T = T;
