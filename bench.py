@@ -177,6 +177,25 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Element-wise maximum of a list of floats over all ranks (identity
+    without a process group): the slowest rank sets every time."""
+    if dist is None:
+        return list(values)
+    import torch
+
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def shard(count, rank, ws):
+    """Indices of independent work units (graphs, requests) owned by a rank:
+    round robin, so every rank gets a similar size mix; no unit is shared and
+    no collective touches the data path."""
+    return list(range(rank, count, ws))
+
+
 def cpu_oracle_lp(xadj, adj, k, seed, max_rounds=5, budget_s=12.0):
     """Oracle level-0 clustering rounds (one thread) until the budget is spent."""
     import oracle
@@ -268,7 +287,15 @@ def run_batch(args, w):
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
-    recipe = synth.batch_recipe(w["count"], seed=w["seed"])
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    # weak scaling: count graphs per GPU, every rank its own shard of a
+    # recipe of count * ws graphs (independent problems, no collective)
+    recipe_all = synth.batch_recipe(w["count"] * ws, seed=w["seed"])
+    recipe = [recipe_all[i] for i in shard(len(recipe_all), rank, ws)]
     t0 = time.perf_counter()
     csr = [synth.batch_graph(s) for s in recipe]
     gen_s = time.perf_counter() - t0
@@ -292,6 +319,8 @@ def run_batch(args, w):
         times.append(time.perf_counter() - t0)
     launches = tp.launch_count() - l0
     batch_s = statistics.median(times)
+    if dist:
+        dist.barrier()
     # the plain single-graph path, default knobs, one stream
     p0 = tp.default_params(seed=w["seed"])
     torch.cuda.synchronize()
@@ -300,6 +329,12 @@ def run_batch(args, w):
     torch.cuda.synchronize()
     plain_s = time.perf_counter() - t0
     same = all(bool(torch.equal(a[0], b[0])) for a, b in zip(out, plain))
+    batch_s, plain_s, same_f = max_over_ranks([batch_s, plain_s, 0.0 if same else 1.0], dist,
+                                              "cuda")
+    same = same_f == 0.0
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
     if rank != 0:
         return
     knobs = {f: getattr(params, f) for f in ("tier_lane", "tier_small", "tier_mid",
@@ -549,10 +584,7 @@ def run_native(args, w):
     lp_edges = rounds * m2 * args.steps
     lp_ms_z = sum(r["stz"]["ms_lp_level0"] for r in recs)
     lp_ms_c = sum(r["stc"]["ms_lp_level0"] for r in recs)
-    if dist:
-        t = torch.tensor([total_ms, lp_ms_z, lp_ms_c], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, lp_ms_z, lp_ms_c = t.tolist()
+    total_ms, lp_ms_z, lp_ms_c = max_over_ranks([total_ms, lp_ms_z, lp_ms_c], dist, "cuda")
     value = ws * lp_edges / lp_ms_z / 1e6
     gteps_csr = ws * lp_edges / lp_ms_c / 1e6
 
@@ -577,10 +609,7 @@ def run_native(args, w):
         if i >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
     e2e_step = sum(e2e_ms) / len(e2e_ms)
-    if dist:
-        t = torch.tensor([e2e_step], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_step = t.item()
+    (e2e_step,) = max_over_ranks([e2e_step], dist, "cuda")
     e2e_value = ws * rounds * m2 / e2e_step / 1e6
 
     if rank != 0:

@@ -1,0 +1,77 @@
+"""Multi-rank host logic on the CPU (two gloo ranks): independent work units
+are sharded over ranks with no collective on the data path, every unit's
+result is the one a single process computes, and timings reduce to the
+slowest rank. The GPU path runs one replica per rank the same way."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+import bench
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+dist = pytest.importorskip("torch.distributed")
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, ws, port, recipe, out_q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(ws))
+    import torch.distributed as d
+
+    d.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        mine = bench.shard(len(recipe), rank, ws)
+        results = {}
+        for i in mine:
+            xadj, adj = synth.batch_graph(recipe[i])
+            part, st = oracle.partition(oracle.Graph(xadj, adj), recipe[i]["k"], 0.03,
+                                        oracle.Params(seed=1))
+            results[i] = (part.tolist(), st["cut"])
+        gathered = [None] * ws
+        d.all_gather_object(gathered, results)  # test only: collect the shards
+        slowest = bench.max_over_ranks([10.0 * (rank + 1), -float(rank)], d)
+        if rank == 0:
+            merged = {}
+            for g in gathered:
+                merged.update(g)
+            out_q.put((merged, slowest))
+    finally:
+        d.destroy_process_group()
+
+
+def test_sharded_units_equal_single_process():
+    recipe = synth.batch_recipe(10, seed=5, log2_lo=8.0, log2_hi=10.0)
+    ws = 2
+    assert sorted(sum((bench.shard(len(recipe), r, ws) for r in range(ws)), [])) == list(
+        range(len(recipe)))
+    ctx = torch.multiprocessing.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, ws, port, recipe, q)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    merged, slowest = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert slowest == [20.0, 0.0]  # element-wise max over the two ranks
+    assert sorted(merged) == list(range(len(recipe)))
+    for i, spec in enumerate(recipe):
+        xadj, adj = synth.batch_graph(spec)
+        part, st = oracle.partition(oracle.Graph(xadj, adj), spec["k"], 0.03, oracle.Params(seed=1))
+        assert merged[i][0] == part.tolist() and merged[i][1] == st["cut"], i
+
+
+def test_helpers_without_a_process_group():
+    assert bench.max_over_ranks([1.5, 2.0]) == [1.5, 2.0]
+    assert bench.shard(5, 0, 1) == [0, 1, 2, 3, 4]
+    assert bench.shard(5, 1, 2) == [1, 3]
