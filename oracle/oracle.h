@@ -18,9 +18,10 @@
  *   orc_two_hop                           pinned (cap + grouping invariants, hand cases)
  *   orc_contract                          pinned (weight sums, identity, all-in-one)
  *   orc_initial_partition, orc_refine,
- *   orc_rebalance, orc_partition          pinned by invariants only (balance, cut
- *                                          bounds, projection preserves cut);
- *                                          the heuristic itself has no closed form
+ *   orc_rebalance, orc_partition          parity unpinned beyond invariants
+ *                                          (balance, cut bounds, projection
+ *                                          preserves cut): the heuristic itself
+ *                                          has no closed form
  */
 #ifndef TERAPART_ORACLE_H
 #define TERAPART_ORACLE_H
