@@ -76,8 +76,6 @@ struct RateCtx {
   const int32_t *bucket;
   const int64_t *bucket_off;
   int64_t bucket_nb;
-  // lane tier: work-class thresholds (degree for CSR, record bytes compressed)
-  int64_t lane_cls[3];
 };
 
 __device__ __forceinline__ int64_t node_w(const GView &g, int64_t u) { return g.vw ? g.vw[u] : 1; }
@@ -313,17 +311,15 @@ __global__ void k_rate_small(RateCtx c) {
 // ---------------------------------------------------------------- lane tier
 // Low-degree vertices, one lane per vertex, so a warp keeps 32
 // neighbourhoods in flight. Each warp step:
-//   1. fetches a window of up to 128 active vertices (this sub-round's
-//      bucket list, or a scan of 256-vertex slabs) and partitions it stably
-//      into four work classes (degree; compressed: record length), so each
-//      batch of 32 that follows has lanes of similar degree;
-//   2. per batch, every lane stages its compressed record in its own
-//      shared-memory column with independent 16-byte loads (the next batch's
-//      records are prefetched to L2 meanwhile), reads its degree from the
-//      record's and the next record's headers, and decodes its neighbours
-//      one VarInt at a time straight into label gathers held in registers
-//      (CSR: the adjacency entries directly), so every gather is in flight
-//      before the first one is used;
+//   1. takes a window of up to 128 active vertices (this sub-round's bucket
+//      list, or a scan of 256-vertex slabs) and rates it as four batches of
+//      32 in list order;
+//   2. per batch, every lane loads its compressed record at once (five
+//      16-byte groups; the next batch's records are prefetched to L2
+//      meanwhile) and decodes it a 32-bit word at a time into its column of
+//      shared memory; the gaps are then summed into neighbour ids while the
+//      label gathers are issued, all of them before the first is used (CSR:
+//      the adjacency entries directly);
 //   3. the labels are sorted with Batcher's odd-even merge network of 16 or
 //      32 elements (picked per batch), so equal labels form runs whose
 //      lengths (summed weights) are the ratings;
@@ -404,15 +400,6 @@ __device__ __forceinline__ int lane_decode(const GView &g, int32_t u, uint32_t *
     }
   }
   return min(max(idx, 0), kLaneMaxDeg);
-}
-
-// Work class 0..3 of a lane-tier vertex: its degree (CSR) or record length
-// in bytes (compressed) against three ascending thresholds.
-template <bool COMP>
-__device__ __forceinline__ int lane_class(const RateCtx &c, int64_t u) {
-  const int64_t len = COMP ? (int64_t)(off_at(c.g, u + 1) - off_at(c.g, u))
-                           : c.g.xadj[u + 1] - c.g.xadj[u];
-  return (len > c.lane_cls[0]) + (len > c.lane_cls[1]) + (len > c.lane_cls[2]);
 }
 
 template <bool COMP>
@@ -631,16 +618,11 @@ __global__ void __launch_bounds__(lane_warps<W>() * 32, W ? 1 : kLaneBlocksPerSM
     base = c.g.n;  // no slab scan
   }
   for (;;) {
-    int take;
-    int32_t e[4];
+    int take, wstart = 0;
     if (list_mode) {
       if (bnext >= bcount) break;
+      wstart = bnext;
       take = bcount - bnext < kLaneWin ? bcount - bnext : kLaneWin;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int i = lane + 32 * j;
-        e[j] = i < take ? blist[bnext + i] : -1;
-      }
       // never step past the end (keeps bnext below 2^31)
       bnext = bcount - bnext > nw * kLaneWin ? bnext + nw * kLaneWin : bcount;
     } else {
@@ -656,34 +638,16 @@ __global__ void __launch_bounds__(lane_warps<W>() * 32, W ? 1 : kLaneBlocksPerSM
       if (pending == 0) break;
       __syncwarp();
       take = pending < kLaneWin ? pending : kLaneWin;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int i = lane + 32 * j;
-        e[j] = i < take ? queue[i] : -1;
-      }
-      __syncwarp();
     }
-    // stable partition of the window into work classes
-    int cls[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) cls[j] = e[j] >= 0 ? lane_class<COMP>(c, e[j]) : 4;
-    int cursor = 0;
-#pragma unroll
-    for (int cl = 0; cl < 4; ++cl) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const bool m = cls[j] == cl;
-        const unsigned b = __ballot_sync(kFull, m);
-        if (m) queue[cursor + __popc(b & lanemask_lt())] = e[j];
-        cursor += __popc(b);
-      }
-    }
-    __syncwarp();
+    // batches of 32 in list order: vertices close in the list are close in
+    // the graph, so a batch's records and label gathers share cache lines
+    // (grouping a window by degree instead was measured slower)
+    const int32_t *win = list_mode ? blist + wstart : queue;
     int nmv = 0;  // movers of this window so far (warp-uniform)
     for (int q = 0; q < take; q += 32) {
       const bool has = q + lane < take;
-      const int32_t u = has ? queue[q + lane] : 0;
-      if (q + 32 + lane < take) lane_prefetch<COMP>(c.g, queue[q + 32 + lane]);
+      const int32_t u = has ? win[q + lane] : 0;
+      if (q + 32 + lane < take) lane_prefetch<COMP>(c.g, win[q + 32 + lane]);
       int deg = 0;
       if (has) {
         if (COMP) deg = lane_decode(c.g, u, col);
@@ -1057,14 +1021,6 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
   if (n_lane > 0) {
     if (prof) prof_begin(PF_RATE_LANE, s);
     constexpr int LM = MODE == M_REBAL ? M_LP : MODE;
-    // work classes: degree <= 8, 16, 24 (compressed: the record length those
-    // degrees take at this stream's bytes per adjacency entry)
-    for (int i = 0; i < 3; ++i) {
-      const int64_t d = 8 * (i + 1);
-      c.lane_cls[i] = comp && g->m2 > 0
-                          ? (int64_t)((double)d * (double)g->nbytes / (double)g->m2 + 0.5)
-                          : d;
-    }
     if (g->unit_ew) {
       unsigned blocks = (unsigned)std::min<int64_t>(
           (g->n + 256 * kLaneWarps - 1) / (256 * kLaneWarps), (int64_t)sms * kLaneBlocksPerSM);
