@@ -75,3 +75,27 @@ def test_helpers_without_a_process_group():
     assert bench.max_over_ranks([1.5, 2.0]) == [1.5, 2.0]
     assert bench.shard(5, 0, 1) == [0, 1, 2, 3, 4]
     assert bench.shard(5, 1, 2) == [1, 3]
+
+
+def test_autotune_candidates_and_sample():
+    from paper_2410_19119_gb300 import autotune
+
+    cands = list(autotune.candidates())
+    keys = {tuple(sorted(c.items())) for c in cands}
+    assert len(keys) == len(cands) == (len(autotune.TIER_LANE) * len(autotune.TIER_SMALL) *
+                                       len(autotune.TIER_MID) * len(autotune.WARPS_PER_BLOCK))
+    assert all(c["tier_mid"] <= 512 for c in cands)  # the mid tier's table holds degree <= 512
+
+    class G:
+        def __init__(self, n, m2):
+            self.n, self._m2 = n, m2
+
+        def info(self):
+            return {"m2": self._m2}
+
+    gs = [G(n, 8 * n) for n in (5, 900, 30, 7000, 400, 12, 65000, 2000)]
+    idx = autotune.sample_indices(gs, 4)
+    assert len(idx) == 4 and len(set(idx)) == 4
+    sizes = sorted(gs[i].n for i in idx)
+    assert sizes[0] == 5 and sizes[-1] >= 2000  # spread from the smallest upwards
+    assert sorted(autotune.sample_indices(gs, 99)) == list(range(len(gs)))
