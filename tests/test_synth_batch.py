@@ -55,3 +55,18 @@ def test_batch_recipe():
         assert len(xadj) == spec["n"] + 1
         _csr_ok(xadj, adj)
         assert abs(len(adj) / spec["n"] - spec["deg"]) < 0.25 * spec["deg"]
+
+
+def test_serving_recipe():
+    import bench
+
+    w = bench.WORKLOADS["serve"]
+    r = bench.serve_recipe(w)
+    assert r == bench.serve_recipe(w) and len(r) == w["count"]
+    resident = [x for x in r if x["resident"]]
+    assert len(resident) == w["count"] // 8  # every 8th request
+    ks = [x["k"] for x in r]
+    assert min(ks) >= 2 and max(ks) <= 1024 and len(set(ks)) > 20  # log-uniform over [2, 1024]
+    ns = [x["n"] for x in r if not x["resident"]]
+    assert min(ns) >= 2 ** w["log2_lo"] and max(ns) <= 2 ** w["log2_hi"]
+    assert {x["gen"] for x in r if not x["resident"]} == set(synth.BATCH_GENERATORS)
