@@ -633,6 +633,12 @@ def run_native(args, w):
                     "traffic": ncu_traffic(top, args.workload),
                     "alg_bytes_per_launch": per_launch_bytes, "launch_ms": per_launch_ms,
                     "launches": e["launches"]}
+        try:  # the same rate counted in CSR-equivalent (decoded) bytes
+            comp_round = r0["zstream"] + 4.0 * (n + 1) + 4.0 * m2 + 12.0 * n
+            csr_round = 8.0 * (n + 1) + 4.0 * m2 + 4.0 * m2 + 12.0 * n
+            roofline["decoded_equivalent_gbs"] = achieved * csr_round / comp_round
+        except Exception:
+            pass
     line = {
         "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
