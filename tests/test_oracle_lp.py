@@ -156,3 +156,65 @@ def test_two_hop_shared_favourite():
     np.add.at(Wc, C, 1)
     oracle.two_hop(g, C, Wc, 3, 1, 0)
     assert list(C) == [0, 0, 0, 3, 3, 3, 6, 6, 6, 9]
+
+
+def _two_hop_restated(xadj, adj, ew, vw, C, Wc, U, seed, level):
+    """Two-hop packing written out from its definition: singletons (C[u] = u
+    and Wc[u] = c(u)) keyed by their favourite cluster (best rating ignoring
+    the cap; n if none), sorted by (key, u); inside a key, exclusive weight
+    prefix P puts u in bin P // U unless it straddles the bin's end (then it
+    stays alone); every bin becomes one cluster named after its first member."""
+    n = len(xadj) - 1
+    TWOHOP, TIE = 0x54776F486F704D74, 0x5469654272656B72  # tags "TwoHopMt", "TieBrekr"
+    rk = bf.round_key(seed, TWOHOP, level, 0)
+    single = [u for u in range(n) if C[u] == u and Wc[u] == vw[u]]
+    keyed = []
+    for u in single:
+        hv = bf.step(bf.step(rk, u), TIE)
+        ok, t, _ = bf.rate(xadj, adj, ew, vw, u, C, Wc, n, None, True, hv)
+        keyed.append((t if ok else n, u))
+    keyed.sort()
+    out = C.copy()
+    i = 0
+    while i < len(keyed):
+        j = i
+        while j < len(keyed) and keyed[j][0] == keyed[i][0]:
+            j += 1
+        P, first = 0, {}
+        for _, u in keyed[i:j]:
+            b = P // U
+            if P + vw[u] <= (b + 1) * U:
+                first.setdefault(b, u)
+                out[u] = first[b]
+            P += vw[u]
+        i = j
+    return out
+
+
+def _two_hop_case(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(8, 21))
+    xadj, adj, ew, vw = bf.random_graph(rng, n, float(rng.uniform(0.05, 0.35)), max_w=3)
+    reps = [u for u in range(n) if rng.random() < 0.8]
+    C = np.arange(n, dtype=np.int32)
+    for u in range(n):  # some vertices already joined another representative
+        if u not in reps and reps and rng.random() < 0.5:
+            C[u] = reps[int(rng.integers(len(reps)))]
+    Wc = np.zeros(n, np.int64)
+    np.add.at(Wc, C, vw)
+    return xadj, adj, ew, vw, C, Wc, int(rng.integers(3, 11))
+
+
+def test_two_hop_cases_exercise_packing():
+    moved = [int(np.sum(_two_hop_restated(*_two_hop_case(s), 5, 2) != _two_hop_case(s)[4]))
+             for s in range(12)]
+    assert sum(m > 0 for m in moved) >= 8 and sum(moved) >= 20
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_two_hop_by_restatement(seed):
+    xadj, adj, ew, vw, C, Wc, U = _two_hop_case(seed)
+    want = _two_hop_restated(xadj, adj, ew, vw, C, Wc, U, 5, 2)
+    got = C.copy()
+    oracle.two_hop(oracle.Graph(xadj, adj, vw=vw, ew=ew), got, Wc.copy(), U, 5, 2)
+    assert list(got) == list(want)
