@@ -17,8 +17,12 @@
  *                                                  approval vs subset enumeration)
  *   orc_two_hop                           pinned (cap + grouping invariants, hand cases)
  *   orc_contract                          pinned (weight sums, identity, all-in-one)
- *   orc_initial_partition, orc_refine,
- *   orc_rebalance, orc_partition          parity unpinned beyond invariants
+ *   orc_initial_partition                 growing step pinned (BFS order,
+ *                                          prefix and attempt choice restated
+ *                                          for k = 2); recursion + 2-way LP:
+ *                                          parity unpinned beyond invariants
+ *   orc_refine, orc_rebalance,
+ *   orc_partition                         parity unpinned beyond invariants
  *                                          (balance, cut bounds, projection
  *                                          preserves cut): the heuristic itself
  *                                          has no closed form

@@ -143,3 +143,59 @@ def test_partition_k1_and_empty():
     g0 = oracle.Graph(np.zeros(1, np.int64), np.zeros(0, np.int32))
     part, st = oracle.partition(g0, 4, 0.03, oracle.Params())
     assert len(part) == 0 and st["cut"] == 0
+
+
+def _bfs_growing_restated(xadj, adj, ew, vw, seed, attempts):
+    """k = 2 without 2-way refinement, written out from the definition: per
+    attempt a, FIFO breadth-first order from vertex round_key(seed, ip-seed,
+    node key, a) mod n (neighbours in ascending id, unreached vertices
+    appended in ascending id); side 0 is the longest prefix of that order of
+    weight <= floor(W * 1 / 2); the attempt with the smallest cut wins (the
+    lowest attempt on ties)."""
+    from collections import deque
+
+    n = len(xadj) - 1
+    IPSEED = 0x495053656564566B  # "IPSeedVk"
+    key = (0 << 32) | 2  # root node: block offset 0, two blocks
+    W = int(np.sum(vw))
+    target0 = (W * 1) // 2
+    best = None
+    for a in range(attempts):
+        s0 = bf.round_key(seed, IPSEED, key, a) % n
+        seen = [False] * n
+        order = [s0]
+        seen[s0] = True
+        q = deque([s0])
+        while q:
+            u = q.popleft()
+            for e in range(xadj[u], xadj[u + 1]):
+                v = int(adj[e])
+                if not seen[v]:
+                    seen[v] = True
+                    order.append(v)
+                    q.append(v)
+        order += [u for u in range(n) if not seen[u]]
+        side = np.ones(n, np.int32)
+        acc = 0
+        for u in order:
+            acc += int(vw[u])
+            if acc > target0:
+                break
+            side[u] = 0
+        c = bf.cut(xadj, adj, ew, side)
+        if best is None or c < best[0]:
+            best = (c, side)
+    return best[1]
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_bfs_growing_bisection_by_restatement(seed):
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(5, 40))
+    xadj, adj, ew, vw = bf.random_graph(rng, n, float(rng.uniform(0.05, 0.3)), max_w=3)
+    W = int(np.sum(vw))
+    l_max = W  # no cap binds: the growing step alone decides
+    got = oracle.initial_partition(oracle.Graph(xadj, adj, vw=vw, ew=ew), 2, l_max,
+                                   oracle.Params(seed=7, refine_rounds=0, ip_attempts=8))
+    want = _bfs_growing_restated(xadj, adj, ew, vw, 7, 8)
+    assert list(got) == list(want)
