@@ -120,12 +120,15 @@ tp_status tp_graph_from_csr(int64_t n, const int64_t *xadj, const int32_t *adj,
  * relative to the neighbourhood start and chunks of 1 000 neighbours, each
  * chunk starting with VarInt(2|v0-u| + [v0<u]) followed by VarInt gaps; a
  * terminal header holding 2m sits at off[n]. Offsets are u32 when the stream
- * is below 4 GiB, else u64. TP_ERR_INVALID for weighted graphs or an already
+ * is below 4 GiB, else u64 (u64 for any stream when the environment variable
+ * TP_OFFSETS_U64 is "1", to check the wide-offset path on small graphs; the
+ * results do not depend on the width). TP_ERR_INVALID for weighted graphs or an already
  * compressed input. Synchronises (to size the output). */
 tp_status tp_graph_compress(const tp_graph *csr, void *stream, tp_graph **out);
 
 /* Makes a compressed graph from a stream in the format above: nbytes bytes
- * and n+1 u64 offsets (host_ptrs as for tp_graph_from_csr; copied in). Every
+ * and n+1 u64 offsets (host_ptrs as for tp_graph_from_csr; copied in; kept
+ * on the device as u32 or u64 by the rule of tp_graph_compress). Every
  * neighbourhood is decoded once on the device to validate it; a malformed
  * stream (bad header, truncated VarInt, id out of range, wrong chunk table,
  * unsorted ids) gives TP_ERR_CORRUPT. Synchronises. */

@@ -592,6 +592,15 @@ static void finish_graph_stats(tp_graph *g, cudaStream_t s) {
   g->max_ew = g->unit_ew ? 1 : max_i64(g->ew.get(), g->m2, s);
 }
 
+// Offsets are u32 while the byte stream is below 4 GiB, else u64. Setting
+// TP_OFFSETS_U64=1 in the environment selects u64 offsets for any stream, so
+// that the wide-offset path can be checked on small graphs.
+static bool wide_offsets(uint64_t nbytes) {
+  if (nbytes >= (1ull << 32)) return true;
+  const char *e = getenv("TP_OFFSETS_U64");
+  return e && e[0] == '1' && e[1] == 0;
+}
+
 tp_graph *compress(const tp_graph *c, cudaStream_t s) {
   TP_REQUIRE(!c->compressed && c->unit_ew && c->unit_vw, TP_ERR_INVALID);
   tp_graph *z = new_graph();
@@ -625,7 +634,7 @@ tp_graph *compress(const tp_graph *c, cudaStream_t s) {
     }
     launch(k_zip_terminal, 1, 1, 0, s, (uint64_t)body, c->m2, z->bytes.get());
     TP_LAUNCH_CHECK();
-    z->off_is64 = z->nbytes >= (1ull << 32);
+    z->off_is64 = wide_offsets(z->nbytes);
     if (z->off_is64) {
       z->off64.alloc(n + 1, s);
       launch(k_off_copy, grid_for(n + 1, 256), 256, 0, s, off.get(), n + 1, z->off64.get());
@@ -712,7 +721,7 @@ tp_graph *from_compressed(int64_t n, uint64_t nbytes, const uint8_t *bytes, cons
     TP_CUDA(cudaStreamSynchronize(s));
     for (int64_t u = 0; u <= n; ++u)
       TP_REQUIRE(ho[u] < nbytes && (u == 0 || ho[u] >= ho[u - 1]), TP_ERR_CORRUPT);
-    z->off_is64 = nbytes >= (1ull << 32);
+    z->off_is64 = wide_offsets(nbytes);
     if (z->off_is64) {
       z->off64 = std::move(o);
     } else {

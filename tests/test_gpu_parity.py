@@ -88,6 +88,32 @@ def test_from_compressed_validates():
     assert e.value.code == 4
 
 
+def test_wide_offsets(monkeypatch):
+    """u64 offsets (chosen from 4 GiB of stream on; forced here on small
+    graphs) give the same stream, clusterings and partitions as u32 ones."""
+    monkeypatch.setenv("TP_OFFSETS_U64", "1")
+    for xadj, adj in (_star_path(12000), synth.rmat(12, 16, seed=5)):
+        n = len(xadj) - 1
+        og = oracle.Graph(xadj, adj)
+        want_data, want_off = oracle.encode(xadj, adj)
+        want_c = oracle.cluster(og, 30, oracle.Params(seed=5), 0)
+        want_p, _ = oracle.partition(og, 8, 0.03, oracle.Params(seed=5))
+        for z in (tp.graph_from_csr(xadj, adj).compress(),
+                  tp.graph_from_compressed(n, want_data, want_off)):
+            inf = z.info()
+            assert inf["compressed"] and inf["bytes"] == inf["stream_bytes"] + 8 * (n + 1)
+            data, off = z.export_compressed()
+            assert np.array_equal(_host(off).astype(np.uint64), want_off)
+            assert np.array_equal(_host(data), want_data)
+            x2, a2, _, _ = z.decompress().export_csr()
+            assert np.array_equal(_host(x2), xadj) and np.array_equal(_host(a2), adj)
+            got = tp.lp_cluster(z, 30, tp.default_params(seed=5), 0)
+            assert np.array_equal(_host(got), want_c)
+            part, _ = tp.partition(z, 8, 0.03, tp.default_params(seed=5))
+            assert np.array_equal(_host(part), want_p)
+            z.check()
+
+
 def test_rejects_invalid_csr():
     xadj, adj = synth.gnm(100, 400, 1)
     bad = adj.copy()
