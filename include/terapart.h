@@ -280,7 +280,10 @@ tp_status tp_partition_batch(int32_t count, tp_graph *const *graphs, const int32
 typedef struct tp_server tp_server;
 
 typedef struct {
-  const tp_graph *graph; /* resident device graph (not owned), or NULL: */
+  const tp_graph *graph; /* resident device graph (not owned; the server runs one
+                            request on it at a time, and the caller must not use
+                            or destroy it while a request on it is queued or
+                            running), or NULL: */
   int64_t n;             /*   host CSR with n vertices, uploaded per request */
   const int64_t *xadj;   /*   host, n + 1 entries; must stay valid until waited */
   const int32_t *adj;    /*   host, xadj[n] entries, same lifetime */
@@ -316,7 +319,8 @@ tp_status tp_server_create(int64_t budget_bytes, int32_t workers, const tp_param
 tp_status tp_server_submit(tp_server *sv, const tp_request *req, uint64_t *ticket);
 
 /* Blocks until the request is done, fills stats and info (both nullable)
- * and returns its status; a ticket can be waited once. */
+ * and returns its status; a ticket can be waited once (TP_ERR_INVALID for
+ * an unknown ticket, one already waited, or one another thread waits on). */
 tp_status tp_server_wait(tp_server *sv, uint64_t ticket, tp_stats *stats, tp_request_info *info);
 
 /* Largest sum of footprints the server has had running at once. */

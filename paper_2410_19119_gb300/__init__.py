@@ -8,6 +8,7 @@ This module marshals arguments only. PyTorch provides device memory and
 streams; numpy arrays are accepted as host inputs.
 """
 import ctypes
+import threading
 
 import numpy as np
 
@@ -277,6 +278,7 @@ class Server:
                                      ctypes.byref(h)), "tp_server_create")
         self._h = h
         self._pending = {}
+        self._lock = threading.Lock()
 
     def submit(self, k, eps=0.03, xadj=None, adj=None, graph=None, compress=False):
         """Queues a request on a host CSR (xadj, adj numpy) or a resident Graph;
@@ -297,15 +299,20 @@ class Server:
         t = ctypes.c_uint64()
         check(lib().tp_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)),
               "tp_server_submit")
-        self._pending[t.value] = (part, n, keep, graph)
+        with self._lock:
+            self._pending[t.value] = (part, n, keep, graph)
         return t.value
 
     def wait(self, ticket):
         """(partition numpy int32, stats dict, info dict) of a submitted request."""
+        with self._lock:  # a ticket is waited once
+            entry = self._pending.pop(ticket, None)
+        if entry is None:
+            raise TpError(1, "tp_server_wait (unknown or already waited ticket)")
+        part, n, _, _ = entry
         st, info = Stats(), RequestInfo()
-        code = lib().tp_server_wait(self._h, ticket, ctypes.byref(st), ctypes.byref(info))
-        part, n, _, _ = self._pending.pop(ticket)
-        check(code, "tp_server_wait")
+        check(lib().tp_server_wait(self._h, ticket, ctypes.byref(st), ctypes.byref(info)),
+              "tp_server_wait")
         return part[:n], stats_dict(st), {f: getattr(info, f) for f, _ in RequestInfo._fields_}
 
     def peak_in_use(self):

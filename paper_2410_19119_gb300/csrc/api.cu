@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -326,7 +327,13 @@ tp_status tp_partition_batch(int32_t count, tp_graph *const *graphs, const int32
   const int32_t nthreads = std::min(concurrency, std::min(count, 256));
   std::vector<std::thread> pool;
   pool.reserve((size_t)nthreads - 1);
-  for (int32_t t = 1; t < nthreads; ++t) pool.emplace_back(worker);
+  for (int32_t t = 1; t < nthreads; ++t) {
+    try {
+      pool.emplace_back(worker);
+    } catch (const std::system_error &) {
+      break;  // fewer threads: the shared counter still hands out every graph
+    }
+  }
   worker();
   for (std::thread &t : pool) t.join();
   tp_status first = TP_OK;

@@ -16,6 +16,8 @@
 #include <deque>
 #include <memory>
 #include <mutex>
+#include <new>
+#include <system_error>
 #include <thread>
 #include <unordered_map>
 #include <unordered_set>
@@ -40,6 +42,7 @@ struct Request {
   tp_request r;
   int64_t need = 0;  // admitted footprint (bytes)
   int state = 0;     // 0 queued, 1 running, 2 done
+  bool waited = false;  // a waiter holds this request (a ticket is waited once)
   tp_status status = TP_OK;
   tp_stats stats{};
   int64_t peak = 0;
@@ -163,7 +166,12 @@ tp_status tp_server_create(int64_t budget_bytes, int32_t workers, const tp_param
     delete sv;
     return TP_ERR_CUDA;
   }
-  for (int32_t i = 0; i < workers; ++i) sv->workers.emplace_back([sv] { sv->worker(); });
+  try {
+    for (int32_t i = 0; i < workers; ++i) sv->workers.emplace_back([sv] { sv->worker(); });
+  } catch (const std::system_error &) {
+    tp_server_destroy(sv);  // stops and joins the workers already started
+    return TP_ERR_OOM;
+  }
   *out = sv;
   return TP_OK;
 }
@@ -176,16 +184,32 @@ tp_status tp_server_submit(tp_server *sv, const tp_request *req, uint64_t *ticke
   int64_t m2 = r.graph ? r.graph->m2 : (r.xadj && r.n >= 0 ? r.xadj[r.n] : -1);
   if (n < 0 || m2 < 0 || (n > 0 && !r.part) || (!r.graph && (!r.xadj || (m2 > 0 && !r.adj))))
     return TP_ERR_INVALID;
-  auto q = std::make_unique<Request>();
+  std::unique_ptr<Request> q;
+  try {
+    q = std::make_unique<Request>();
+  } catch (const std::bad_alloc &) {
+    return TP_ERR_OOM;
+  }
   q->r = r;
   q->need = tp_footprint_bytes(n, m2, r.k, r.graph ? 0 : 1, r.graph ? 0 : r.compress);
   if (q->need > sv->budget) return TP_ERR_BUDGET;
   q->t_submit = Clock::now();
   std::lock_guard<std::mutex> lk(sv->mu);
   if (sv->stopping) return TP_ERR_INVALID;
-  *ticket = sv->next_ticket++;
-  sv->queue.push_back(*ticket);
-  sv->reqs.emplace(*ticket, std::move(q));
+  const uint64_t t = sv->next_ticket;
+  try {
+    sv->reqs.emplace(t, std::move(q));
+    try {
+      sv->queue.push_back(t);
+    } catch (const std::bad_alloc &) {
+      sv->reqs.erase(t);
+      throw;
+    }
+  } catch (const std::bad_alloc &) {
+    return TP_ERR_OOM;
+  }
+  ++sv->next_ticket;
+  *ticket = t;
   sv->cv_work.notify_all();
   return TP_OK;
 }
@@ -196,6 +220,8 @@ tp_status tp_server_wait(tp_server *sv, uint64_t ticket, tp_stats *stats, tp_req
   auto it = sv->reqs.find(ticket);
   if (it == sv->reqs.end()) return TP_ERR_INVALID;
   Request *q = it->second.get();
+  if (q->waited) return TP_ERR_INVALID;  // another thread is already waiting on it
+  q->waited = true;
   sv->cv_done.wait(lk, [&] { return q->state == 2; });
   if (stats) *stats = q->stats;
   if (info) {

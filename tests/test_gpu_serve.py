@@ -1,6 +1,8 @@
 """Serving with continuous batching: every request's result equals its
 partition alone (and the oracle), admission keeps the running footprints
 within the budget, and the footprint bound holds for every request."""
+import threading
+
 import numpy as np
 import pytest
 
@@ -65,6 +67,27 @@ def test_budget_admission(mix):
             x, a = host[int(np.argmax(fps))]
             sv.submit(ks[int(np.argmax(fps))], 0.03, xadj=x, adj=a, compress=True)
     assert all(i["peak_bytes"] <= i["footprint_bytes"] for i in infos)
+
+
+def test_ticket_is_waited_once(mix):
+    recipe, host, ks, _, _ = mix
+    x, a = host[-1]
+    with tp.Server(budget_bytes=1 << 36, workers=2) as sv:
+        t = sv.submit(ks[-1], 0.03, xadj=x, adj=a)
+        # two waits on one ticket from two threads, through the C-ABI: exactly
+        # one gets the request's status, the other TP_ERR_INVALID
+        codes = []
+        ths = [threading.Thread(target=lambda: codes.append(
+            tp.lib().tp_server_wait(sv._h, t, None, None))) for _ in range(2)]
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+        assert sorted(codes) == [0, 1]
+        t2 = sv.submit(ks[0], 0.03, xadj=host[0][0], adj=host[0][1])
+        part, _, _ = sv.wait(t2)
+        with pytest.raises(tp.TpError):
+            sv.wait(t2)
 
 
 def test_footprint_bound_large_and_skewed():
