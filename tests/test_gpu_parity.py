@@ -284,6 +284,55 @@ def test_partition_parity_families(kind, k, compressed):
     assert st["cut"] == wst["cut"] and st["level_n"] == wst["level_n"]
 
 
+def _degree_boundaries(leaves=30000, seed=12):
+    # hubs whose degrees sit on both sides of every tier boundary and of the
+    # chunking threshold (10 000 / 10 001 neighbours, chunks of 1 000), over
+    # leaves joined by a path and random edges
+    degs = [1, 31, 32, 33, 63, 64, 65, 511, 512, 513, 1000, 9999, 10000, 10001, 10999, 11000]
+    h = len(degs)
+    rng = np.random.default_rng(seed)
+    edges = set()
+    for i, d in enumerate(degs):
+        for v in rng.choice(leaves, d, replace=False):
+            edges.add((i, h + int(v)))
+    for v in range(leaves - 1):
+        edges.add((h + v, h + v + 1))
+    for a, b in rng.integers(0, leaves, size=(2 * leaves, 2)):
+        if a != b:
+            edges.add((h + int(min(a, b)), h + int(max(a, b))))
+    n = h + leaves
+    nb = [[] for _ in range(n)]
+    for a, b in edges:
+        nb[a].append(b)
+        nb[b].append(a)
+    xadj = np.zeros(n + 1, np.int64)
+    xadj[1:] = np.cumsum([len(x) for x in nb])
+    adj = np.concatenate([np.sort(np.array(x, np.int32)) for x in nb]).astype(np.int32)
+    assert list(np.diff(xadj)[:h]) == degs
+    return xadj, adj
+
+
+@pytest.mark.parametrize("compressed", [False, True])
+def test_degree_boundaries(compressed):
+    xadj, adj = _degree_boundaries()
+    og = oracle.Graph(xadj, adj)
+    g = tp.graph_from_csr(xadj, adj)
+    if compressed:
+        g = g.compress()
+        data, off = g.export_compressed()
+        want_data, want_off = oracle.encode(xadj, adj)
+        assert np.array_equal(_host(off).astype(np.uint64), want_off)
+        assert np.array_equal(_host(data), want_data)
+    for U, level in ((40, 0), (20000, 1)):
+        want = oracle.cluster(og, U, oracle.Params(seed=11), level)
+        got = tp.lp_cluster(g, U, tp.default_params(seed=11), level)
+        assert np.array_equal(_host(got), want), U
+    want, wst = oracle.partition(og, 16, 0.03, oracle.Params(seed=11))
+    part, st = tp.partition(g, 16, 0.03, tp.default_params(seed=11))
+    assert np.array_equal(_host(part), want) and st["cut"] == wst["cut"]
+    g.check()
+
+
 def test_performance_knobs_do_not_change_results():
     xadj, adj = synth.rmat(14, 16, seed=6)
     og = oracle.Graph(xadj, adj)
