@@ -15,13 +15,17 @@
  *   orc_varint_*, orc_encode, orc_decode  pinned (hand-computed bytes, round trip)
  *   orc_lp_*                              pinned (brute-force argmax, cap invariant,
  *                                                  approval vs subset enumeration)
- *   orc_two_hop                           pinned (cap + grouping invariants, hand cases)
+ *   orc_two_hop                           pinned (hand cases, restated packing)
+ *   orc_cluster                           pinned (rounds by enumeration + restated
+ *                                                  packing)
  *   orc_contract                          pinned (weight sums, identity, all-in-one)
  *   orc_initial_partition                 growing step pinned (BFS order,
  *                                          prefix and attempt choice restated
  *                                          for k = 2); recursion + 2-way LP:
  *                                          parity unpinned beyond invariants
- *   orc_refine, orc_rebalance,
+ *   orc_refine                            pinned: rounds restated by
+ *                                          enumeration (blocks as labels)
+ *   orc_rebalance                         pinned: brute-force restatement
  *   orc_partition                         parity unpinned beyond invariants
  *                                          (balance, cut bounds, projection
  *                                          preserves cut): the heuristic itself

@@ -218,3 +218,96 @@ def test_two_hop_by_restatement(seed):
     got = C.copy()
     oracle.two_hop(oracle.Graph(xadj, adj, vw=vw, ew=ew), got, Wc.copy(), U, 5, 2)
     assert list(got) == list(want)
+
+
+# Round tags spelled out from their ASCII names ("LPClustr", "LPRefine",
+# "TieBrekr"), independently of the oracle's own constants.
+TAG_CLUSTER = int.from_bytes(b"LPClustr", "big")
+TAG_REFINE = int.from_bytes(b"LPRefine", "big")
+TAG_TIE = int.from_bytes(b"TieBrekr", "big")
+
+
+def _rounds_restated(xadj, adj, ew, vw, label, lw, nlabels, cap, seed, tag, level, rounds, S):
+    """LP rounds from their definition: round r uses key (seed, tag, level, r)
+    and runs sub-rounds 0..S-1, each by enumeration."""
+    for r in range(rounds):
+        rk = bf.round_key(seed, tag, level, r)
+        for s in range(S):
+            label, lw = bf.subround(xadj, adj, ew, vw, label, lw, nlabels, cap, rk, S, s, TAG_TIE)
+    return label, lw
+
+
+def _level_case(seed):
+    rng, xadj, adj, ew, vw = _tiny(700 + seed, n=int(np.random.default_rng(seed).integers(8, 14)),
+                                   p=0.4, max_w=4)
+    p = oracle.Params(seed=int(rng.integers(1, 2**40)), cluster_rounds=int(rng.integers(1, 6)),
+                      refine_rounds=int(rng.integers(1, 6)), sub_rounds=int(rng.integers(1, 5)))
+    return rng, xadj, adj, ew, vw, p, int(rng.integers(0, 6))
+
+
+def _cluster_case(seed):
+    rng, xadj, adj, ew, vw, p, level = _level_case(seed)
+    return xadj, adj, ew, vw, p, level, int(rng.integers(int(vw.max()), 14))
+
+
+def _refine_case(seed):
+    rng, xadj, adj, ew, vw, p, level = _level_case(seed)
+    n = len(xadj) - 1
+    k = int(rng.integers(2, 5))
+    part = rng.integers(0, k, n).astype(np.int32)
+    B = np.bincount(part, weights=vw, minlength=k).astype(np.int64)
+    l_max = int(B.max()) + int(rng.integers(0, 5))  # some blocks can take moves, some not
+    return xadj, adj, ew, vw, p, level, k, part, B, l_max
+
+
+def _cluster_restated(xadj, adj, ew, vw, p, level, U):
+    n = len(xadj) - 1
+    label, lw = _rounds_restated(xadj, adj, ew, vw, np.arange(n, dtype=np.int32), vw.copy(), n,
+                                 np.full(n, U, np.int64), p.seed, TAG_CLUSTER, level,
+                                 p.cluster_rounds, p.sub_rounds)
+    if p.two_hop:
+        label = _two_hop_restated(xadj, adj, ew, vw, label, lw, U, p.seed, level)
+    return label
+
+
+def _refine_restated(xadj, adj, ew, vw, p, level, k, part, B, l_max):
+    return _rounds_restated(xadj, adj, ew, vw, part.copy(), B.copy(), k,
+                            np.full(k, l_max, np.int64), p.seed, TAG_REFINE, level,
+                            p.refine_rounds, p.sub_rounds)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_cluster_level_by_restatement(seed):
+    # one coarsening level's clustering: the LP rounds with the cluster keys,
+    # then two-hop packing of what stayed alone
+    xadj, adj, ew, vw, p, level, U = _cluster_case(seed)
+    g = oracle.Graph(xadj, adj, vw=vw, ew=ew)
+    for two_hop in (0, 1):
+        p.two_hop = two_hop
+        want = _cluster_restated(xadj, adj, ew, vw, p, level, U)
+        assert list(oracle.cluster(g, U, p, level)) == list(want), two_hop
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_refine_level_by_restatement(seed):
+    # k-way refinement: the same LP with blocks as labels, block weights as
+    # label weights, L_max as every block's cap and the refinement keys
+    xadj, adj, ew, vw, p, level, k, part, B, l_max = _refine_case(seed)
+    want, want_B = _refine_restated(xadj, adj, ew, vw, p, level, k, part, B, l_max)
+    got, got_B = part.copy(), B.copy()
+    oracle.refine(oracle.Graph(xadj, adj, vw=vw, ew=ew), got, got_B, k, l_max, p, level)
+    assert list(got) == list(want) and list(got_B) == list(want_B)
+
+
+def test_level_restatements_exercise_moves():
+    # the cases above are not vacuous: most of them move vertices
+    moved_c = moved_r = 0
+    for seed in range(10):
+        xadj, adj, ew, vw, p, level, U = _cluster_case(seed)
+        p.two_hop = 0
+        lab = _cluster_restated(xadj, adj, ew, vw, p, level, U)
+        moved_c += int(np.any(lab != np.arange(len(xadj) - 1)))
+        case = _refine_case(seed)
+        lab, _ = _refine_restated(*case)
+        moved_r += int(np.any(lab != case[7]))
+    assert moved_c >= 8 and moved_r >= 5, (moved_c, moved_r)
