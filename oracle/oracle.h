@@ -19,16 +19,16 @@
  *   orc_cluster                           pinned (rounds by enumeration + restated
  *                                                  packing)
  *   orc_contract                          pinned (weight sums, identity, all-in-one)
- *   orc_initial_partition                 growing step pinned (BFS order,
- *                                          prefix and attempt choice restated
- *                                          for k = 2); recursion + 2-way LP:
- *                                          parity unpinned beyond invariants
+ *   orc_initial_partition                 pinned: recursive bisection
+ *                                          restated (growing, 2-way LP by
+ *                                          enumeration, recursion)
  *   orc_refine                            pinned: rounds restated by
  *                                          enumeration (blocks as labels)
  *   orc_rebalance                         pinned: brute-force restatement
  *   orc_partition                         parity unpinned beyond invariants
  *                                          (balance, cut bounds, projection
- *                                          preserves cut): the heuristic itself
+ *                                          preserves cut) and its pinned
+ *                                          stages: the heuristic as a whole
  *                                          has no closed form
  */
 #ifndef TERAPART_ORACLE_H

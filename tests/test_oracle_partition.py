@@ -199,3 +199,112 @@ def test_bfs_growing_bisection_by_restatement(seed):
                                    oracle.Params(seed=7, refine_rounds=0, ip_attempts=8))
     want = _bfs_growing_restated(xadj, adj, ew, vw, 7, 8)
     assert list(got) == list(want)
+
+
+def _recursive_bisection_restated(xadj, adj, ew, vw, k, l_max, seed, attempts, rounds, S):
+    """Initial partitioning written out from its definition: a tree node owns
+    an ascending vertex list and the blocks [offset, offset + kk); with
+    k0 = ceil(kk/2), k1 = floor(kk/2) it works on the induced subgraph in
+    local ids, grows side 0 by BFS from a hashed seed up to floor(W k0 / kk)
+    in every attempt, runs the 2-way LP (blocks {0, 1}, caps k0 L_max and
+    k1 L_max, keys (seed, ip-lp, node key, (attempt << 8) + round)), keeps the
+    smallest cut (lowest attempt on ties) and recurses into both sides."""
+    from collections import deque
+
+    IPSEED = int.from_bytes(b"IPSeedVk", "big")
+    IPLP = int.from_bytes(b"IPLP2Way", "big")
+    TIE = int.from_bytes(b"TieBrekr", "big")
+    part = np.zeros(len(xadj) - 1, np.int32)
+
+    def node(vs, kk, offset):
+        if kk == 1:
+            part[vs] = offset
+            return
+        ns = len(vs)
+        if ns == 0:
+            return
+        k0, k1 = (kk + 1) // 2, kk // 2
+        loc = {int(v): i for i, v in enumerate(vs)}
+        sx, sa, se = [0], [], []
+        for v in vs:
+            for e in range(xadj[v], xadj[v + 1]):
+                if int(adj[e]) in loc:
+                    sa.append(loc[int(adj[e])])
+                    se.append(int(ew[e]))
+            sx.append(len(sa))
+        sx, sa, se = np.array(sx, np.int64), np.array(sa, np.int32), np.array(se, np.int64)
+        svw = np.array([int(vw[v]) for v in vs], np.int64)
+        W = int(svw.sum())
+        target0 = W * k0 // kk
+        caps = np.array([k0 * l_max, k1 * l_max], np.int64)
+        key = (offset << 32) | kk
+        best = None
+        for a in range(attempts):
+            s0 = bf.round_key(seed, IPSEED, key, a) % ns
+            seen = [False] * ns
+            order, q = [s0], deque([s0])
+            seen[s0] = True
+            while q:
+                x = q.popleft()
+                for e in range(sx[x], sx[x + 1]):
+                    y = int(sa[e])
+                    if not seen[y]:
+                        seen[y] = True
+                        order.append(y)
+                        q.append(y)
+            order += [x for x in range(ns) if not seen[x]]
+            side = np.ones(ns, np.int32)
+            acc = 0
+            for x in order:
+                if acc + int(svw[x]) > target0:
+                    break
+                acc += int(svw[x])
+                side[x] = 0
+            lw = np.array([acc, W - acc], np.int64)
+            for r in range(rounds):
+                rk = bf.round_key(seed, IPLP, key, (a << 8) + r)
+                for s in range(S):
+                    side, lw = bf.subround(sx, sa, se, svw, side, lw, 2, caps, rk, S, s, TIE)
+            c = bf.cut(sx, sa, se, side)
+            if best is None or c < best[0]:
+                best = (c, side.copy())
+        side = best[1]
+        node(vs[side == 0], k0, offset)
+        node(vs[side == 1], k1, offset + k0)
+
+    node(np.arange(len(xadj) - 1), k, 0)
+    return part
+
+
+def _ip_case(seed):
+    rng = np.random.default_rng(400 + seed)
+    n = int(rng.integers(6, 30))
+    xadj, adj, ew, vw = bf.random_graph(rng, n, float(rng.uniform(0.08, 0.35)), max_w=3)
+    k = int(rng.integers(2, 7))
+    W = int(np.sum(vw))
+    l_max = -(-W // k) + int(rng.integers(0, 3))  # ceil(W/k) plus a little slack
+    p = oracle.Params(seed=int(rng.integers(1, 2**40)), refine_rounds=int(rng.integers(0, 4)),
+                      sub_rounds=int(rng.integers(1, 4)), ip_attempts=int(rng.integers(1, 5)))
+    return xadj, adj, ew, vw, k, l_max, p
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_initial_partition_by_restatement(seed):
+    xadj, adj, ew, vw, k, l_max, p = _ip_case(seed)
+    got = oracle.initial_partition(oracle.Graph(xadj, adj, vw=vw, ew=ew), k, l_max, p)
+    want = _recursive_bisection_restated(xadj, adj, ew, vw, k, l_max, p.seed, p.ip_attempts,
+                                         p.refine_rounds, p.sub_rounds)
+    assert list(got) == list(want)
+
+
+def test_initial_partition_cases_exercise_lp():
+    # the 2-way LP changes the grown sides in several of the cases above
+    changed = 0
+    for seed in range(12):
+        xadj, adj, ew, vw, k, l_max, p = _ip_case(seed)
+        a = _recursive_bisection_restated(xadj, adj, ew, vw, k, l_max, p.seed, p.ip_attempts,
+                                          p.refine_rounds, p.sub_rounds)
+        b = _recursive_bisection_restated(xadj, adj, ew, vw, k, l_max, p.seed, p.ip_attempts, 0,
+                                          p.sub_rounds)
+        changed += int(list(a) != list(b))
+    assert changed >= 4, changed
