@@ -25,11 +25,11 @@
  *   orc_refine                            pinned: rounds restated by
  *                                          enumeration (blocks as labels)
  *   orc_rebalance                         pinned: brute-force restatement
- *   orc_partition                         parity unpinned beyond invariants
- *                                          (balance, cut bounds, projection
- *                                          preserves cut) and its pinned
- *                                          stages: the heuristic as a whole
- *                                          has no closed form
+ *   orc_partition                         pinned: driver restated (caps,
+ *                                          stop rules, projection, rebalance
+ *                                          then refine) over the pinned stages,
+ *                                          plus invariants (balance, cut
+ *                                          bounds, projection preserves cut)
  */
 #ifndef TERAPART_ORACLE_H
 #define TERAPART_ORACLE_H

@@ -1,6 +1,7 @@
 """Pins for the oracle's balance caps, cut, projection, initial partitioning,
 rebalancing, refinement and the multilevel driver (problem statement of the
 paper's introduction; Sections "The Multilevel Scheme" and "KaMinPar")."""
+import math
 import os
 
 import numpy as np
@@ -308,3 +309,61 @@ def test_initial_partition_cases_exercise_lp():
                                           p.sub_rounds)
         changed += int(list(a) != list(b))
     assert changed >= 4, changed
+
+
+def _multilevel_restated(xadj, adj, k, eps, p):
+    """The multilevel driver written out from its definition, with the
+    (separately pinned) oracle stages as steps: caps from integer ppm
+    arithmetic; coarsen while n > c_lim k and fewer than max_levels graphs
+    exist, discarding a level that keeps more than 95% of the vertices;
+    initial partition of the coarsest graph; then from coarsest to finest:
+    project, rebalance if some block exceeds L_max, refine."""
+    g = oracle.Graph(xadj, adj)
+    W = g.n
+    ppm = int(math.floor(eps * 1e6 + 0.5))
+    U = max(1, ppm * W // (10**6 * k))
+    l_max = (10**6 + ppm) * (-(-W // k)) // 10**6
+    levels, maps, level_n = [g], [], [g.n]
+    if k > 1:
+        while levels[-1].n > p.c_lim * k and len(levels) < min(p.max_levels, 64):
+            fine = levels[-1]
+            C = oracle.cluster(fine, U, p, len(levels) - 1)
+            coarse, mp = oracle.contract(fine, C)
+            if 20 * coarse.n > 19 * fine.n:
+                break
+            levels.append(coarse)
+            maps.append(mp)
+            level_n.append(coarse.n)
+    L = len(levels) - 1
+    cur = np.zeros(levels[L].n, np.int32)
+    if k > 1:
+        cur = oracle.initial_partition(levels[L], k, l_max, p).copy()
+    for lv in range(L, -1, -1):
+        if lv < L:
+            cur = cur[maps[lv]].astype(np.int32)
+        if k > 1:
+            B = oracle.block_weights(levels[lv], cur, k)
+            if B.max() > l_max:
+                oracle.rebalance(levels[lv], cur, B, k, l_max)
+            oracle.refine(levels[lv], cur, B, k, l_max, p, lv)
+    return cur, level_n, l_max
+
+
+def _ml_cases():
+    return [
+        ("rgg", synth.rgg2d(3000, 12.0, 5), 4, 0.03, oracle.Params(seed=3, c_lim=20)),
+        ("gnm", synth.gnm(2500, 9000, 6), 5, 0.0, oracle.Params(seed=4, c_lim=16)),
+        ("rmat", synth.rmat(11, 8, seed=7), 8, 0.03, oracle.Params(seed=5, c_lim=10, two_hop=0)),
+        ("rgg-2lv", synth.rgg2d(2000, 10.0, 8), 3, 0.1, oracle.Params(seed=6, c_lim=5,
+                                                                      max_levels=2)),
+        ("gnm-k1", synth.gnm(500, 2000, 9), 1, 0.03, oracle.Params(seed=7)),
+    ]
+
+
+@pytest.mark.parametrize("case", range(5))
+def test_multilevel_driver_by_restatement(case):
+    name, (xadj, adj), k, eps, p = _ml_cases()[case]
+    want, level_n, l_max = _multilevel_restated(xadj, adj, k, eps, p)
+    got, st = oracle.partition(oracle.Graph(xadj, adj), k, eps, p)
+    assert list(got) == list(want), name
+    assert st["level_n"] == level_n and st["l_max"] == l_max, name
