@@ -58,9 +58,29 @@ WORKLOADS = {
 }
 EPS = 0.03
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e data-sheet bandwidth, the second denominator
 KERNEL_NAMES = {"rate_lane": "k_rate_lane", "rate_small": "k_rate_small",
                 "rate_mid": "k_rate_list (shared tables)", "rate_big": "k_rate_list (global tables)",
                 "rate_huge": "k_rate_huge_chunks + k_rate_huge_decide"}
+
+
+def host_cpu():
+    """CPU model and logical core count of the host that runs the oracle."""
+    import platform
+
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                key, _, val = ln.partition(":")
+                fields.setdefault(key.strip(), val.strip())
+    except OSError:
+        pass
+    model = fields.get("model name")
+    if not model and fields.get("CPU part"):
+        model = f"{platform.machine()} implementer {fields.get('CPU implementer', '?')} " \
+                f"part {fields['CPU part']}"
+    return {"model": model or platform.machine(), "nproc": os.cpu_count()}
 
 
 def make_graph(w):
@@ -254,7 +274,7 @@ def run_reference(args, w):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic", "config": {"workload": w["desc"]},
             "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "host": host_cpu()},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -495,7 +515,7 @@ def run_batch_reference(args, w):
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": w["desc"]},
             "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "host": host_cpu()},
             "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -630,6 +650,7 @@ def run_native(args, w):
         roofline = {"kernel": KERNEL_NAMES[top] + " (level-0 LP rating, compressed graph)",
                     "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                     "frac": achieved / hbm, "peak_source": peak_kind,
+                    "peak_nominal": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                     "traffic": ncu_traffic(top, args.workload),
                     "alg_bytes_per_launch": per_launch_bytes, "launch_ms": per_launch_ms,
                     "launches": e["launches"]}
@@ -670,7 +691,8 @@ def run_native(args, w):
         v, rounds_done, dt = cpu_oracle_lp(xadj, adj, k, w["seed"])
         line["cpu_baseline"] = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                                 "sample": f"{rounds_done} level-0 LP clustering round(s) of the "
-                                          f"full CSR graph in {dt:.1f} s, one thread"}
+                                          f"full CSR graph in {dt:.1f} s, one thread",
+                                "host": host_cpu()}
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

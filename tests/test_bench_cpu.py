@@ -42,6 +42,7 @@ def _check_line(line, steps, warmup, unit):
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["sample"]
     assert cb["value"] == line["value"] and cb["unit"] == unit
+    assert cb["host"]["model"] and cb["host"]["nproc"] >= 1
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == unit
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
@@ -96,3 +97,22 @@ def test_profile_summary_fields():
         assert t == float(fields["dram_bytes_per_launch"])
     else:
         assert t is None
+
+
+def test_host_cpu_from_arm_cpuinfo(monkeypatch, tmp_path):
+    # Arm kernels list implementer and part numbers instead of a model name
+    fake = tmp_path / "cpuinfo"
+    fake.write_text("processor\t: 0\nBogoMIPS\t: 2000.00\nCPU implementer\t: 0x41\n"
+                    "CPU part\t: 0xd4f\n\nprocessor\t: 1\nCPU part\t: 0xd4f\n")
+    real_open = open
+
+    def fake_open(path, *a, **k):
+        return real_open(fake if path == "/proc/cpuinfo" else path, *a, **k)
+
+    monkeypatch.setattr("builtins.open", fake_open)
+    sys.path.insert(0, ROOT)
+    import bench
+
+    h = bench.host_cpu()
+    assert "implementer 0x41" in h["model"] and "part 0xd4f" in h["model"]
+    assert h["nproc"] >= 1
