@@ -49,6 +49,9 @@ def _load():
             "orc_encoded_size": (i64, [i64, vp, vp]),
             "orc_encode": (i64, [i64, vp, vp, vp, vp]),
             "orc_decode": (ctypes.c_int, [i64, vp, i64, vp, vp, vp, i64]),
+            "orc_encode_ex": (i64, [i64, vp, vp, vp, ctypes.c_int, vp, vp]),
+            "orc_decode_ex": (ctypes.c_int, [i64, vp, i64, vp, ctypes.c_int, ctypes.c_int, vp, vp,
+                                             vp, i64]),
             "orc_rate_vertex": (ctypes.c_int, [vp, i64, vp, vp, i64, vp, ctypes.c_int, u64, vp, vp]),
             "orc_rate_vertex_sorted": (ctypes.c_int, [vp, i64, vp, vp, i64, vp, ctypes.c_int, u64, vp, vp]),
             "orc_lp_subround": (i64, [vp, vp, vp, i64, i64, vp, u64, i32, i32]),
@@ -182,6 +185,41 @@ def decode(n, data, off, m2_cap):
     if r != 0:
         raise ValueError("corrupt compressed graph")
     return xadj, adj[: xadj[n]]
+
+
+def encode_ex(xadj, adj, ew=None, intervals=True):
+    """Interval + weight format: returns (bytes uint8[nbytes], off uint64[n+1])."""
+    xadj = np.ascontiguousarray(xadj, np.int64)
+    adj = np.ascontiguousarray(adj, np.int32)
+    ewp = None
+    if ew is not None:
+        ew = np.ascontiguousarray(ew, np.int64)
+        ewp = ew.ctypes.data
+    n = len(xadj) - 1
+    lib = _load()
+    size = lib.orc_encode_ex(n, xadj.ctypes.data, adj.ctypes.data, ewp, int(intervals), None, None)
+    out = np.zeros(max(size, 1), np.uint8)
+    off = np.zeros(n + 1, np.uint64)
+    got = lib.orc_encode_ex(n, xadj.ctypes.data, adj.ctypes.data, ewp, int(intervals),
+                            out.ctypes.data, off.ctypes.data)
+    assert got == size
+    return out[:size], off
+
+
+def decode_ex(n, data, off, m2_cap, intervals=True, weighted=False):
+    """Returns (xadj, adj, ew) of an interval + weight stream (ew all ones
+    when the stream holds no weights)."""
+    data = np.ascontiguousarray(data, np.uint8)
+    off = np.ascontiguousarray(off, np.uint64)
+    xadj = np.zeros(n + 1, np.int64)
+    adj = np.zeros(max(m2_cap, 1), np.int32)
+    ew = np.ones(max(m2_cap, 1), np.int64)
+    r = _load().orc_decode_ex(n, data.ctypes.data, len(data), off.ctypes.data, int(intervals),
+                              int(weighted), xadj.ctypes.data, adj.ctypes.data, ew.ctypes.data,
+                              m2_cap)
+    if r != 0:
+        raise ValueError("corrupt compressed graph")
+    return xadj, adj[: xadj[n]], ew[: xadj[n]]
 
 
 # ---------------------------------------------------------------- LP

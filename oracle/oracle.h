@@ -13,6 +13,9 @@
  *
  * Parity status per function:
  *   orc_varint_*, orc_encode, orc_decode  pinned (hand-computed bytes, round trip)
+ *   orc_encode_ex, orc_decode_ex          pinned (hand-computed bytes, equal to
+ *                                          orc_encode without intervals and
+ *                                          weights, size formula, round trip)
  *   orc_lp_*                              pinned (brute-force argmax, cap invariant,
  *                                                  approval vs subset enumeration)
  *   orc_two_hop                           pinned (hand cases, restated packing)
@@ -93,6 +96,17 @@ int64_t orc_encode(int64_t n, const int64_t *xadj, const int32_t *adj, uint8_t *
  * adj_out has m2 entries (m2 taken from the terminal header). */
 int orc_decode(int64_t n, const uint8_t *bytes, int64_t nbytes, const uint64_t *off,
                int64_t *xadj_out, int32_t *adj_out, int64_t adj_cap);
+
+/* Interval encoding and compressed edge weights (codec_iv.c). ew may be NULL
+ * (unit weights, none stored); intervals = 0 gives the plain format with the
+ * weights interleaved (byte for byte orc_encode without weights). bytes and
+ * off may be NULL to size the stream. Returns the stream length. */
+int64_t orc_encode_ex(int64_t n, const int64_t *xadj, const int32_t *adj, const int64_t *ew,
+                      int intervals, uint8_t *bytes, uint64_t *off);
+/* Returns 0 on success, -1 on a corrupt stream; ew_out may be NULL. */
+int orc_decode_ex(int64_t n, const uint8_t *bytes, int64_t nbytes, const uint64_t *off,
+                  int intervals, int weighted, int64_t *xadj_out, int32_t *adj_out,
+                  int64_t *ew_out, int64_t adj_cap);
 
 /* ---- label propagation (Algorithm 1, made synchronous and deterministic) ---- */
 /* Decision for one vertex against a state snapshot. Returns 1 if u moves. */
