@@ -19,8 +19,8 @@
  *    Work is stream-ordered: an entry point may return before its kernels
  *    finish, except where it says it synchronises.
  *  - Errors are status codes; nothing throws or aborts across the ABI.
- *    Errors that kernels detect (a corrupt compressed stream, an exhausted
- *    spin limit) are latched in the graph's error word and returned by
+ *    Errors that kernels detect (a corrupt compressed stream, a full rating
+ *    hash table) are latched in the graph's error word and returned by
  *    tp_graph_check or by the next entry point that synchronises.
  *  - Vertex ids are int32 (n < 2^31); edge offsets, node and edge weights are
  *    int64. Graphs are undirected: each edge stored in both directions,
@@ -48,7 +48,7 @@ typedef enum {
   TP_ERR_OOM = 2,     /* device allocation failed (nothing leaked) */
   TP_ERR_CUDA = 3,    /* a CUDA runtime call failed */
   TP_ERR_CORRUPT = 4, /* compressed stream failed validation in a kernel */
-  TP_ERR_TIMEOUT = 5, /* a bounded device-side wait ran out */
+  TP_ERR_TIMEOUT = 5, /* reserved: the kernels never wait on one another */
   TP_ERR_BUDGET = 6   /* request exceeds a memory budget */
 } tp_status;
 
