@@ -350,6 +350,40 @@ def test_performance_knobs_do_not_change_results():
             assert np.array_equal(_host(part), want), trial
 
 
+def _sym_weights(xadj, adj, rng, hi):
+    ew = np.zeros(len(adj), np.int64)
+    for u in range(len(xadj) - 1):
+        for e in range(xadj[u], xadj[u + 1]):
+            v = int(adj[e])
+            if v > u:
+                w = int(rng.integers(1, hi))
+                ew[e] = w
+                ew[xadj[v] + int(np.searchsorted(adj[xadj[v]:xadj[v + 1]], u))] = w
+    return ew
+
+
+def test_partition_parameter_extremes():
+    # eps = 0 (cluster cap 1: no level coarsens), k = 1024 on 2 500 vertices,
+    # k = n, and an input graph with node and edge weights
+    xadj, adj = synth.gnm(2500, 9000, 6)
+    og = oracle.Graph(xadj, adj)
+    g = tp.graph_from_csr(xadj, adj)
+    for k, eps in ((5, 0.0), (1024, 0.03), (2500, 0.03)):
+        want, wst = oracle.partition(og, k, eps, oracle.Params(seed=8))
+        part, st = tp.partition(g, k, eps, tp.default_params(seed=8))
+        assert np.array_equal(_host(part), want), (k, eps)
+        assert st["cut"] == wst["cut"] and st["level_n"] == wst["level_n"], (k, eps)
+    rng = np.random.default_rng(4)
+    xadj, adj = synth.rgg2d(3000, 12.0, 9)
+    vw = rng.integers(1, 6, len(xadj) - 1).astype(np.int64)
+    ew = _sym_weights(xadj, adj, rng, 10)
+    want, wst = oracle.partition(oracle.Graph(xadj, adj, vw=vw, ew=ew), 7, 0.03,
+                                 oracle.Params(seed=8))
+    part, st = tp.partition(tp.graph_from_csr(xadj, adj, vw, ew), 7, 0.03,
+                            tp.default_params(seed=8))
+    assert np.array_equal(_host(part), want) and st["cut"] == wst["cut"]
+
+
 def test_edge_cases():
     # empty graph, isolated vertices only, k = 1, k > n
     empty = tp.graph_from_csr(np.zeros(1, np.int64), np.zeros(0, np.int32))
