@@ -229,3 +229,21 @@ def test_rejects_corrupt_streams():
     d[4] = 0x0b  # vertex 0, second weight 5 - 5
     with pytest.raises(ValueError):
         oracle.decode_ex(n, d, o, len(adj), intervals=False, weighted=True)
+
+
+def test_coarse_levels_round_trip_with_weights():
+    # coarse levels carry node and edge weights; their adjacency and edge
+    # weights round-trip through the weighted format (coarse-level
+    # compression, the row after interval encoding)
+    xadj, adj = synth.rgg2d(20000, 16.0, 7)
+    g = oracle.Graph(xadj, adj)
+    for level in range(3):
+        C = oracle.cluster(g, 40 * (level + 1), oracle.Params(seed=2), level)
+        g, _ = oracle.contract(g, C)
+        for intervals in (False, True):
+            data, off = oracle.encode_ex(g.xadj, g.adj, g.ew, intervals=intervals)
+            x2, a2, w2 = oracle.decode_ex(g.n, data, off, len(g.adj), intervals=intervals,
+                                          weighted=True)
+            assert np.array_equal(x2, g.xadj) and np.array_equal(a2, g.adj)
+            assert np.array_equal(w2, g.ew)
+            assert len(data) == _size_by_formula(g.xadj, g.adj, g.ew, intervals)
