@@ -50,6 +50,13 @@ def _load():
             "orc_encode": (i64, [i64, vp, vp, vp, vp]),
             "orc_decode": (ctypes.c_int, [i64, vp, i64, vp, vp, vp, i64]),
             "orc_encode_ex": (i64, [i64, vp, vp, vp, ctypes.c_int, vp, vp]),
+            "orc_gt_build": (vp, [vp, vp, ctypes.c_int32]),
+            "orc_gt_get": (i64, [vp, i64, ctypes.c_int32]),
+            "orc_gt_move": (None, [vp, vp, i64, ctypes.c_int32, ctypes.c_int32]),
+            "orc_gt_bytes": (i64, [vp]),
+            "orc_gt_layout": (None, [vp, i64, vp, vp, vp, vp]),
+            "orc_gt_check": (ctypes.c_int, [vp]),
+            "orc_gt_free": (None, [vp]),
             "orc_decode_ex": (ctypes.c_int, [i64, vp, i64, vp, ctypes.c_int, ctypes.c_int, vp, vp,
                                              vp, i64]),
             "orc_rate_vertex": (ctypes.c_int, [vp, i64, vp, vp, i64, vp, ctypes.c_int, u64, vp, vp]),
@@ -220,6 +227,41 @@ def decode_ex(n, data, off, m2_cap, intervals=True, weighted=False):
     if r != 0:
         raise ValueError("corrupt compressed graph")
     return xadj, adj[: xadj[n]], ew[: xadj[n]]
+
+
+class GainTable:
+    """Space-efficient gain table of a partition (affinity of every vertex to
+    every block; dense k values above degree k, sparse hash tables below)."""
+
+    def __init__(self, g: "Graph", part, k):
+        self._g = g
+        self._part = np.ascontiguousarray(part, np.int32)
+        self.k = k
+        self._h = _load().orc_gt_build(g.c, self._part.ctypes.data, k)
+
+    def get(self, v, b):
+        return _load().orc_gt_get(self._h, v, b)
+
+    def move(self, u, frm, to):
+        _load().orc_gt_move(self._h, self._g.c, u, frm, to)
+
+    def bytes(self):
+        return _load().orc_gt_bytes(self._h)
+
+    def layout(self, v):
+        cap, st = ctypes.c_int64(), ctypes.c_int64()
+        w, d = ctypes.c_int32(), ctypes.c_int32()
+        _load().orc_gt_layout(self._h, v, ctypes.byref(cap), ctypes.byref(w), ctypes.byref(d),
+                              ctypes.byref(st))
+        return {"cap": cap.value, "width": w.value, "dense": bool(d.value), "stored": st.value}
+
+    def check(self):
+        return _load().orc_gt_check(self._h)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _load().orc_gt_free(self._h)
+            self._h = None
 
 
 # ---------------------------------------------------------------- LP

@@ -28,6 +28,10 @@
  *   orc_refine                            pinned: rounds restated by
  *                                          enumeration (blocks as labels)
  *   orc_rebalance                         pinned: brute-force restatement
+ *   orc_gt_*                              pinned (affinities recounted by brute
+ *                                          force after random moves, probe-path
+ *                                          invariant, footprint and widths by
+ *                                          formula)
  *   orc_partition                         pinned: driver restated (caps,
  *                                          stop rules, projection, rebalance
  *                                          then refine) over the pinned stages,
@@ -107,6 +111,21 @@ int64_t orc_encode_ex(int64_t n, const int64_t *xadj, const int32_t *adj, const 
 int orc_decode_ex(int64_t n, const uint8_t *bytes, int64_t nbytes, const uint64_t *off,
                   int intervals, int weighted, int64_t *xadj_out, int32_t *adj_out,
                   int64_t *ew_out, int64_t adj_cap);
+
+/* ---- space-efficient gain table (Section "Space-Efficient Gain Tables"; gain_table.c) ---- */
+typedef struct orc_gain_table orc_gain_table;
+orc_gain_table *orc_gt_build(const orc_graph *g, const int32_t *part, int32_t k);
+int64_t orc_gt_get(const orc_gain_table *t, int64_t v, int32_t b); /* affinity w(v, V_b) */
+/* Updates the neighbours of u for a move of u from block `from` to `to`. */
+void orc_gt_move(orc_gain_table *t, const orc_graph *g, int64_t u, int32_t from, int32_t to);
+int64_t orc_gt_bytes(const orc_gain_table *t); /* size of the value array */
+/* v's slots (k when dense), bytes per value, dense flag and stored entries. */
+void orc_gt_layout(const orc_gain_table *t, int64_t v, int64_t *cap, int32_t *width,
+                   int32_t *dense, int64_t *stored);
+/* 0 if every sparse table holds only non-zero values, no duplicate and every
+ * key on its probe path; else a code naming the broken rule. */
+int orc_gt_check(const orc_gain_table *t);
+void orc_gt_free(orc_gain_table *t);
 
 /* ---- label propagation (Algorithm 1, made synchronous and deterministic) ---- */
 /* Decision for one vertex against a state snapshot. Returns 1 if u moves. */
