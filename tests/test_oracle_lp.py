@@ -311,3 +311,36 @@ def test_level_restatements_exercise_moves():
         lab, _ = _refine_restated(*case)
         moved_r += int(np.any(lab != case[7]))
     assert moved_c >= 8 and moved_r >= 5, (moved_c, moved_r)
+
+
+def _tie_vec(hv, xs):
+    # the tie hash of many labels at once (uint64 arithmetic wraps)
+    z = np.uint64(hv) ^ (xs + np.uint64(bf.GAMMA))
+    z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    z = z ^ (z >> np.uint64(31))
+    return z >> np.uint64(32)
+
+
+def test_label_breaks_ties_of_rating_and_tie_hash():
+    # the third level of the rating order only decides when two labels have
+    # the same rating and the same 32-bit tie hash: find such a pair and put
+    # both next to u with equal weight
+    hv = 0x1234_5678_9ABC_DEF0
+    xs = np.arange(1 << 18, dtype=np.uint64)
+    t = _tie_vec(hv, xs)
+    order = np.argsort(t, kind="stable")
+    dup = np.nonzero(t[order][1:] == t[order][:-1])[0]
+    assert len(dup) > 0
+    x1, x2 = sorted((int(order[dup[0]]), int(order[dup[0] + 1])))
+    assert bf.tie(hv, x1) == bf.tie(hv, x2)
+    xadj = np.array([0, 2, 3, 4], np.int64)
+    adj = np.array([1, 2, 0, 0], np.int32)
+    for first, second in ((x2, x1), (x1, x2)):  # either neighbour order
+        label = np.array([0, first, second], np.int32)
+        lw = np.zeros(x2 + 1, np.int64)
+        lw[0] = lw[x1] = lw[x2] = 1
+        g = oracle.Graph(xadj, adj)
+        for rate in (oracle.rate_vertex, oracle.rate_vertex_sorted):
+            moved, target, gain = rate(g, 0, label, lw, 10, hv=hv)
+            assert moved and target == x1 and gain == 1, rate
