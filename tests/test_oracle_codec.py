@@ -128,3 +128,28 @@ def test_decode_rejects_corruption():
     off2[u + 1:] += len(oracle.varint(2 * 10**6)) - 1
     with pytest.raises(ValueError):
         oracle.decode(n, bad2, off2, len(adj))
+
+
+def test_decode_rejects_bad_first_header_and_unordered_chunks():
+    xadj, adj = synth.gnm(200, 1000, 2)
+    data, off = oracle.encode(xadj, adj)
+    bad = data.copy()
+    bad[0] = 0x01  # the first neighbourhood must start at edge id 0
+    with pytest.raises(ValueError):
+        oracle.decode(len(xadj) - 1, bad, off, len(adj))
+    # every header one higher (edge ids counted from 1): the records still
+    # agree with each other, only the first header shows the shift
+    shifted, soff = oracle.encode(xadj + 1, np.concatenate([[0], adj]).astype(np.int32))
+    with pytest.raises(ValueError):
+        oracle.decode(len(xadj) - 1, shifted, soff, len(adj) + 1)
+    # star with 10 001 leaves: chunk 1 starts at byte 1041 with VarInt(2 * 1001)
+    # (two bytes); VarInt(2 * 500) also takes two bytes and sends chunk 1 back
+    # below the end of chunk 0
+    leaves = 10001
+    xadj, adj = _csr(leaves + 1, [(0, v) for v in range(1, leaves + 1)])
+    data, off = oracle.encode(xadj, adj)
+    assert bytes(data[1041:1043]) == oracle.varint(2 * 1001)
+    bad = data.copy()
+    bad[1041:1043] = np.frombuffer(oracle.varint(2 * 500), np.uint8)
+    with pytest.raises(ValueError):
+        oracle.decode(leaves + 1, bad, off, len(adj))

@@ -367,3 +367,13 @@ def test_multilevel_driver_by_restatement(case):
     got, st = oracle.partition(oracle.Graph(xadj, adj), k, eps, p)
     assert list(got) == list(want), name
     assert st["level_n"] == level_n and st["l_max"] == l_max, name
+
+
+def test_stats_imbalance_and_block_weight():
+    # W = 1000, k = 7: the perfectly balanced block weighs ceil(1000 / 7) = 143
+    xadj, adj = synth.gnm(1000, 4000, 3)
+    part, st = oracle.partition(oracle.Graph(xadj, adj), 7, 0.03, oracle.Params())
+    B = np.bincount(part, minlength=7)
+    assert st["max_block_weight"] == B.max()
+    assert st["imbalance"] == B.max() / 143 - 1
+    assert st["l_max"] == 147  # floor(1.03 * 143)
