@@ -50,6 +50,7 @@ def _load():
             "orc_encode": (i64, [i64, vp, vp, vp, vp]),
             "orc_decode": (ctypes.c_int, [i64, vp, i64, vp, vp, vp, i64]),
             "orc_encode_ex": (i64, [i64, vp, vp, vp, ctypes.c_int, vp, vp]),
+            "orc_fm_refine": (i64, [vp, vp, vp, ctypes.c_int32, i64, ctypes.c_int32]),
             "orc_gt_build": (vp, [vp, vp, ctypes.c_int32]),
             "orc_gt_get": (i64, [vp, i64, ctypes.c_int32]),
             "orc_gt_move": (None, [vp, vp, i64, ctypes.c_int32, ctypes.c_int32]),
@@ -227,6 +228,12 @@ def decode_ex(n, data, off, m2_cap, intervals=True, weighted=False):
     if r != 0:
         raise ValueError("corrupt compressed graph")
     return xadj, adj[: xadj[n]], ew[: xadj[n]]
+
+
+def fm_refine(g: "Graph", part, B, k, l_max, passes=8):
+    """k-way FM over the gain table, in place on part (int32) and B (int64);
+    returns the cut reduction."""
+    return _load().orc_fm_refine(g.c, part.ctypes.data, B.ctypes.data, k, l_max, passes)
 
 
 class GainTable:

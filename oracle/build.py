@@ -4,7 +4,7 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "liboracle.so")
-SOURCES = ["hash.c", "codec.c", "codec_iv.c", "gain_table.c", "lp.c", "contract.c", "partition.c"]
+SOURCES = ["hash.c", "codec.c", "codec_iv.c", "gain_table.c", "fm.c", "lp.c", "contract.c", "partition.c"]
 
 
 def build(force: bool = False) -> str:

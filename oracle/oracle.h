@@ -32,6 +32,9 @@
  *                                          force after random moves, probe-path
  *                                          invariant, footprint and widths by
  *                                          formula)
+ *   orc_fm_refine                         pinned (restated by brute force on
+ *                                          tiny graphs, cut and balance
+ *                                          invariants, 1-opt at the end)
  *   orc_partition                         pinned: driver restated (caps,
  *                                          stop rules, projection, rebalance
  *                                          then refine) over the pinned stages,
@@ -126,6 +129,11 @@ void orc_gt_layout(const orc_gain_table *t, int64_t v, int64_t *cap, int32_t *wi
  * key on its probe path; else a code naming the broken rule. */
 int orc_gt_check(const orc_gain_table *t);
 void orc_gt_free(orc_gain_table *t);
+
+/* k-way FM over the gain table (fm.c): at most `passes` passes, in place on
+ * part and B; returns the total cut reduction. */
+int64_t orc_fm_refine(const orc_graph *g, int32_t *part, int64_t *B, int32_t k, int64_t l_max,
+                      int32_t passes);
 
 /* ---- label propagation (Algorithm 1, made synchronous and deterministic) ---- */
 /* Decision for one vertex against a state snapshot. Returns 1 if u moves. */
