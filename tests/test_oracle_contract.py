@@ -65,3 +65,42 @@ def test_contract_after_clustering_large():
     C = oracle.cluster(g, 40, oracle.Params(), 0)
     ones = np.ones(len(adj), np.int64)
     _check(xadj, adj, ones, np.ones(len(xadj) - 1, np.int64), C)
+
+
+def test_validate_names_each_broken_rule():
+    # the validator the contraction pins rely on: every rule of the graph
+    # representation, broken one at a time on a valid 4-cycle with weights
+    xadj = np.array([0, 2, 4, 6, 8], np.int64)
+    adj = np.array([1, 3, 0, 2, 1, 3, 0, 2], np.int32)
+    ew = np.array([5, 7, 5, 6, 6, 4, 7, 4], np.int64)
+    vw = np.array([1, 2, 3, 4], np.int64)
+    assert oracle.validate(oracle.Graph(xadj, adj, vw, ew)) == 0
+
+    def code(xadj=xadj, adj=adj, ew=ew, vw=vw):
+        return oracle.validate(oracle.Graph(xadj, adj, vw, ew))
+
+    assert code(xadj=np.array([1, 2, 4, 6, 8], np.int64)) == 1  # does not start at 0
+    # codes name the first broken rule in vertex order: break each at vertex 0
+    assert code(xadj=np.array([0, -1, 4, 6, 8], np.int64)) == 2  # offsets decrease
+    assert code(vw=np.array([1, 0, 3, 4], np.int64)) == 3  # node weight not positive
+    bad = adj.copy()
+    bad[0] = 9
+    assert code(adj=bad) == 4  # neighbour id out of range
+    bad = adj.copy()
+    bad[0] = 0
+    assert code(adj=bad) == 5  # self-loop
+    bad, badw = adj.copy(), ew.copy()
+    bad[0], bad[1] = bad[1], bad[0]
+    badw[0], badw[1] = badw[1], badw[0]
+    assert code(adj=bad, ew=badw) == 6  # unsorted neighbourhood
+    bad = ew.copy()
+    bad[1] = 0
+    assert code(ew=bad) == 7  # edge weight not positive
+    bad = ew.copy()
+    bad[1] = 8
+    assert code(ew=bad) == 8  # w(0,3) != w(3,0)
+    # an edge stored in one direction only: 0-2 added at vertex 0 alone
+    x2 = np.array([0, 3, 5, 7, 9], np.int64)
+    a2 = np.array([1, 2, 3, 0, 2, 1, 3, 0, 2], np.int32)
+    w2 = np.array([5, 1, 7, 5, 6, 6, 4, 7, 4], np.int64)
+    assert code(xadj=x2, adj=a2, ew=w2) == 8
