@@ -1,5 +1,6 @@
-"""Input generators of the batched workload (CPU): the random hyperbolic
-generator against a direct all-pairs test, its shape, and the batch recipe."""
+"""Input generators (CPU): the random hyperbolic generator against a direct
+all-pairs test, the shapes of every generator (valid undirected CSR, sizes,
+degrees, locality, skew, determinism) and the batch and serving recipes."""
 import numpy as np
 import pytest
 
@@ -70,3 +71,28 @@ def test_serving_recipe():
     ns = [x["n"] for x in r if not x["resident"]]
     assert min(ns) >= 2 ** w["log2_lo"] and max(ns) <= 2 ** w["log2_hi"]
     assert {x["gen"] for x in r if not x["resident"]} == set(synth.BATCH_GENERATORS)
+
+
+def test_gnm_rgg_rmat_shapes():
+    # G(n,m): exactly m distinct edges, ids without locality
+    xadj, adj = synth.gnm(5000, 20000, 3)
+    _csr_ok(xadj, adj)
+    assert len(adj) == 2 * 20000
+    # RGG-2D: expected degree d (a little less: points near the border lose
+    # part of their disk), neighbour ids close to the vertex (cell order)
+    n, d = 1 << 15, 16.0
+    xadj, adj = synth.rgg2d(n, d, 4)
+    _csr_ok(xadj, adj)
+    assert 0.95 * d < len(adj) / n <= d
+    src = np.repeat(np.arange(n), np.diff(xadj))
+    assert np.median(np.abs(adj - src)) < n / 50
+    # R-MAT scale 12, 16 samples per vertex: deduplicated and symmetrised
+    # (so at most 2 * 16 * 2^12 entries), skewed towards low ids
+    xadj, adj = synth.rmat(12, 16, seed=5)
+    _csr_ok(xadj, adj)
+    deg = np.diff(xadj)
+    assert len(adj) <= 2 * 16 * 4096 and deg.max() > 20 * deg.mean()
+    assert deg[: 4096 // 16].sum() > deg[-4096 // 16:].sum()
+    # same seed, same graph; another seed, another graph
+    assert np.array_equal(synth.gnm(5000, 20000, 3)[1], synth.gnm(5000, 20000, 3)[1])
+    assert not np.array_equal(synth.gnm(5000, 20000, 3)[1], synth.gnm(5000, 20000, 4)[1])
