@@ -24,7 +24,7 @@ class _CGraph(ctypes.Structure):
 class _CParams(ctypes.Structure):
     _fields_ = [("seed", u64), ("cluster_rounds", i32), ("refine_rounds", i32),
                 ("sub_rounds", i32), ("c_lim", i32), ("ip_attempts", i32), ("two_hop", i32),
-                ("max_levels", i32)]
+                ("max_levels", i32), ("fm_passes", i32)]
 
 
 class _CStats(ctypes.Structure):
@@ -120,16 +120,16 @@ class Graph:
 
 class Params:
     def __init__(self, seed=1, cluster_rounds=5, refine_rounds=5, sub_rounds=8, c_lim=160,
-                 ip_attempts=8, two_hop=1, max_levels=64):
+                 ip_attempts=8, two_hop=1, max_levels=64, fm_passes=0):
         self.seed, self.cluster_rounds, self.refine_rounds = seed, cluster_rounds, refine_rounds
         self.sub_rounds, self.c_lim, self.ip_attempts = sub_rounds, c_lim, ip_attempts
-        self.two_hop, self.max_levels = two_hop, max_levels
+        self.two_hop, self.max_levels, self.fm_passes = two_hop, max_levels, fm_passes
 
     @property
     def c(self):
         return ctypes.byref(_CParams(self.seed, self.cluster_rounds, self.refine_rounds,
                                      self.sub_rounds, self.c_lim, self.ip_attempts,
-                                     self.two_hop, self.max_levels))
+                                     self.two_hop, self.max_levels, self.fm_passes))
 
 
 def eps_to_ppm(eps: float) -> int:

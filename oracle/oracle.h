@@ -73,6 +73,8 @@ typedef struct {
   int32_t ip_attempts;    /* bisection attempts per tree node, T (8) */
   int32_t two_hop;        /* 1: pack leftover singletons after clustering */
   int32_t max_levels;     /* at most this many graphs in the hierarchy (64) */
+  int32_t fm_passes;      /* k-way FM passes after LP refinement per level (0: none;
+                             the GPU path has no FM, so parity runs use 0) */
 } orc_params;
 
 typedef struct {

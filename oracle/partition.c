@@ -22,7 +22,8 @@
  *    seeded attempts of BFS growing plus 2-way label propagation and keeps the
  *    smallest cut (see bisect_node).
  *  - Every level: project, rebalance if a block exceeds L_max, then refine
- *    with label propagation (cap L_max).
+ *    with label propagation (cap L_max), then (fm_passes > 0, off by default)
+ *    with k-way FM over the gain table.
  */
 #include "oracle.h"
 #include <stdlib.h>
@@ -340,6 +341,7 @@ int orc_partition(const orc_graph *g0, int32_t k, int64_t eps_ppm, const orc_par
       for (int32_t b = 0; b < k; ++b) over |= B[b] > l_max;
       if (over) orc_rebalance(&levels[l], cur, B, k, l_max);
       orc_refine(&levels[l], cur, B, k, l_max, p, l);
+      if (p->fm_passes > 0) orc_fm_refine(&levels[l], cur, B, k, l_max, p->fm_passes);
     }
   }
   memcpy(part, cur, sizeof(int32_t) * (size_t)g0->n);

@@ -317,7 +317,8 @@ def _multilevel_restated(xadj, adj, k, eps, p):
     arithmetic; coarsen while n > c_lim k and fewer than max_levels graphs
     exist, discarding a level that keeps more than 95% of the vertices;
     initial partition of the coarsest graph; then from coarsest to finest:
-    project, rebalance if some block exceeds L_max, refine."""
+    project, rebalance if some block exceeds L_max, refine (then FM, when
+    asked for)."""
     g = oracle.Graph(xadj, adj)
     W = g.n
     ppm = int(math.floor(eps * 1e6 + 0.5))
@@ -346,6 +347,8 @@ def _multilevel_restated(xadj, adj, k, eps, p):
             if B.max() > l_max:
                 oracle.rebalance(levels[lv], cur, B, k, l_max)
             oracle.refine(levels[lv], cur, B, k, l_max, p, lv)
+            if p.fm_passes > 0:
+                oracle.fm_refine(levels[lv], cur, B, k, l_max, p.fm_passes)
     return cur, level_n, l_max
 
 
@@ -357,10 +360,12 @@ def _ml_cases():
         ("rgg-2lv", synth.rgg2d(2000, 10.0, 8), 3, 0.1, oracle.Params(seed=6, c_lim=5,
                                                                       max_levels=2)),
         ("gnm-k1", synth.gnm(500, 2000, 9), 1, 0.03, oracle.Params(seed=7)),
+        ("rgg-fm", synth.rgg2d(2500, 12.0, 6), 8, 0.03, oracle.Params(seed=8, c_lim=20,
+                                                                     fm_passes=4)),
     ]
 
 
-@pytest.mark.parametrize("case", range(5))
+@pytest.mark.parametrize("case", range(6))
 def test_multilevel_driver_by_restatement(case):
     name, (xadj, adj), k, eps, p = _ml_cases()[case]
     want, level_n, l_max = _multilevel_restated(xadj, adj, k, eps, p)
