@@ -326,7 +326,10 @@ tp_status tp_server_wait(tp_server *sv, uint64_t ticket, tp_stats *stats, tp_req
 /* Largest sum of footprints the server has had running at once. */
 int64_t tp_server_peak_in_use(tp_server *sv);
 
-/* Runs every queued request to completion, then stops the workers. */
+/* Runs every queued request to completion, then stops the workers and frees
+ * the server. Results not yet waited for are dropped. No other thread may be
+ * inside tp_server_submit or tp_server_wait on this server when it is
+ * called. */
 void tp_server_destroy(tp_server *sv);
 
 /* ---- tracing ---- */
