@@ -247,3 +247,24 @@ def test_coarse_levels_round_trip_with_weights():
             assert np.array_equal(x2, g.xadj) and np.array_equal(a2, g.adj)
             assert np.array_equal(w2, g.ew)
             assert len(data) == _size_by_formula(g.xadj, g.adj, g.ew, intervals)
+
+
+def test_rejects_chunks_that_run_backwards():
+    # star with 10 001 leaves, intervals on: every chunk is one interval.
+    # Chunk 0 takes 4 bytes after the 1-byte header and the 40-byte table
+    # (count 01, start 2*1 = 02, length 997 - 3 in two bytes), so chunk 1
+    # starts at byte 45 with count 01 and start VarInt(2 * 1001) in two
+    # bytes; VarInt(2 * 500) also takes two bytes and sends chunk 1 back over
+    # ids chunk 0 already holds
+    leaves = 10001
+    nb = [dict() for _ in range(leaves + 1)]
+    for v in range(1, leaves + 1):
+        nb[0][v] = nb[v][0] = 1
+    xadj, adj, _ = _csr_from(nb)
+    data, off = oracle.encode_ex(xadj, adj, None, intervals=True)
+    assert data[45] == 1 and bytes(data[46:48]) == oracle.varint(2 * 1001)
+    oracle.decode_ex(leaves + 1, data, off, len(adj), intervals=True)
+    bad = data.copy()
+    bad[46:48] = np.frombuffer(oracle.varint(2 * 500), np.uint8)
+    with pytest.raises(ValueError):
+        oracle.decode_ex(leaves + 1, bad, off, len(adj), intervals=True)
