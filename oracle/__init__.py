@@ -94,7 +94,8 @@ class Graph:
     """CSR graph held in numpy arrays (int64 xadj, int32 adj, int64 weights)."""
 
     def __init__(self, xadj, adj, vw=None, ew=None, implicit_unit=False):
-        """implicit_unit: no weight arrays at all (only rate_vertex_sorted accepts that)."""
+        """implicit_unit: no weight arrays at all (unit weights, read as 1 by every
+        function; large graphs need not carry arrays of ones)."""
         self.xadj = np.ascontiguousarray(xadj, dtype=np.int64)
         self.adj = np.ascontiguousarray(adj, dtype=np.int32)
         n = len(self.xadj) - 1

@@ -68,12 +68,12 @@ int64_t orc_contract(const orc_graph *g, const int32_t *C, orc_graph *out, int32
     int64_t nt = 0;
     for (int64_t q = mstart[a]; q < mstart[a + 1]; ++q) {
       int64_t u = members[q];
-      out->vw[a] += g->vw[u];
+      out->vw[a] += orc_vw(g, u);
       for (int64_t e = g->xadj[u]; e < g->xadj[u + 1]; ++e) {
         int32_t b = map[g->adj[e]];
         if (b == a) continue;
         if (R[b] == 0) touched[nt++] = b;
-        R[b] += g->ew[e];
+        R[b] += orc_ew(g, e);
       }
     }
     qsort(touched, (size_t)nt, sizeof(int32_t), cmp_i32);

@@ -33,8 +33,8 @@ typedef struct {
 static void apply(orc_gain_table *t, const orc_graph *g, int32_t *part, int64_t *B, int64_t v,
                   int32_t from, int32_t to) {
   orc_gt_move(t, g, v, from, to);
-  B[from] -= g->vw[v];
-  B[to] += g->vw[v];
+  B[from] -= orc_vw(g, v);
+  B[to] += orc_vw(g, v);
   part[v] = to;
 }
 
@@ -56,7 +56,7 @@ int64_t orc_fm_refine(const orc_graph *g, int32_t *part, int64_t *B, int32_t k, 
         int64_t a_own = orc_gt_get(t, v, own);
         for (int64_t e = g->xadj[v]; e < g->xadj[v + 1]; ++e) {
           int32_t x = part[g->adj[e]];
-          if (x == own || B[x] + g->vw[v] > l_max) continue;
+          if (x == own || B[x] + orc_vw(g, v) > l_max) continue;
           int64_t gain = orc_gt_get(t, v, x) - a_own;
           /* v ascends in the scan: a later v wins only with a larger gain */
           if (bv < 0 || gain > bgain || (v == bv && gain == bgain && x < bt)) {

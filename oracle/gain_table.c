@@ -152,7 +152,7 @@ orc_gain_table *orc_gt_build(const orc_graph *g, const int32_t *part, int32_t k)
   int64_t pos = 0;
   for (int64_t v = 0; v < n; ++v) {
     int64_t d = degree(g, v), total = 0;
-    for (int64_t e = g->xadj[v]; e < g->xadj[v + 1]; ++e) total += g->ew[e];
+    for (int64_t e = g->xadj[v]; e < g->xadj[v + 1]; ++e) total += orc_ew(g, e);
     int w = 1;
     while (w < 8 && (uint64_t)total >> (8 * w) != 0) w *= 2;
     t->width[v] = (uint8_t)w;
@@ -176,7 +176,7 @@ orc_gain_table *orc_gt_build(const orc_graph *g, const int32_t *part, int32_t k)
     for (int64_t i = 0; i < t->cap[v]; ++i) store_key(slot_at(t, v, i), -1);
   }
   for (int64_t v = 0; v < n; ++v)
-    for (int64_t e = g->xadj[v]; e < g->xadj[v + 1]; ++e) add_affinity(t, v, part[g->adj[e]], g->ew[e]);
+    for (int64_t e = g->xadj[v]; e < g->xadj[v + 1]; ++e) add_affinity(t, v, part[g->adj[e]], orc_ew(g, e));
   return t;
 }
 
@@ -192,8 +192,8 @@ void orc_gt_move(orc_gain_table *t, const orc_graph *g, int64_t u, int32_t from,
   if (from == to) return;
   for (int64_t e = g->xadj[u]; e < g->xadj[u + 1]; ++e) {
     int64_t v = g->adj[e];
-    add_affinity(t, v, to, g->ew[e]); /* add first: a sparse table never overflows */
-    add_affinity(t, v, from, -g->ew[e]);
+    add_affinity(t, v, to, orc_ew(g, e)); /* add first: a sparse table never overflows */
+    add_affinity(t, v, from, -orc_ew(g, e));
   }
 }
 

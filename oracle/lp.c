@@ -61,7 +61,7 @@ static int rate_with(const orc_graph *g, int64_t u, const int32_t *label, const 
   for (int64_t e = g->xadj[u]; e < g->xadj[u + 1]; ++e) {
     int32_t x = label[g->adj[e]];
     if (rm->R[x] == 0) rm->touched[nt++] = x;
-    rm->R[x] += g->ew[e];
+    rm->R[x] += orc_ew(g, e);
   }
   int64_t r_own = rm->R[own];
   int64_t best = -1, best_r = 0;
@@ -69,7 +69,7 @@ static int rate_with(const orc_graph *g, int64_t u, const int32_t *label, const 
   for (int64_t i = 0; i < nt; ++i) {
     int32_t x = rm->touched[i];
     if (x == own) continue;
-    if (!ignore_cap && lw[x] + g->vw[u] > cap_of(cap_uniform, cap, x)) continue;
+    if (!ignore_cap && lw[x] + orc_vw(g, u) > cap_of(cap_uniform, cap, x)) continue;
     uint32_t t = tie_hash(hv, x);
     if (best < 0 || better(rm->R[x], t, x, best_r, best_t, best)) {
       best = x;
@@ -127,7 +127,7 @@ int orc_rate_vertex_sorted(const orc_graph *g, int64_t u, const int32_t *label, 
   label_weight *p = (label_weight *)malloc(sizeof(label_weight) * (size_t)(d + 1));
   for (int64_t i = 0; i < d; ++i) {
     p[i].x = label[g->adj[g->xadj[u] + i]];
-    p[i].w = g->ew ? g->ew[g->xadj[u] + i] : 1;
+    p[i].w = orc_ew(g, g->xadj[u] + i);
   }
   qsort(p, (size_t)d, sizeof(label_weight), cmp_label_weight);
   int32_t own = label[u];
@@ -142,7 +142,7 @@ int orc_rate_vertex_sorted(const orc_graph *g, int64_t u, const int32_t *label, 
       r_own = r;
       continue;
     }
-    if (!ignore_cap && lw[x] + (g->vw ? g->vw[u] : 1) > cap_of(cap_uniform, cap, x)) continue;
+    if (!ignore_cap && lw[x] + orc_vw(g, u) > cap_of(cap_uniform, cap, x)) continue;
     uint32_t t = tie_hash(hv, x);
     if (best < 0 || better(r, t, x, best_r, best_t, best)) {
       best = x;
@@ -188,7 +188,7 @@ static int64_t subround_with(const orc_graph *g, int32_t *label, int64_t *lw, in
       mv[nm].u = u;
       mv[nm].t = t;
       mv[nm].gain = gain;
-      mv[nm].w = g->vw[u];
+      mv[nm].w = orc_vw(g, u);
       mv[nm].approved = 0;
       ++nm;
     }
@@ -293,7 +293,7 @@ void orc_two_hop(const orc_graph *g, int32_t *C, const int64_t *Wc, int64_t U, u
   rm.R = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
   rm.touched = (int32_t *)malloc(sizeof(int32_t) * (size_t)(g->m2 + 1));
   for (int64_t u = 0; u < n; ++u) {
-    if (C[u] != u || Wc[u] != g->vw[u]) continue;
+    if (C[u] != u || Wc[u] != orc_vw(g, u)) continue;
     uint64_t hu = orc_step(rk, (uint64_t)u);
     int32_t t;
     int64_t gain;
@@ -310,7 +310,7 @@ void orc_two_hop(const orc_graph *g, int32_t *C, const int64_t *Wc, int64_t U, u
     while (j < nf && f[j].key == f[i].key) ++j;
     int64_t P = 0, cur_bin = -1, head = -1;
     for (int64_t q = i; q < j; ++q) {
-      int64_t u = f[q].u, c = g->vw[u];
+      int64_t u = f[q].u, c = orc_vw(g, u);
       int64_t bin = P / U;
       int straddle = P + c > (bin + 1) * U;
       P += c;
@@ -333,7 +333,7 @@ void orc_cluster(const orc_graph *g, int64_t U, const orc_params *p, int64_t lev
   int64_t *Wc = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
   for (int64_t u = 0; u < n; ++u) {
     C[u] = (int32_t)u;
-    Wc[u] = g->vw[u];
+    Wc[u] = orc_vw(g, u);
   }
   orc_lp_rounds(g, C, Wc, n, U, NULL, p->seed, orc_tag(0), (uint64_t)level, 0, p->cluster_rounds,
                 p->sub_rounds);

@@ -53,7 +53,10 @@ extern "C" {
 /* Undirected graph in CSR form (Section "Graph Representation"): the
  * neighbours of u are adj[xadj[u] .. xadj[u+1]), sorted ascending, no
  * self-loops, no duplicates, every edge stored in both directions.
- * vw = node weights c(u) (> 0), ew = edge weights w(u,v) (> 0). */
+ * vw = node weights c(u) (> 0), ew = edge weights w(u,v) (> 0). A NULL vw or
+ * ew means unit weights (an input graph need not carry arrays of ones);
+ * every function reads weights through orc_vw / orc_ew, and coarse graphs
+ * built by contraction always carry both arrays. */
 typedef struct {
   int64_t n;
   int64_t m2; /* adjacency entries = 2m */
@@ -62,6 +65,9 @@ typedef struct {
   int64_t *vw;
   int64_t *ew;
 } orc_graph;
+
+static inline int64_t orc_vw(const orc_graph *g, int64_t u) { return g->vw ? g->vw[u] : 1; }
+static inline int64_t orc_ew(const orc_graph *g, int64_t e) { return g->ew ? g->ew[e] : 1; }
 
 /* Semantic parameters: they change results. */
 typedef struct {

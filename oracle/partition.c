@@ -58,15 +58,15 @@ int orc_validate(const orc_graph *g) {
   if (g->n < 0 || g->xadj[0] != 0 || g->xadj[g->n] != g->m2) return 1;
   for (int64_t u = 0; u < g->n; ++u) {
     if (g->xadj[u + 1] < g->xadj[u]) return 2;
-    if (g->vw[u] <= 0) return 3;
+    if (orc_vw(g, u) <= 0) return 3;
     for (int64_t e = g->xadj[u]; e < g->xadj[u + 1]; ++e) {
       int64_t v = g->adj[e];
       if (v < 0 || v >= g->n) return 4;
       if (v == u) return 5;
       if (e > g->xadj[u] && g->adj[e - 1] >= v) return 6;
-      if (g->ew[e] <= 0) return 7;
+      if (orc_ew(g, e) <= 0) return 7;
       int64_t r = find_in(g, v, u);
-      if (r < 0 || g->ew[r] != g->ew[e]) return 8;
+      if (r < 0 || orc_ew(g, r) != orc_ew(g, e)) return 8;
     }
   }
   return 0;
@@ -74,7 +74,7 @@ int orc_validate(const orc_graph *g) {
 
 void orc_block_weights(const orc_graph *g, const int32_t *part, int32_t k, int64_t *B) {
   for (int32_t b = 0; b < k; ++b) B[b] = 0;
-  for (int64_t u = 0; u < g->n; ++u) B[part[u]] += g->vw[u];
+  for (int64_t u = 0; u < g->n; ++u) B[part[u]] += orc_vw(g, u);
 }
 
 /* Edge cut: half the weight of adjacency entries whose ends lie in different
@@ -83,7 +83,7 @@ int64_t orc_cut(const orc_graph *g, const int32_t *part) {
   int64_t c = 0;
   for (int64_t u = 0; u < g->n; ++u)
     for (int64_t e = g->xadj[u]; e < g->xadj[u + 1]; ++e)
-      if (part[u] != part[g->adj[e]]) c += g->ew[e];
+      if (part[u] != part[g->adj[e]]) c += orc_ew(g, e);
   return c / 2;
 }
 
@@ -104,12 +104,12 @@ static void induced(const orc_graph *g, const int64_t *vs, int64_t ns, int64_t *
   int64_t p = 0;
   for (int64_t i = 0; i < ns; ++i) {
     sub->xadj[i] = p;
-    sub->vw[i] = g->vw[vs[i]];
+    sub->vw[i] = orc_vw(g, vs[i]);
     for (int64_t e = g->xadj[vs[i]]; e < g->xadj[vs[i] + 1]; ++e) {
       int64_t l = loc[g->adj[e]];
       if (l < 0) continue;
       sub->adj[p] = (int32_t)l;
-      sub->ew[p] = g->ew[e];
+      sub->ew[p] = orc_ew(g, e);
       ++p;
     }
   }
@@ -251,8 +251,8 @@ int orc_rebalance(const orc_graph *g, int32_t *part, int64_t *B, int32_t k, int6
     int32_t best_t = -1;
     for (int64_t u = 0; u < g->n; ++u) {
       if (part[u] != b) continue;
-      int64_t c = g->vw[u];
-      for (int64_t e = g->xadj[u]; e < g->xadj[u + 1]; ++e) R[part[g->adj[e]]] += g->ew[e];
+      int64_t c = orc_vw(g, u);
+      for (int64_t e = g->xadj[u]; e < g->xadj[u + 1]; ++e) R[part[g->adj[e]]] += orc_ew(g, e);
       int32_t t = -1;
       for (int32_t x = 0; x < k; ++x) {
         if (x == b || B[x] + c > l_max) continue;
@@ -272,8 +272,8 @@ int orc_rebalance(const orc_graph *g, int32_t *part, int64_t *B, int32_t k, int6
       ret = 1;
       break;
     }
-    B[b] -= g->vw[best_u];
-    B[best_t] += g->vw[best_u];
+    B[b] -= orc_vw(g, best_u);
+    B[best_t] += orc_vw(g, best_u);
     part[best_u] = best_t;
   }
   free(R);
@@ -291,7 +291,7 @@ int orc_partition(const orc_graph *g0, int32_t k, int64_t eps_ppm, const orc_par
   memset(st, 0, sizeof(*st));
   if (k < 1 || eps_ppm < 0) return 1;
   int64_t W = 0;
-  for (int64_t u = 0; u < g0->n; ++u) W += g0->vw[u];
+  for (int64_t u = 0; u < g0->n; ++u) W += orc_vw(g0, u);
   int64_t U = orc_cluster_cap(W, k, eps_ppm);
   int64_t l_max = orc_block_cap(W, k, eps_ppm);
   st->l_max = l_max;

@@ -382,3 +382,26 @@ def test_stats_imbalance_and_block_weight():
     assert st["max_block_weight"] == B.max()
     assert st["imbalance"] == B.max() / 143 - 1
     assert st["l_max"] == 147  # floor(1.03 * 143)
+
+
+@pytest.mark.parametrize("gen", ["rgg", "rmat"])
+def test_implicit_unit_weights_equal_explicit_arrays(gen):
+    """A graph without weight arrays means unit weights: clustering,
+    contraction, cut and the whole partition equal those of the same graph
+    with explicit arrays of ones (large inputs are run without the arrays)."""
+    xadj, adj = synth.rgg2d(3000, 12.0, 4) if gen == "rgg" else synth.rmat(11, 8, seed=4)
+    ge = oracle.Graph(xadj, adj)
+    gi = oracle.Graph(xadj, adj, implicit_unit=True)
+    assert gi.vw is None and gi.ew is None
+    p = oracle.Params(seed=3)
+    Ce, Ci = oracle.cluster(ge, 20, p, 0), oracle.cluster(gi, 20, p, 0)
+    assert np.array_equal(Ce, Ci)
+    (ce, me), (ci, mi) = oracle.contract(ge, Ce), oracle.contract(gi, Ci)
+    assert np.array_equal(me, mi) and np.array_equal(ce.adj, ci.adj) and np.array_equal(ce.ew, ci.ew)
+    assert np.array_equal(ce.vw, ci.vw)
+    for k in (2, 8, 13):
+        pe, se = oracle.partition(ge, k, 0.03, p)
+        pi, si = oracle.partition(gi, k, 0.03, p)
+        assert np.array_equal(pe, pi) and se == si
+        assert oracle.cut(gi, pi) == se["cut"]
+    assert oracle.validate(gi) == 0
