@@ -216,6 +216,18 @@ def shard(count, rank, ws):
     return list(range(rank, count, ws))
 
 
+def bench_config(w, n, m2, ws):
+    """The config object both arms print (the reference arm runs the same
+    workload on the host)."""
+    return {"workload": w["desc"], "n": n, "m2": m2, "k": w["k"], "eps": EPS,
+            "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"}
+
+
+E2E_UNIT = "GTEPS"
+E2E_DEF = ("level-0 LP clustering edges (5 rounds x 2m) per second of one whole user call "
+           "chain: host CSR in, graph creation, compression, partition, partition back to host")
+
+
 def cpu_oracle_lp(xadj, adj, k, seed, max_rounds=5, budget_s=12.0):
     """Oracle level-0 clustering rounds (one thread) until the budget is spent."""
     import oracle
@@ -272,10 +284,10 @@ def run_reference(args, w):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": {"workload": w["desc"]},
+            "data": "synthetic", "config": bench_config(w, n, len(adj), ws),
             "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                              "sample": sample, "host": host_cpu()},
-            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0,
+            "e2e": {"value": value, "unit": E2E_UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -537,6 +549,62 @@ def run_partition_only(args, w):
     print(json.dumps({"partition_only": w["desc"], **st}))
 
 
+def rmat_extra(args, hbm):
+    """Config 3 (R-MAT scale 26, k = 256, compressed with chunking) beside the
+    headline: level-0 LP GTEPS and partition time over a fixed small count of
+    partitions (one warm-up, two timed), and the per-tier rating roofline
+    from one more partition with per-launch events."""
+    import torch
+
+    import paper_2410_19119_gb300 as tp
+
+    w = WORKLOADS["rmat26"]
+    t0 = time.perf_counter()
+    xadj, adj = make_graph(w)
+    gen_s = time.perf_counter() - t0
+    n, m2 = len(xadj) - 1, len(adj)
+    g = tp.graph_from_csr(xadj, adj)
+    del xadj, adj
+    z = g.compress()
+    del g
+    params = tp.default_params(seed=w["seed"])
+    tp.partition(z, w["k"], EPS, params)
+    torch.cuda.synchronize()
+    runs = []
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, st = tp.partition(z, w["k"], EPS, params)
+        e1.record()
+        torch.cuda.synchronize()
+        runs.append((e0.elapsed_time(e1), st))
+    tp.profile_read()
+    tp.profile_enable(True)
+    tp.partition(z, w["k"], EPS, params)
+    tp.profile_enable(False)
+    prof = tp.profile_read()
+    st = runs[-1][1]
+    lp_ms = statistics.mean(r[1]["ms_lp_level0"] for r in runs)
+    tiers = {}
+    for fam, e in prof.items():
+        if fam.startswith("rate_") and e["launches"]:
+            ms = e["ms"] / e["launches"]
+            gbs = e["bytes"] / e["launches"] / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+            tiers[fam] = {"kernel": KERNEL_NAMES[fam], "launches": e["launches"],
+                          "ms_total": e["ms"], "ms_per_launch": ms, "achieved_gbs": gbs,
+                          "frac": gbs / hbm}
+    zi = z.info()
+    return {"workload": w["desc"], "n": n, "m2": m2, "compressed_bytes": zi["bytes"],
+            "lp_gteps_compressed": 5.0 * m2 / lp_ms / 1e6, "lp_ms_level0": lp_ms,
+            "partition_ms_compressed": statistics.mean(r[0] for r in runs),
+            "partitions_timed": len(runs), "cut": st["cut"], "imbalance": st["imbalance"],
+            "levels": st["levels"], "level_n": st["level_n"], "level_m2": st["level_m2"],
+            "peak_bytes": st["peak_bytes"],
+            "phase_ms": {"coarsen": st["ms_coarsen"], "initial": st["ms_initial"],
+                         "uncoarsen": st["ms_uncoarsen"]},
+            "rating_tiers_level0": tiers, "generate_s": gen_s}
+
+
 def run_native(args, w):
     import torch
 
@@ -558,16 +626,12 @@ def run_native(args, w):
     stream = torch.cuda.current_stream()
     g = tp.graph_from_csr(xadj, adj)
 
-    def step(profile):
+    def step():
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         ev[0].record(stream)
         z = g.compress()
         ev[1].record(stream)
-        if profile:
-            tp.profile_enable(True)
         _, stz = tp.partition(z, k, EPS, params)
-        if profile:
-            tp.profile_enable(False)
         ev[2].record(stream)
         _, stc = tp.partition(g, k, EPS, params)
         ev[3].record(stream)
@@ -575,11 +639,11 @@ def run_native(args, w):
         zinfo = z.info()
         return {"step_ms": ev[0].elapsed_time(ev[3]), "compress_ms": ev[0].elapsed_time(ev[1]),
                 "part_z_ms": ev[1].elapsed_time(ev[2]), "part_c_ms": ev[2].elapsed_time(ev[3]),
-                "stz": stz, "stc": stc, "zbytes": zinfo["bytes"], "zstream": zinfo["stream_bytes"]}
+                "stz": stz, "stc": stc, "zbytes": zinfo["bytes"], "zstream": zinfo["stream_bytes"],
+                "z": z}
 
     for _ in range(args.warmup):
-        step(False)
-        tp.profile_read()
+        step()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -587,18 +651,31 @@ def run_native(args, w):
     prof = {}
     recs = []
     with ClockSampler(dev_index) as clk:
+        # timed steps run exactly what a user call runs (no per-launch events)
         t_start = torch.cuda.Event(enable_timing=True)
         t_end = torch.cuda.Event(enable_timing=True)
         t_start.record(stream)
+        z = None
         for _ in range(args.steps):
-            recs.append(step(True))
+            r = step()
+            z = r.pop("z")  # keep only the last compressed graph
+            recs.append(r)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        launches = tp.launch_count() - launches0
+        # second timed loop: the same compressed partition with CUDA events
+        # around every rating launch of the level-0 clustering rounds (on the
+        # launching stream), for the per-kernel roofline
+        tp.profile_read()
+        for _ in range(args.steps):
+            tp.profile_enable(True)
+            tp.partition(z, k, EPS, params)
+            tp.profile_enable(False)
             for fam, e in tp.profile_read().items():
                 acc = prof.setdefault(fam, {"launches": 0, "ms": 0.0, "bytes": 0.0})
                 for key in acc:
                     acc[key] += e[key]
-        t_end.record(stream)
-        torch.cuda.synchronize()
-    launches = tp.launch_count() - launches0
+    del z
     total_ms = t_start.elapsed_time(t_end)
     rounds = params.cluster_rounds
     lp_edges = rounds * m2 * args.steps
@@ -664,8 +741,7 @@ def run_native(args, w):
         "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": w["desc"], "n": n, "m2": m2, "k": k, "eps": EPS,
-                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{ws}"},
+        "config": bench_config(w, n, m2, ws),
         "lp_gteps_csr": gteps_csr,
         "lp_ms_level0_compressed": lp_ms_z / args.steps, "lp_ms_level0_csr": lp_ms_c / args.steps,
         "partition_ms_compressed": statistics.mean(r["part_z_ms"] for r in recs),
@@ -680,13 +756,17 @@ def run_native(args, w):
                                 "initial": r0["stz"]["ms_initial"],
                                 "uncoarsen": r0["stz"]["ms_uncoarsen"]},
         "kernel_profile": prof,
+        "kernel_profile_timing": "a second loop of --steps compressed partitions with CUDA "
+                                 "events around each rating launch of the level-0 clustering",
         "roofline": roofline,
         "clocks": clk.summary(),
-        "e2e": {"value": e2e_value, "unit": "GTEPS (level-0 LP edges per end-to-end second)",
+        "e2e": {"value": e2e_value, "unit": E2E_UNIT, "definition": E2E_DEF,
                 "ms_per_step": e2e_step, "h2d_bytes_per_step": 8 * (n + 1) + 4 * m2,
                 "d2h_bytes_per_step": 4 * n},
         "gpu_launches": launches,
     }
+    if ws == 1 and w is WORKLOADS["rgg24"] and not args.no_rmat:
+        line["rmat26"] = rmat_extra(args, hbm)
     if ws == 1 and not args.no_cpu_baseline:
         v, rounds_done, dt = cpu_oracle_lp(xadj, adj, k, w["seed"])
         line["cpu_baseline"] = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle",
@@ -707,6 +787,8 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="rgg24")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rmat", action="store_true",
+                    help="skip the R-MAT scale 26 keys of the default line")
     ap.add_argument("--lp-only", action="store_true",
                     help="run only the level-0 clustering once (profiler captures)")
     ap.add_argument("--partition-only", action="store_true",

@@ -98,9 +98,14 @@ void tp_params_default(tp_params *p);
 const char *tp_status_string(tp_status s);
 
 /* Device memory hook. alloc(bytes, stream, ctx) must return stream-ordered
- * device memory or NULL; free(ptr, bytes, stream, ctx) releases it. Passing
- * NULL functions restores the default (cudaMallocAsync / cudaFreeAsync). The
- * hook is process-wide; set it before creating graphs. */
+ * device memory or NULL (the call then fails with TP_ERR_OOM); free(ptr,
+ * bytes, stream, ctx) releases it. Passing NULL functions restores the
+ * default (cudaMallocAsync / cudaFreeAsync). The hook is process-wide and
+ * applies to allocations made after the call; memory is always released
+ * through the hook that allocated it (graphs made earlier keep theirs), so
+ * the functions must stay callable while such memory lives. The Python
+ * binding installs PyTorch's caching allocator with use_torch_allocator().
+ * Set it while no other library call is running. */
 tp_status tp_set_allocator(void *(*alloc)(size_t, void *, void *),
                            void (*free_fn)(void *, size_t, void *, void *), void *ctx);
 
@@ -218,20 +223,25 @@ tp_status tp_metrics(const tp_graph *g, const int32_t *d_part, int32_t k, int64_
                      int64_t *h_block_weights, void *stream);
 
 /* tp_metrics without device allocation: the same cut and block weights,
- * with the scratch (cut accumulator and k block sums) in a fixed array
- * inside the library instead of memory from the allocator. For callers that
- * cannot allocate device memory when they need the metrics: code running
- * under CUDA stream capture (cudaMalloc cannot be captured), services with a
- * device-memory footprint fixed up front, callers without an allocator of
- * their own. The paper has no counterpart; this is an interface convenience.
- *  - k must be <= 16383 (scratch of 128 KiB, kept by every GPU that loads
- *    the library until the process exits); larger k returns TP_ERR_BUDGET.
- *  - The first call on a device looks up the array's device address; make
- *    that first call before any stream capture begins.
+ * with the scratch (cut accumulator, a bad-id flag and k block sums) in a
+ * fixed array inside the library instead of memory from the allocator. For
+ * callers that cannot allocate device memory when they need the metrics:
+ * services whose device-memory footprint is fixed up front (admission by
+ * memory budget, pools that must not grow) and callers without an allocator
+ * of their own. The paper has no counterpart; this is an interface
+ * convenience.
+ *  - k must be <= 16383 (scratch of 16 385 eight-byte words, about 128 KiB,
+ *    kept by every GPU that loads the library until the process exits);
+ *    larger k returns TP_ERR_BUDGET.
+ *  - Every d_part[u] must lie in [0, k); otherwise TP_ERR_INVALID (such
+ *    entries are skipped on the device, never written out of bounds).
+ *  - The first call on a device looks up the array's device address.
+ *  - The call synchronises the stream and writes host outputs, so it cannot
+ *    be captured into a CUDA graph: on a capturing stream it returns
+ *    TP_ERR_INVALID before enqueuing anything (the capture is not broken).
  *  - Every call uses the same array: calls whose work overlaps on the GPU
  *    (concurrent streams, other host threads) race and give wrong sums.
- *  - Synchronises stream; cut and h_block_weights (nullable, k entries) are
- *    host outputs. */
+ *  - cut and h_block_weights (nullable, k entries) are host outputs. */
 tp_status tp_metrics_static(const tp_graph *g, const int32_t *d_part, int32_t k, int64_t *cut,
                             int64_t *h_block_weights, void *stream);
 

@@ -18,7 +18,7 @@ __all__ = ["Graph", "Params", "Stats", "TpError", "default_params", "graph_from_
            "graph_from_compressed", "partition", "lp_cluster", "lp_subround", "contract",
            "initial_partition", "lp_refine", "rebalance", "metrics", "launch_count",
            "profile_enable", "profile_read", "PROFILE_FAMILIES", "partition_batch", "Server",
-           "footprint_bytes"]
+           "footprint_bytes", "use_torch_allocator", "use_default_allocator", "set_allocator"]
 
 PROFILE_FAMILIES = ("rate_small", "rate_mid", "rate_big", "rate_huge", "approve", "rate_lane")
 
@@ -44,6 +44,60 @@ def _ptr(x):
         return ctypes.c_void_p(x.ctypes.data)
     assert x.is_contiguous()
     return ctypes.c_void_p(x.data_ptr())
+
+
+# Device-memory hook (tp_set_allocator): alloc(bytes, stream, ctx) -> pointer,
+# free(pointer, bytes, stream, ctx).
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_hook = None  # the installed callbacks, kept alive while the library may call them
+
+
+def set_allocator(alloc, free):
+    """Installs Python callables as the library's device allocator:
+    alloc(nbytes, stream_handle) -> int pointer (0 or an exception: out of
+    memory), free(pointer, nbytes, stream_handle). None, None restores the
+    library's default (cudaMallocAsync / cudaFreeAsync). Process-wide; set it
+    while no library call is running."""
+    global _hook
+    if alloc is None and free is None:
+        check(lib().tp_set_allocator(None, None, None), "tp_set_allocator")
+        _hook = None
+        return
+
+    def _a(nbytes, stream, ctx):
+        try:
+            return alloc(int(nbytes), int(stream or 0)) or None
+        except Exception:
+            return None
+
+    def _f(ptr, nbytes, stream, ctx):
+        free(int(ptr or 0), int(nbytes), int(stream or 0))
+
+    hook = (ALLOC_FN(_a), FREE_FN(_f))
+    check(lib().tp_set_allocator(ctypes.cast(hook[0], ctypes.c_void_p),
+                                 ctypes.cast(hook[1], ctypes.c_void_p), None), "tp_set_allocator")
+    _hook = hook
+
+
+def use_torch_allocator():
+    """Routes every device allocation of the library through PyTorch's
+    caching allocator (on the stream the library allocates on), so the
+    partitioner shares torch's memory pool instead of allocating beside it."""
+    torch = _torch()
+
+    def alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, stream=stream)
+
+    def free(ptr, nbytes, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    set_allocator(alloc, free)
+
+
+def use_default_allocator():
+    """Restores the library's own stream-ordered allocator."""
+    set_allocator(None, None)
 
 
 def default_params(**overrides) -> Params:

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <new>
 
 #include "decode.cuh"
 
@@ -12,9 +13,10 @@ namespace tp {
 
 // ---------------------------------------------------------------- allocator
 namespace {
-void *(*g_alloc)(size_t, void *, void *) = nullptr;
-void (*g_free)(void *, size_t, void *, void *) = nullptr;
-void *g_ctx = nullptr;
+// The current hook; hooks are immutable and never freed (buffers keep
+// pointing at the one that made them). Null functions: cudaMallocAsync.
+const AllocHook g_default_hook{nullptr, nullptr, nullptr};
+std::atomic<const AllocHook *> g_hook{&g_default_hook};
 std::atomic<int> g_sms{0};
 }  // namespace
 
@@ -33,11 +35,12 @@ static void mem_add(int64_t b) {
   if (t_live > t_peak) t_peak = t_live;
 }
 
-void *dev_alloc(size_t bytes, cudaStream_t s) {
+void *dev_alloc(size_t bytes, cudaStream_t s, const AllocHook **from) {
   if (bytes == 0) return nullptr;
   void *p = nullptr;
-  if (g_alloc) {
-    p = g_alloc(bytes, (void *)s, g_ctx);
+  const AllocHook *h = g_hook.load();
+  if (h->alloc) {
+    p = h->alloc(bytes, (void *)s, h->ctx);
     if (!p) throw Error{TP_ERR_OOM};
   } else {
     cudaError_t e = cudaMallocAsync(&p, bytes, s);
@@ -47,14 +50,15 @@ void *dev_alloc(size_t bytes, cudaStream_t s) {
     }
   }
   mem_add((int64_t)bytes);
+  *from = h;
   return p;
 }
 
-void dev_free(void *p, size_t bytes, cudaStream_t s) {
+void dev_free(void *p, size_t bytes, cudaStream_t s, const AllocHook *from) {
   if (!p) return;
   t_live -= (int64_t)bytes;
-  if (g_free) {
-    g_free(p, bytes, (void *)s, g_ctx);
+  if (from && from->free) {
+    from->free(p, bytes, (void *)s, from->ctx);
     return;
   }
   cudaFreeAsync(p, s);
@@ -851,8 +855,13 @@ extern "C" int tp_profile_read(tp_profile_entry *out, int max, void *stream) {
 extern "C" tp_status tp_set_allocator(void *(*alloc)(size_t, void *, void *),
                                       void (*free_fn)(void *, size_t, void *, void *), void *ctx) {
   if ((alloc == nullptr) != (free_fn == nullptr)) return TP_ERR_INVALID;
-  tp::g_alloc = alloc;
-  tp::g_free = free_fn;
-  tp::g_ctx = ctx;
+  if (!alloc) {
+    tp::g_hook.store(&tp::g_default_hook);
+    return TP_OK;
+  }
+  // kept for the process lifetime: buffers made through it free through it
+  const tp::AllocHook *h = new (std::nothrow) tp::AllocHook{alloc, free_fn, ctx};
+  if (!h) return TP_ERR_OOM;
+  tp::g_hook.store(h);
   return TP_OK;
 }

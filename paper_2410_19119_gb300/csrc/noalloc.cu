@@ -2,13 +2,15 @@
 //
 // tp_metrics needs a little device scratch (the cut accumulator and the
 // per-block weight sums) and takes it from the allocator. Some callers
-// cannot allocate at that point: code running while a CUDA stream is being
-// captured into a graph (cudaMalloc is not a capturable operation), code
-// with a fixed device-memory footprint decided up front (a service that
-// admits work by memory budget, or a pool that must not grow), and callers
-// that own no allocator of their own. tp_metrics_static serves them: its
-// scratch is the file-scope array below, so it calls no cudaMalloc,
-// cudaFree or allocating library routine.
+// cannot allocate device memory at the point where they want the metrics:
+// code with a device-memory footprint fixed up front (a service that admits
+// work by memory budget, or a pool that must not grow), and callers that own
+// no allocator of their own. tp_metrics_static serves them: its scratch is
+// the file-scope array below, so it calls no cudaMalloc, cudaFree or
+// allocating library routine. It synchronises the stream to return host
+// values, so it cannot be recorded into a CUDA graph; on a stream that is
+// being captured it returns TP_ERR_INVALID before enqueuing anything, which
+// leaves the caller's capture intact.
 #include <mutex>
 
 #include "decode.cuh"
@@ -16,12 +18,14 @@
 namespace tp {
 namespace {
 
-// Largest k accepted. Scratch = 8 bytes x (1 + kStaticMaxBlocks) = 128 KiB,
-// held by every GPU that loads this library until the process exits.
+// Largest k accepted. Scratch = 8 bytes x (2 + kStaticMaxBlocks), about
+// 128 KiB, held by every GPU that loads this library until the process exits.
 constexpr int32_t kStaticMaxBlocks = 16383;
+constexpr int kScratchCut = 0;     // edge-cut accumulator (both directions)
+constexpr int kScratchBad = 1;     // set when a block id lies outside [0, k)
+constexpr int kScratchBlocks = 2;  // [2, 2 + k): block weights
 
-// [0] edge-cut accumulator (both directions), [1 .. 1 + k) block weights.
-__device__ __align__(256) unsigned long long g_static_scratch[1 + kStaticMaxBlocks];
+__device__ __align__(256) unsigned long long g_static_scratch[kScratchBlocks + kStaticMaxBlocks];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
@@ -43,11 +47,19 @@ unsigned long long *scratch_address() {
   return g_static_ptr[dev];
 }
 
-__global__ void k_static_weights(const int32_t *part, const int64_t *vw, int64_t n,
-                                 unsigned long long *B) {
+// Block ids outside [0, k) are skipped (they would index past the array)
+// and flagged in bad.
+__global__ void k_static_weights(const int32_t *part, const int64_t *vw, int64_t n, int32_t k,
+                                 unsigned long long *B, unsigned long long *bad) {
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
-       u += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&B[part[u]], (unsigned long long)(vw ? vw[u] : 1));
+       u += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t b = part[u];
+    if (b < 0 || b >= k) {
+      *bad = 1;
+      continue;
+    }
+    atomicAdd(&B[b], (unsigned long long)(vw ? vw[u] : 1));
+  }
 }
 
 template <bool COMP>
@@ -74,25 +86,35 @@ extern "C" tp_status tp_metrics_static(const tp_graph *g, const int32_t *d_part,
                                        int64_t *cut, int64_t *h_block_weights, void *stream) {
   if (!g || k < 1 || (g->n && !d_part)) return TP_ERR_INVALID;
   if (k > kStaticMaxBlocks) return TP_ERR_BUDGET;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return TP_ERR_CUDA;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return TP_ERR_INVALID;  // nothing enqueued
   return guard([&] {
-    cudaStream_t s = (cudaStream_t)stream;
     unsigned long long *scratch = scratch_address();
     // the array keeps the previous call's sums: clear what this call uses
-    TP_CUDA(cudaMemsetAsync(scratch, 0, (size_t)(1 + k) * sizeof(unsigned long long), s));
+    TP_CUDA(cudaMemsetAsync(scratch, 0, (size_t)(kScratchBlocks + k) * sizeof(unsigned long long),
+                            s));
     if (g->n) {
       launch(k_static_weights, grid_for(g->n, 256), 256, 0, s, d_part,
-             g->unit_vw ? nullptr : g->vw.get(), g->n, scratch + 1);
+             g->unit_vw ? nullptr : g->vw.get(), g->n, k, scratch + kScratchBlocks,
+             scratch + kScratchBad);
       unsigned blocks = grid_for(g->n * 32, 256);
-      if (g->compressed) launch(k_static_cut<true>, blocks, 256, 0, s, view(g), d_part, scratch);
-      else launch(k_static_cut<false>, blocks, 256, 0, s, view(g), d_part, scratch);
+      if (g->compressed)
+        launch(k_static_cut<true>, blocks, 256, 0, s, view(g), d_part, scratch + kScratchCut);
+      else launch(k_static_cut<false>, blocks, 256, 0, s, view(g), d_part, scratch + kScratchCut);
       TP_LAUNCH_CHECK();
     }
-    unsigned long long c2 = 0;
-    TP_CUDA(cudaMemcpyAsync(&c2, scratch, sizeof(c2), cudaMemcpyDeviceToHost, s));
+    unsigned long long head[2] = {0, 0};  // cut, bad-id flag
+    TP_CUDA(cudaMemcpyAsync(head, scratch, sizeof(head), cudaMemcpyDeviceToHost, s));
     if (h_block_weights)
-      TP_CUDA(cudaMemcpyAsync(h_block_weights, scratch + 1, (size_t)k * sizeof(int64_t),
-                              cudaMemcpyDeviceToHost, s));
+      TP_CUDA(cudaMemcpyAsync(h_block_weights, scratch + kScratchBlocks,
+                              (size_t)k * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     TP_CUDA(cudaStreamSynchronize(s));
-    if (cut) *cut = (int64_t)(c2 / 2);
+    TP_REQUIRE(head[kScratchBad] == 0, TP_ERR_INVALID);
+    if (cut) *cut = (int64_t)(head[kScratchCut] / 2);
   });
 }

@@ -49,8 +49,16 @@ tp_status guard(F &&f) {
 }
 
 // ---------------------------------------------------------------- device memory
-void *dev_alloc(size_t bytes, cudaStream_t s);
-void dev_free(void *p, size_t bytes, cudaStream_t s);
+// The allocator a buffer came from (tp_set_allocator's functions, or null
+// functions for the library's own cudaMallocAsync). Every buffer is released
+// through the allocator that made it, even if the hook changed meanwhile.
+struct AllocHook {
+  void *(*alloc)(size_t, void *, void *);
+  void (*free)(void *, size_t, void *, void *);
+  void *ctx;
+};
+void *dev_alloc(size_t bytes, cudaStream_t s, const AllocHook **from);
+void dev_free(void *p, size_t bytes, cudaStream_t s, const AllocHook *from);
 // Per-thread device-memory high-water mark: mem_mark() starts a window and
 // returns the current holding; mem_peak_since(mark) is the rise since then.
 int64_t mem_mark();
@@ -62,16 +70,17 @@ struct Buf {
   T *p = nullptr;
   size_t n = 0;
   cudaStream_t s = nullptr;
+  const AllocHook *from = nullptr;
   Buf() = default;
   Buf(size_t count, cudaStream_t st) { alloc(count, st); }
   void alloc(size_t count, cudaStream_t st) {
     release();
     s = st;
+    p = count ? static_cast<T *>(dev_alloc(count * sizeof(T), st, &from)) : nullptr;
     n = count;
-    p = count ? static_cast<T *>(dev_alloc(count * sizeof(T), st)) : nullptr;
   }
   void release() {
-    if (p) dev_free(p, n * sizeof(T), s);
+    if (p) dev_free(p, n * sizeof(T), s, from);
     p = nullptr;
     n = 0;
   }
@@ -79,10 +88,10 @@ struct Buf {
   ~Buf() { release(); }
   Buf(const Buf &) = delete;
   Buf &operator=(const Buf &) = delete;
-  Buf(Buf &&o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr, o.n = 0; }
+  Buf(Buf &&o) noexcept : p(o.p), n(o.n), s(o.s), from(o.from) { o.p = nullptr, o.n = 0; }
   Buf &operator=(Buf &&o) noexcept {
     release();
-    p = o.p, n = o.n, s = o.s;
+    p = o.p, n = o.n, s = o.s, from = o.from;
     o.p = nullptr, o.n = 0;
     return *this;
   }

@@ -34,13 +34,13 @@ EPS = 0.03
 
 def graph_hash(xadj, adj):
     h = hashlib.sha256()
-    h.update(np.ascontiguousarray(xadj, np.int64).tobytes())
-    h.update(np.ascontiguousarray(adj, np.int32).tobytes())
+    h.update(np.ascontiguousarray(xadj, np.int64).data)
+    h.update(np.ascontiguousarray(adj, np.int32).data)
     return h.hexdigest()
 
 
 def array_hash(a):
-    return hashlib.sha256(np.ascontiguousarray(a, np.int32).tobytes()).hexdigest()
+    return hashlib.sha256(np.ascontiguousarray(a, np.int32).data).hexdigest()
 
 
 def main():

@@ -51,7 +51,16 @@ def _check_line(line, steps, warmup, unit):
 def test_reference_arm_single_graph():
     lines = _bench("--impl", "reference", "--workload", "gnm14", "--steps", "3", "--warmup", "3")
     assert len(lines) == 1
-    _check_line(json.loads(lines[0]), 3, 3, "GTEPS")
+    line = json.loads(lines[0])
+    _check_line(line, 3, 3, "GTEPS")
+    # the same config object and e2e unit as the GPU arm prints, so the two
+    # lines can be compared key by key
+    import bench
+
+    w = bench.WORKLOADS["gnm14"]
+    xadj, adj = bench.make_graph(w)
+    assert line["config"] == bench.bench_config(w, len(xadj) - 1, len(adj), 1)
+    assert line["e2e"]["unit"] == bench.E2E_UNIT
 
 
 def test_reference_arm_batch():

@@ -123,3 +123,51 @@ def test_rmat26_partition_properties(rmat26):
     assert stz["cut"] == _cut_host(xadj, adj, part)
     B = np.bincount(part, minlength=256)
     assert B.max() == stz["max_block_weight"]
+
+
+def _golden_rmat26():
+    import json
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "rmat26_k256.json")
+    if not os.path.exists(path):
+        pytest.skip("tests/golden/rmat26_k256.json not written yet (make_rmat_golden.py)")
+    with open(path) as f:
+        return json.load(f)
+
+
+def _sha(a, dtype):
+    import hashlib
+
+    return hashlib.sha256(np.ascontiguousarray(a, dtype).data).hexdigest()
+
+
+def test_rmat26_partition_equals_oracle(rmat26):
+    """The whole k = 256 partition of R-MAT scale 26, CSR and compressed,
+    against the oracle's result stored by tests/golden/make_rmat_golden.py
+    (the oracle takes about an hour on one core, so it runs once and its
+    result is kept by the hash of the input graph and the parameters)."""
+    gold = _golden_rmat26()
+    xadj, adj = rmat26
+    import hashlib
+
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(xadj, np.int64).data)
+    h.update(np.ascontiguousarray(adj, np.int32).data)
+    assert h.hexdigest() == gold["graph_sha256"]
+    P = gold["params"]
+    p = tp.default_params(seed=P["seed"])
+    for key in ("cluster_rounds", "refine_rounds", "sub_rounds", "c_lim", "ip_attempts",
+                "two_hop", "max_levels"):
+        assert getattr(p, key) == P[key], key
+    g = tp.graph_from_csr(xadj, adj)
+    z = g.compress()
+    C = tp.lp_cluster(z, gold["cluster_cap"], p, 0)
+    assert _sha(_host(C), np.int32) == gold["level0_clustering_sha256"]
+    del C
+    for gg in (z, g):
+        part, st = tp.partition(gg, P["k"], P["eps"], p)
+        assert _sha(_host(part), np.int32) == gold["partition_sha256"]
+        for key in ("cut", "max_block_weight", "l_max", "imbalance", "levels", "level_n",
+                    "level_m2"):
+            assert st[key] == gold["stats"][key], key
