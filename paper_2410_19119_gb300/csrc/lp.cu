@@ -76,6 +76,8 @@ struct RateCtx {
   const int32_t *bucket;
   const int64_t *bucket_off;
   int64_t bucket_nb;
+  // per listed vertex: record start << 8 | record length (compressed graphs)
+  const uint64_t *bucket_rec;
 };
 
 __device__ __forceinline__ int64_t node_w(const GView &g, int64_t u) { return g.vw ? g.vw[u] : 1; }
@@ -355,9 +357,8 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
 // before the record are turned into value ends and, like the header, are
 // written to slot 0, which the first neighbour then overwrites; bytes after
 // it are turned into continuation bytes, so they end no value.
-__device__ __forceinline__ int lane_decode(const GView &g, int32_t u, uint32_t *col) {
+__device__ __forceinline__ int lane_decode(const GView &g, uint64_t b, uint64_t e, uint32_t *col) {
   constexpr int G = 5;  // 80-byte window
-  const uint64_t b = off_at(g, u), e = off_at(g, u + 1);
   const uint64_t ws = b & ~(uint64_t)15;
   const int p0 = (int)(b - ws), endp = (int)(e - ws);
   const uint4 *src = reinterpret_cast<const uint4 *>(g.bytes + ws);
@@ -402,10 +403,26 @@ __device__ __forceinline__ int lane_decode(const GView &g, int32_t u, uint32_t *
   return min(max(idx, 0), kLaneMaxDeg);
 }
 
+// Record range of a compressed lane-tier vertex: from the bucket list when
+// it carries the ranges (coalesced with the vertex ids), else the offsets.
+__device__ __forceinline__ void lane_record(const GView &g, const uint64_t *rec, int64_t pos,
+                                            int32_t u, uint64_t &b, uint64_t &e) {
+  if (rec) {
+    const uint64_t r = rec[pos];
+    b = r >> 8;
+    e = b + (r & 255u);
+  } else {
+    b = off_at(g, u);
+    e = off_at(g, u + 1);
+  }
+}
+
 template <bool COMP>
-__device__ __forceinline__ void lane_prefetch(const GView &g, int64_t u) {
+__device__ __forceinline__ void lane_prefetch(const GView &g, const uint64_t *rec, int64_t pos,
+                                              int64_t u) {
   if (COMP) {
-    const uint64_t b = off_at(g, u), e = off_at(g, u + 1);
+    uint64_t b, e;
+    lane_record(g, rec, pos, (int32_t)u, b, e);
     prefetch_l2(g.bytes + b);
     prefetch_l2(g.bytes + e);
   } else {
@@ -460,111 +477,12 @@ struct LaneMovers {
   int32_t u[kLaneWin], t[kLaneWin], o[kLaneWin], g[kLaneWin];
 };
 
-// Rates one batch: this lane's vertex u with deg neighbours (compressed:
-// already decoded into the column; CSR: adjacency from xadj[u]) and emits
-// the favourite, or queues the move in the warp's window buffer (nmv
-// records so far, warp-uniform). N >= the largest degree of the batch.
-template <bool COMP, int MODE, bool W, int N>
-__device__ __forceinline__ void lane_batch(const RateCtx &c, bool has, int32_t u, int deg,
-                                           uint32_t *col, uint32_t *wcol, uint8_t *cnt,
-                                           LaneMovers &mb, int &nmv) {
-  const int32_t own = has ? c.label[u] : -1;
-  int32_t rown = 0, rmax = 0;
-  int ncand = 0;
-  int32_t *ccol = reinterpret_cast<int32_t *>(col);
-  // gather, sort, and turn runs into (label, rating) pairs without own
-  if constexpr (W) {  // weighted levels are CSR
-    // label << 32 | weight; padding: label INT32_MAX, weight 0
-    constexpr uint64_t kPad = (uint64_t)INT32_MAX << 32;
-    const int64_t b = has ? c.g.xadj[u] : 0;
-    uint64_t a[kLaneMaxDeg];
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-      a[i] = i < deg ? ((uint64_t)(uint32_t)__ldg(c.label + __ldcs(c.g.adj + b + i)) << 32) |
-                           (uint32_t)__ldcs(c.g.ew + b + i)
-                     : kPad;
-    oem_sort<N>(a);
-    uint32_t run = 0;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const int32_t x = (int32_t)(a[i] >> 32);
-      run += (uint32_t)a[i];
-      const bool end = i + 1 == N || (int32_t)(a[i + 1] >> 32) != x;
-      const bool real = end && x != INT32_MAX;
-      const bool cand = real && x != own;
-      ccol[ncand * 32] = x;
-      wcol[ncand * 32] = run;
-      rown = real && !cand ? (int32_t)run : rown;
-      rmax = cand ? max(rmax, (int32_t)run) : rmax;
-      ncand += cand;
-      run = end ? 0u : run;
-    }
-  } else {
-    int32_t a[kLaneMaxDeg];
-    if constexpr (COMP) {
-      // raw values -> neighbour ids (first: signed offset from u, then gaps)
-      const uint32_t nmax = (uint32_t)(c.g.n - 1);
-      int32_t prev = u;
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        const uint32_t v = col[i * 32];
-        int32_t x = i == 0 ? ((v & 1u) ? u - (int32_t)(v >> 1) : u + (int32_t)(v >> 1))
-                           : prev + (int32_t)v;
-        // streams are validated on creation; the clamp only keeps a
-        // corrupted one from reading out of bounds
-        x = (int32_t)min((uint32_t)x, nmax);
-        prev = x;
-        a[i] = i < deg ? __ldg(c.label + x) : INT32_MAX;
-      }
-    } else {
-      const int64_t b = has ? c.g.xadj[u] : 0;
-#pragma unroll
-      for (int i = 0; i < N; ++i) a[i] = i < deg ? __ldg(c.label + __ldcs(c.g.adj + b + i)) : INT32_MAX;
-    }
-    oem_sort<N>(a);
-    // branch-free run scan: every position writes slot ncand, which only
-    // advances past a candidate (later writes overwrite the others)
-    int start = 0;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      const bool end = i + 1 == N || a[i + 1] != a[i];
-      const int32_t run = i + 1 - start;
-      const bool real = end && a[i] != INT32_MAX;
-      const bool cand = real && a[i] != own;
-      ccol[ncand * 32] = a[i];
-      cnt[ncand * 32] = (uint8_t)run;
-      rown = real && !cand ? run : rown;
-      rmax = cand ? max(rmax, run) : rmax;
-      ncand += cand;
-      start = end ? i + 1 : start;
-    }
-  }
-  auto rating = [&](int k) -> int32_t { return W ? (int32_t)wcol[k * 32] : (int32_t)cnt[k * 32]; };
-  const int64_t cu = has ? node_w(c.g, u) : 1;
-  LaneCand best{-1, 0xffffffffu, INT32_MAX};
-  if (MODE == M_FAV ? rmax > 0 : rmax > rown) {
-    const uint64_t hv = tie_key<MODE>(c, u);
-    // the best candidate overall is tied at the top rating
-    LaneCand b1{-1, 0xffffffffu, INT32_MAX};
-    for (int k = 0; k < ncand; ++k) {
-      if (rating(k) != rmax) continue;
-      const int32_t x = ccol[k * 32];
-      const LaneCand cand{rmax, tie_hash(hv, x), x};
-      if (lane_better(cand, b1)) b1 = cand;
-    }
-    if (MODE == M_FAV || c.lw[b1.x] + cu <= c.cap) {
-      best = b1;
-    } else {
-      // the winner is full: the best admissible candidate that improves
-      for (int k = 0; k < ncand; ++k) {
-        const int32_t r = rating(k);
-        const int32_t x = ccol[k * 32];
-        if (r <= rown || x == b1.x) continue;
-        const LaneCand cand{r, tie_hash(hv, x), x};
-        if (lane_better(cand, best) && c.lw[x] + cu <= c.cap) best = cand;
-      }
-    }
-  }
+// Emits the favourite (two-hop mode) or queues the move of this lane's
+// vertex in the warp's buffer (nmv records so far, warp-uniform).
+template <int MODE, class Movers>
+__device__ __forceinline__ void emit_lane(const RateCtx &c, bool has, int32_t u, int32_t own,
+                                          int32_t rown, int64_t cu, const LaneCand &best,
+                                          Movers &mb, int &nmv) {
   if (MODE == M_FAV) {
     if (has) c.fav[u] = best.r > 0 ? best.x : (int32_t)c.g.n;
   } else {
@@ -582,6 +500,235 @@ __device__ __forceinline__ void lane_batch(const RateCtx &c, bool has, int32_t u
   }
 }
 
+// Rates one batch: this lane's vertex u with deg neighbours (compressed:
+// already decoded into the column; CSR: adjacency from xadj[u]) and emits
+// the favourite, or queues the move in the warp's window buffer (nmv
+// records so far, warp-uniform). N >= the largest degree of the batch.
+template <bool COMP, int MODE, bool W, int N>
+__device__ __forceinline__ void lane_batch(const RateCtx &c, bool has, int32_t u, int deg,
+                                           uint32_t *col, uint32_t *wcol, uint8_t *cnt,
+                                           LaneMovers &mb, int &nmv) {
+  const int32_t own = has ? c.label[u] : -1;
+  int32_t rown = 0, rmax = 0;
+  int32_t *ccol = reinterpret_cast<int32_t *>(col);
+  if constexpr (W) {  // weighted levels are CSR; candidates listed in the column
+    // label << 32 | weight; padding: label INT32_MAX, weight 0
+    constexpr uint64_t kPad = (uint64_t)INT32_MAX << 32;
+    const int64_t b = has ? c.g.xadj[u] : 0;
+    uint64_t a[kLaneMaxDeg];
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      a[i] = i < deg ? ((uint64_t)(uint32_t)__ldg(c.label + __ldcs(c.g.adj + b + i)) << 32) |
+                           (uint32_t)__ldcs(c.g.ew + b + i)
+                     : kPad;
+    oem_sort<N>(a);
+    int ncand = 0;
+    uint32_t run = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const int32_t x = (int32_t)(a[i] >> 32);
+      run += (uint32_t)a[i];
+      const bool end = i + 1 == N || (int32_t)(a[i + 1] >> 32) != x;
+      const bool real = end && x != INT32_MAX;
+      const bool cand = real && x != own;
+      ccol[ncand * 32] = x;
+      wcol[ncand * 32] = run;
+      rown = real && !cand ? (int32_t)run : rown;
+      rmax = cand ? max(rmax, (int32_t)run) : rmax;
+      ncand += cand;
+      run = end ? 0u : run;
+    }
+    const int64_t cu = has ? node_w(c.g, u) : 1;
+    LaneCand best{-1, 0xffffffffu, INT32_MAX};
+    if (MODE == M_FAV ? rmax > 0 : rmax > rown) {
+      const uint64_t hv = tie_key<MODE>(c, u);
+      // the best candidate overall is tied at the top rating
+      LaneCand b1{-1, 0xffffffffu, INT32_MAX};
+      for (int k = 0; k < ncand; ++k) {
+        if ((int32_t)wcol[k * 32] != rmax) continue;
+        const int32_t x = ccol[k * 32];
+        const LaneCand cand{rmax, tie_hash(hv, x), x};
+        if (lane_better(cand, b1)) b1 = cand;
+      }
+      if (MODE == M_FAV || c.lw[b1.x] + cu <= c.cap) {
+        best = b1;
+      } else {
+        // the winner is full: the best admissible candidate that improves
+        for (int k = 0; k < ncand; ++k) {
+          const int32_t r = (int32_t)wcol[k * 32];
+          const int32_t x = ccol[k * 32];
+          if (r <= rown || x == b1.x) continue;
+          const LaneCand cand{r, tie_hash(hv, x), x};
+          if (lane_better(cand, best) && c.lw[x] + cu <= c.cap) best = cand;
+        }
+      }
+    }
+    emit_lane<MODE>(c, has, u, own, rown, cu, best, mb, nmv);
+  } else if constexpr (COMP) {
+    // compressed, unit weights: the sorted runs become a list of (label,
+    // rating) candidates in the lane's column; the decoder already keeps the
+    // ALU pipe busy, and listing takes fewer instructions than walking the
+    // runs when many labels tie (the first rounds)
+    int32_t a[kLaneMaxDeg];
+    {
+      // raw values -> neighbour ids (first: signed offset from u, then gaps)
+      const uint32_t nmax = (uint32_t)(c.g.n - 1);
+      int32_t prev = u;
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const uint32_t v = col[i * 32];
+        int32_t x = i == 0 ? ((v & 1u) ? u - (int32_t)(v >> 1) : u + (int32_t)(v >> 1))
+                           : prev + (int32_t)v;
+        // streams are validated on creation; the clamp only keeps a
+        // corrupted one from reading out of bounds
+        x = (int32_t)min((uint32_t)x, nmax);
+        prev = x;
+        a[i] = i < deg ? __ldg(c.label + x) : INT32_MAX;
+      }
+    }
+    oem_sort<N>(a);
+    // branch-free run scan: every position writes slot ncand, which only
+    // advances past a candidate (later writes overwrite the others)
+    int ncand = 0, start = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const bool end = i + 1 == N || a[i + 1] != a[i];
+      const int32_t run = i + 1 - start;
+      const bool real = end && a[i] != INT32_MAX;
+      const bool cand = real && a[i] != own;
+      ccol[ncand * 32] = a[i];
+      cnt[ncand * 32] = (uint8_t)run;
+      rown = real && !cand ? run : rown;
+      rmax = cand ? max(rmax, run) : rmax;
+      ncand += cand;
+      start = end ? i + 1 : start;
+    }
+    const int64_t cu = has ? node_w(c.g, u) : 1;
+    LaneCand best{-1, 0xffffffffu, INT32_MAX};
+    if (MODE == M_FAV ? rmax > 0 : rmax > rown) {
+      const uint64_t hv = tie_key<MODE>(c, u);
+      // the best candidate overall is tied at the top rating
+      LaneCand b1{-1, 0xffffffffu, INT32_MAX};
+      for (int k = 0; k < ncand; ++k) {
+        if ((int32_t)cnt[k * 32] != rmax) continue;
+        const int32_t x = ccol[k * 32];
+        const LaneCand cand{rmax, tie_hash(hv, x), x};
+        if (lane_better(cand, b1)) b1 = cand;
+      }
+      if (MODE == M_FAV || c.lw[b1.x] + cu <= c.cap) {
+        best = b1;
+      } else {
+        // the winner is full: the best admissible candidate that improves
+        for (int k = 0; k < ncand; ++k) {
+          const int32_t r = (int32_t)cnt[k * 32];
+          const int32_t x = ccol[k * 32];
+          if (r <= rown || x == b1.x) continue;
+          const LaneCand cand{r, tie_hash(hv, x), x};
+          if (lane_better(cand, best) && c.lw[x] + cu <= c.cap) best = cand;
+        }
+      }
+    }
+    emit_lane<MODE>(c, has, u, own, rown, cu, best, mb, nmv);
+  } else {
+    // CSR, unit weights: the labels are sorted with the own label as padding (its
+    // count is corrected below), then one register pass finds the own
+    // rating, the top rating among other labels, how many labels share it
+    // and the first two of them
+    int32_t a[kLaneMaxDeg];
+    {
+      const int64_t b = has ? c.g.xadj[u] : 0;
+#pragma unroll
+      for (int i = 0; i < N; ++i) a[i] = i < deg ? __ldg(c.label + __ldcs(c.g.adj + b + i)) : own;
+    }
+    oem_sort<N>(a);
+    int start = 0, ntop = 0;
+    int32_t x1 = 0, x2 = 0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const bool end = i + 1 == N || a[i + 1] != a[i];
+      const int32_t run = i + 1 - start;
+      const bool isown = a[i] == own;
+      rown = end && isown ? run : rown;
+      const bool cand = end && !isown;
+      const bool gt = cand && run > rmax, eq = cand && run == rmax;
+      x2 = eq && ntop == 1 ? a[i] : x2;
+      x1 = gt ? a[i] : x1;
+      ntop = gt ? 1 : ntop + (eq ? 1 : 0);
+      rmax = gt ? run : rmax;
+      start = end ? i + 1 : start;
+    }
+    rown -= N - deg;  // the padding counted as own label
+    const int64_t cu = has ? node_w(c.g, u) : 1;
+    const bool go = MODE == M_FAV ? rmax > 0 : rmax > rown;
+    uint64_t hv = 0;
+    LaneCand b1{rmax, 0u, x1};
+    if (go && ntop >= 2) {
+      hv = tie_key<MODE>(c, u);
+      const LaneCand c1{rmax, tie_hash(hv, x1), x1}, c2{rmax, tie_hash(hv, x2), x2};
+      b1 = lane_better(c1, c2) ? c1 : c2;
+    }
+    const bool many = go && ntop >= 3;
+    bool full = false;
+    if (go && MODE != M_FAV) full = c.lw[b1.x] + cu > c.cap;
+    // rare: three or more labels tied at the top, or the winner is full;
+    // the sorted labels go to this lane's column and the runs are walked
+    if (__any_sync(kFull, many || full)) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) ccol[i * 32] = a[i];
+      if (many || full) {
+        if (!hv) hv = tie_key<MODE>(c, u);
+        const int own_run = rown + (N - deg);  // the own label's entries, padding included
+        LaneCand bb{-1, 0xffffffffu, INT32_MAX};
+        for (int i = 0; i < N;) {
+          const int32_t x = ccol[i * 32];
+          if (x == own) {
+            i += own_run;
+            continue;
+          }
+          int j = i + 1;
+          while (j < N && ccol[j * 32] == x) ++j;
+          const int32_t r = j - i;
+          i = j;
+          if (many && !full) {  // the best of the top-tied labels
+            if (r != rmax) continue;
+          } else {  // the best admissible label that improves
+            if (r <= rown) continue;
+          }
+          const LaneCand cand{r, tie_hash(hv, x), x};
+          if (lane_better(cand, bb) && (!full || MODE == M_FAV || c.lw[x] + cu <= c.cap))
+            bb = cand;
+        }
+        if (!full) {
+          b1 = bb;
+          if (MODE != M_FAV) full = c.lw[b1.x] + cu > c.cap;
+          if (full) {  // the top-tied winner is full: look again for an admissible one
+            bb = LaneCand{-1, 0xffffffffu, INT32_MAX};
+            for (int i = 0; i < N;) {
+              const int32_t x = ccol[i * 32];
+              if (x == own) {
+                i += own_run;
+                continue;
+              }
+              int j = i + 1;
+              while (j < N && ccol[j * 32] == x) ++j;
+              const int32_t r = j - i;
+              i = j;
+              if (r <= rown) continue;
+              const LaneCand cand{r, tie_hash(hv, x), x};
+              if (lane_better(cand, bb) && c.lw[x] + cu <= c.cap) bb = cand;
+            }
+          }
+        }
+        if (full) b1 = bb;
+      }
+    }
+    LaneCand best{-1, 0xffffffffu, INT32_MAX};
+    if (go) best = b1;
+    emit_lane<MODE>(c, has, u, own, rown, cu, best, mb, nmv);
+    return;
+  }
+}
+
 template <bool W>
 __host__ __device__ constexpr int lane_warps() { return W ? 4 : kLaneWarps; }
 
@@ -593,15 +740,15 @@ __global__ void __launch_bounds__(lane_warps<W>() * 32, W ? 1 : kLaneBlocksPerSM
   // per lane: staged record words, then candidate labels
   __shared__ uint32_t lab_all[WARPS][kLaneMaxDeg][32];
   __shared__ uint32_t aux_all[WARPS][W ? kLaneMaxDeg : 1][32];  // candidate ratings (weighted)
-  __shared__ uint8_t cnt_all[WARPS][W ? 1 : kLaneMaxDeg][32];   // candidate ratings (unit)
+  __shared__ uint8_t cnt_all[WARPS][COMP && !W ? kLaneMaxDeg : 1][32];  // candidate ratings
   __shared__ int32_t queue_all[WARPS][kLaneQueue];
   __shared__ LaneMovers movers_all[WARPS];
   const int lane = lane_id(), w = threadIdx.x >> 5;
   uint32_t *col = &lab_all[w][0][lane];
   uint32_t *wcol = &aux_all[w][0][lane];
-  uint8_t *cnt = &cnt_all[w][0][lane];
   int32_t *queue = queue_all[w];
   LaneMovers &mb = movers_all[w];
+  uint8_t *cnt = &cnt_all[w][0][lane];
   // warps and list positions fit 32 bits (lists hold < 2^31 vertex ids)
   const int32_t gw = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int32_t nw = (int32_t)((gridDim.x * blockDim.x) >> 5);
@@ -609,12 +756,14 @@ __global__ void __launch_bounds__(lane_warps<W>() * 32, W ? 1 : kLaneBlocksPerSM
   const bool list_mode = MODE == M_LP && c.bucket != nullptr;
   int32_t bcount = 0, bnext = gw * kLaneWin;
   const int32_t *blist = c.bucket;
+  const uint64_t *brec = COMP ? c.bucket_rec : nullptr;
   int64_t base = (int64_t)gw * 256;
   int j8 = 0, pending = 0;  // slab scan position; queued vertices (warp-uniform)
   if (list_mode) {
     const int64_t bstart = c.bucket_off[(int64_t)c.s * c.bucket_nb];
     bcount = (int32_t)(c.bucket_off[(int64_t)(c.s + 1) * c.bucket_nb] - bstart);
     blist += bstart;
+    if (brec) brec += bstart;
     base = c.g.n;  // no slab scan
   }
   for (;;) {
@@ -643,15 +792,21 @@ __global__ void __launch_bounds__(lane_warps<W>() * 32, W ? 1 : kLaneBlocksPerSM
     // the graph, so a batch's records and label gathers share cache lines
     // (grouping a window by degree instead was measured slower)
     const int32_t *win = list_mode ? blist + wstart : queue;
+    const uint64_t *wrec = list_mode && brec ? brec + wstart : nullptr;
     int nmv = 0;  // movers of this window so far (warp-uniform)
     for (int q = 0; q < take; q += 32) {
       const bool has = q + lane < take;
       const int32_t u = has ? win[q + lane] : 0;
-      if (q + 32 + lane < take) lane_prefetch<COMP>(c.g, win[q + 32 + lane]);
+      if (q + 32 + lane < take) lane_prefetch<COMP>(c.g, wrec, q + 32 + lane, win[q + 32 + lane]);
       int deg = 0;
       if (has) {
-        if (COMP) deg = lane_decode(c.g, u, col);
-        else deg = min((int)(c.g.xadj[u + 1] - c.g.xadj[u]), kLaneMaxDeg);
+        if (COMP) {
+          uint64_t rb, re;
+          lane_record(c.g, wrec, q + lane, u, rb, re);
+          deg = lane_decode(c.g, rb, re, col);
+        } else {
+          deg = min((int)(c.g.xadj[u + 1] - c.g.xadj[u]), kLaneMaxDeg);
+        }
       }
       const unsigned maxdeg = __reduce_max_sync(kFull, (unsigned)deg);
       if (maxdeg <= 16) lane_batch<COMP, MODE, W, 16>(c, has, u, deg, col, wcol, cnt, mb, nmv);
@@ -1164,9 +1319,13 @@ constexpr int kBucketChunks = kBucketSpan / 32;
 // Pass 0 hashes every vertex once and keeps its sub-round (+1; 0: not in the
 // lane tier) in sub[]; pass 1 reads it back. Lanes of a 32-vertex chunk with
 // the same sub-round are grouped with one match instruction.
+// With offsets (compressed graphs), pass 1 also stores each listed vertex's
+// record start << 8 | record length in rec (lane-tier records are <= 65 bytes).
 __global__ void __launch_bounds__(256) k_bucket(const uint8_t *tier, int64_t n, uint64_t rk_in,
                                                 const uint64_t *rk_dev, int32_t S, bool fill,
-                                                int64_t *cnt, int32_t *bucket, uint8_t *sub_byte) {
+                                                int64_t *cnt, int32_t *bucket, uint8_t *sub_byte,
+                                                const uint32_t *o32, const uint64_t *o64,
+                                                uint64_t *rec) {
   __shared__ int32_t chunk_cnt[kBucketChunks][32];  // [chunk][sub-round], S <= 32
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const int64_t nblocks = gridDim.x;
@@ -1215,9 +1374,16 @@ __global__ void __launch_bounds__(256) k_bucket(const uint8_t *tier, int64_t n, 
     const int chunk = w + 8 * q;
     const int32_t sub = sub_of[q];
     const unsigned peers = __match_any_sync(kFull, sub);
-    if (sub >= 0)
-      bucket[cnt[(int64_t)sub * nblocks + blockIdx.x] + chunk_cnt[chunk][sub] +
-             __popc(peers & lanemask_lt())] = (int32_t)(lo + 32 * chunk + lane);
+    if (sub >= 0) {
+      const int64_t pos = cnt[(int64_t)sub * nblocks + blockIdx.x] + chunk_cnt[chunk][sub] +
+                          __popc(peers & lanemask_lt());
+      const int64_t u = lo + 32 * chunk + lane;
+      bucket[pos] = (int32_t)u;
+      if (rec) {
+        const uint64_t b = o32 ? o32[u] : o64[u], e = o32 ? o32[u + 1] : o64[u + 1];
+        rec[pos] = b << 8 | (e - b);
+      }
+    }
   }
 }
 
@@ -1232,11 +1398,16 @@ void lp_bucket(tp_graph *g, LpWork &w, uint64_t rk, int32_t S, const tp_params &
   if (!w.bucket.get()) w.bucket.alloc(std::max<int64_t>(w.n, 1), stream);
   if (!w.bucket_sub.get()) w.bucket_sub.alloc(std::max<int64_t>(w.n, 1), stream);
   if ((int64_t)w.bucket_off.n < S * nblocks + 1) w.bucket_off.alloc(S * nblocks + 1, stream);
+  const bool zrec = g->compressed != 0;
+  if (zrec && !w.bucket_rec.get()) w.bucket_rec.alloc(std::max<int64_t>(w.n, 1), stream);
+  const uint32_t *o32 = zrec && !g->off_is64 ? g->off32.get() : nullptr;
+  const uint64_t *o64 = zrec && g->off_is64 ? g->off64.get() : nullptr;
+  uint64_t *rec = zrec ? w.bucket_rec.get() : nullptr;
   launch(k_bucket, (unsigned)nblocks, 256, 0, stream, g->tiers.tier.get(), g->n, rk, rk_dev, S,
-         false, w.bucket_off.get(), w.bucket.get(), w.bucket_sub.get());
+         false, w.bucket_off.get(), w.bucket.get(), w.bucket_sub.get(), o32, o64, rec);
   exclusive_scan_i64(w.bucket_off.get(), w.bucket_off.get(), S * nblocks, stream);
   launch(k_bucket, (unsigned)nblocks, 256, 0, stream, g->tiers.tier.get(), g->n, rk, rk_dev, S,
-         true, w.bucket_off.get(), w.bucket.get(), w.bucket_sub.get());
+         true, w.bucket_off.get(), w.bucket.get(), w.bucket_sub.get(), o32, o64, rec);
   TP_LAUNCH_CHECK();
   w.bucket_S = S;
   w.bucket_nblocks = nblocks;
@@ -1344,6 +1515,7 @@ void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t
     c.bucket = w.bucket.get();
     c.bucket_off = w.bucket_off.get();
     c.bucket_nb = w.bucket_nblocks;
+    c.bucket_rec = g->compressed ? w.bucket_rec.get() : nullptr;
   }
   rate_tiers<M_LP>(g, c, p, stream);
   prof_begin(PF_APPROVE, stream);
@@ -1382,6 +1554,7 @@ bool lp_rounds_graph(tp_graph *g, const LpState &st, LpWork &w, uint64_t seed, u
   if (!w.bucket.get()) w.bucket.alloc(std::max<int64_t>(w.n, 1), stream);
   if (!w.bucket_sub.get()) w.bucket_sub.alloc(std::max<int64_t>(w.n, 1), stream);
   if ((int64_t)w.bucket_off.n < S * nblocks + 1) w.bucket_off.alloc(S * nblocks + 1, stream);
+  if (g->compressed && !w.bucket_rec.get()) w.bucket_rec.alloc(std::max<int64_t>(w.n, 1), stream);
   Buf<int32_t> d_r(1, stream);
   Buf<uint64_t> d_rk(1, stream);
   TP_CUDA(cudaMemsetAsync(d_r.get(), 0, sizeof(int32_t), stream));

@@ -365,6 +365,7 @@ struct LpWork {
   // lane-tier vertices of the current round grouped by sub-round (A3)
   Buf<int32_t> bucket;       // n
   Buf<uint8_t> bucket_sub;   // n: sub-round + 1 of every vertex this round (0: not listed)
+  Buf<uint64_t> bucket_rec;  // n: record start << 8 | length per listed vertex (compressed)
   Buf<int64_t> bucket_off;   // S * nblocks + 1 offsets (sub-round major)
   int64_t bucket_nblocks = 0;
   int32_t bucket_S = 0;      // S of the current buckets (0: none)
