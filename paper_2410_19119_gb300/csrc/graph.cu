@@ -246,7 +246,8 @@ namespace {
 __global__ void k_classify(const int64_t *deg, int64_t n, int32_t lane_max, int32_t small_max,
                            int32_t mid_max, const uint32_t *off32, const uint64_t *off64,
                            uint8_t *tier, int32_t *flag_small, int32_t *flag_mid,
-                           int32_t *flag_big, int32_t *flag_huge, unsigned long long *stats) {
+                           int32_t *flag_big, int32_t *flag_big2, int32_t *flag_huge,
+                           unsigned long long *stats) {
   int64_t e[5] = {0, 0, 0, 0, 0}, c[5] = {0, 0, 0, 0, 0};
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
        u += (int64_t)gridDim.x * blockDim.x) {
@@ -264,7 +265,8 @@ __global__ void k_classify(const int64_t *deg, int64_t n, int32_t lane_max, int3
     tier[u] = t;
     flag_small[u] = t == TIER_SMALL;
     flag_mid[u] = t == TIER_MID;
-    flag_big[u] = t == TIER_BIG;
+    flag_big[u] = t == TIER_BIG && d <= kBigSplit;
+    flag_big2[u] = t == TIER_BIG && d > kBigSplit;
     flag_huge[u] = t == TIER_HUGE;
     e[t] += d;
     c[t] += 1;
@@ -294,6 +296,13 @@ __global__ void k_table_caps(const int32_t *list, int64_t cnt, const int64_t *de
     slots[i] = (int64_t)1 << lc;
     if (chunks) chunks[i] = (d + kChunkSize - 1) / kChunkSize;
   }
+}
+
+// Segments per huge table (tables above kSegLog slots are cut into segments).
+__global__ void k_table_segs(const int32_t *logcap, int64_t cnt, int64_t *segs) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+       i += (int64_t)gridDim.x * blockDim.x)
+    segs[i] = logcap[i] > kSegLog ? (int64_t)1 << (logcap[i] - kSegLog) : 1;
 }
 
 __global__ void k_fill_table(int32_t *keys, int64_t *vals, int64_t n) {
@@ -329,13 +338,13 @@ void build_tiers(tp_graph *g, const tp_params &p, cudaStream_t s) {
   }
   Buf<int64_t> deg(n, s);
   compute_degrees(g, deg.get(), s);
-  Buf<int32_t> fs(n, s), fm(n, s), fb(n, s), fh(n, s);
+  Buf<int32_t> fs(n, s), fm(n, s), fb(n, s), fb2(n, s), fh(n, s);
   Buf<unsigned long long> te(10, s);
   TP_CUDA(cudaMemsetAsync(te.get(), 0, 10 * sizeof(unsigned long long), s));
   const uint32_t *o32 = g->compressed && !g->off_is64 ? g->off32.get() : nullptr;
   const uint64_t *o64 = g->compressed && g->off_is64 ? g->off64.get() : nullptr;
   launch(k_classify, grid_for(n, 256), 256, 0, s, deg.get(), n, lane_max, small_max, mid_max,
-         o32, o64, T.tier.get(), fs.get(), fm.get(), fb.get(), fh.get(), te.get());
+         o32, o64, T.tier.get(), fs.get(), fm.get(), fb.get(), fb2.get(), fh.get(), te.get());
   TP_LAUNCH_CHECK();
   unsigned long long hte[10];
   TP_CUDA(cudaMemcpyAsync(hte, te.get(), sizeof(hte), cudaMemcpyDeviceToHost, s));
@@ -354,8 +363,9 @@ void build_tiers(tp_graph *g, const tp_params &p, cudaStream_t s) {
   make_list(fs, T.small, T.n_small);
   make_list(fm, T.mid, T.n_mid);
   make_list(fb, T.big, T.n_big);
+  make_list(fb2, T.big2, T.n_big2);
   make_list(fh, T.huge, T.n_huge);
-  // global rating tables for the big and huge tiers
+  // global rating tables for the huge tier (the big tier rates in shared memory)
   auto tables = [&](Buf<int32_t> &list, int64_t cnt, Buf<int64_t> &toff, Buf<int32_t> &tcap,
                     int64_t &slots, Buf<int64_t> *chunk_start, int64_t *nchunks) {
     toff.alloc(cnt + 1, s);
@@ -377,10 +387,18 @@ void build_tiers(tp_graph *g, const tp_params &p, cudaStream_t s) {
       *nchunks = read_scalar(chunk_start->get() + cnt, s);
     }
   };
-  tables(T.big, T.n_big, T.big_toff, T.big_tcap, T.big_slots, nullptr, nullptr);
   tables(T.huge, T.n_huge, T.huge_toff, T.huge_tcap, T.huge_slots, &T.huge_chunk_start,
          &T.n_huge_chunks);
-  int64_t total = T.big_slots + T.huge_slots;
+  if (T.n_huge) {
+    T.huge_seg_start.alloc(T.n_huge + 1, s);
+    launch(k_table_segs, grid_for(T.n_huge, 256), 256, 0, s, T.huge_tcap.get(), T.n_huge,
+           T.huge_seg_start.get());
+    TP_LAUNCH_CHECK();
+    exclusive_scan_i64(T.huge_seg_start.get(), T.huge_seg_start.get(), T.n_huge, s);
+    T.n_huge_segs = read_scalar(T.huge_seg_start.get() + T.n_huge, s);
+    T.huge_seg_best.alloc((size_t)T.n_huge_segs * kSegBestBytes, s);
+  }
+  int64_t total = T.huge_slots;
   if (total) {
     T.tkeys.alloc(total, s);
     T.tvals.alloc(total, s);

@@ -23,6 +23,7 @@
 // per target runs a weighted radix select over the key (gain desc, vertex
 // asc) and approves exactly the longest fitting prefix.
 #include <algorithm>
+#include <type_traits>
 #include <mutex>
 
 #include "decode.cuh"
@@ -37,8 +38,6 @@ constexpr int kSmallLog = 7;   // 128 slots
 constexpr int kMidLog = 10;    // 1024 slots: mid tier, degree <= 512
 constexpr int kHugeLog = 11;   // 2048 slots: one 1000-neighbour chunk of a hub
 constexpr int kMidWarps = 4;
-constexpr int kHugeWarps = 4;  // warps per block in the chunk kernel
-constexpr int kDecideThreads = 256;
 
 struct RateCtx {
   GView g;
@@ -71,6 +70,8 @@ struct RateCtx {
   int64_t tbase;  // slot offset of this tier's tables inside tkeys/tvals
   const int64_t *chunk_start;
   int64_t n_chunks;
+  const int64_t *seg_start;  // huge tables: prefix of segment counts
+  int64_t n_segs;
   // lane tier in LP mode: this round's buckets (null: hash every vertex);
   // sub-round s holds bucket[bucket_off[s * nb] .. bucket_off[(s + 1) * nb])
   const int32_t *bucket;
@@ -218,47 +219,44 @@ __device__ void rate_vertex_warp(const RateCtx &c, int64_t u, int32_t *keys, int
   const uint64_t hv = tie_key<MODE>(c, u);
   Best b;
   b.init();
-  bool fast = false;
-  if (allow_fast && !c.g.ew) {
-    if (!COMP) {
-      fast = c.g.xadj[u + 1] - c.g.xadj[u] <= 32;
-    } else {
-      ZipNbr z = zip_nbr(c.g, u);
-      fast = z.nchunks == 1 && z.end - z.data <= 32;
+  // every lane adds its neighbour's label to the table (shared-memory
+  // atomics are far cheaper than grouping equal labels across lanes first)
+  warp_neighbours<COMP>(c.g, u, -1, [&](bool has, int32_t v, int64_t w) {
+    if (has) tbl_add(keys, vals, logcap, c.label[v], w, c.g.err);
+  });
+  __syncwarp();
+  __threadfence_block();
+  const int cap = 1 << logcap;
+  // the best label ignoring the cap, and the own rating
+  for (int i = lane; i < cap; i += 32) {
+    const int32_t x = keys[i];
+    if (x < 0) continue;
+    if (x == own) {
+      b.rown = vals[i];
+      continue;
     }
-  }
-  if (fast) {
-    // one batch: group equal labels across lanes, no table
-    warp_neighbours<COMP>(c.g, u, -1, [&](bool has, int32_t v, int64_t) {
-      int32_t x = has ? c.label[v] : -1;
-      unsigned peers = __match_any_sync(kFull, x);
-      if (has && (peers & lanemask_lt()) == 0) consider<MODE>(c, b, x, __popc(peers), own, cu, hv);
-    });
-  } else {
-    warp_neighbours<COMP>(c.g, u, -1, [&](bool has, int32_t v, int64_t w) {
-      int32_t x = has ? c.label[v] : -1;
-      if (!c.g.ew) {
-        unsigned peers = __match_any_sync(kFull, x);
-        if (has && (peers & lanemask_lt()) == 0)
-          tbl_add(keys, vals, logcap, x, __popc(peers), c.g.err);
-      } else if (has) {
-        tbl_add(keys, vals, logcap, x, w, c.g.err);
-      }
-    });
-    __syncwarp();
-    __threadfence_block();
-    const int cap = 1 << logcap;
-    for (int i = lane; i < cap; i += 32) {
-      int32_t x = keys[i];
-      if (x >= 0) {
-        consider<MODE>(c, b, x, vals[i], own, cu, hv);
-        keys[i] = -1;
-        vals[i] = 0;
-      }
-    }
-    __syncwarp();
+    const uint32_t t = MODE == M_REBAL ? 0u : tie_hash(hv, x);
+    if (better(vals[i], t, x, b.r, b.t, b.x)) b.r = vals[i], b.t = t, b.x = x;
   }
   warp_reduce_best(b);
+  // the winner is full: the best admissible label instead (for a move it
+  // must also improve on the own rating)
+  if (MODE != M_FAV && b.x != INT32_MAX && c.lw[b.x] + cu > c.cap) {
+    const int64_t rown = b.rown;
+    b.init();
+    for (int i = lane; i < cap; i += 32) {
+      const int32_t x = keys[i];
+      if (x < 0 || x == own) continue;
+      const int64_t R = vals[i];
+      if (MODE == M_LP && R <= rown) continue;
+      const uint32_t t = MODE == M_REBAL ? 0u : tie_hash(hv, x);
+      if (better(R, t, x, b.r, b.t, b.x) && c.lw[x] + cu <= c.cap) b.r = R, b.t = t, b.x = x;
+    }
+    warp_reduce_best(b);
+    b.rown = rown;
+  }
+  for (int i = lane; i < cap; i += 32) keys[i] = -1, vals[i] = 0;
+  __syncwarp();
   finalize_warp<MODE>(c, b, u, cu, mb);
 }
 
@@ -869,84 +867,402 @@ __global__ void k_rate_list(RateCtx c) {
   if (MODE == M_LP) flush_movers(c, mb);
 }
 
-// Huge tier, phase 1: one warp per (vertex, chunk) aggregates the chunk in a
-// shared table and flushes it into the vertex's global table.
-template <bool COMP, int MODE>
-__global__ void k_rate_huge_chunks(RateCtx c) {
+// ---------------------------------------------------------------- big tier
+// One block per listed vertex: its ratings are summed in a shared-memory
+// hash table of 2^logc >= 1.5 deg slots (keys, then 32-bit counts for unit
+// weights or 64-bit sums), so no rating touches global memory. A compressed
+// neighbourhood (one chunk below the chunking threshold) is decoded by the
+// whole block: every thread takes a slice of the record's bytes, assembles
+// the values whose last byte lies in its slice (reading back into the
+// previous slice for the first bytes of a value), and two block scans give
+// each value its index and the sum of the gaps before it.
+constexpr int kBlockThreads = 256;
+constexpr int kBlockSmallLog = 13;  // 8192 slots: degrees up to kBigSplit = 4096
+constexpr int kBlockBigLog = 14;    // 16384 slots: degrees up to 10000
+// Record staging and decoded values for a compressed vertex of degree <= dmax:
+// at most 5 bytes per neighbour (+ alignment slack), 4 bytes per value.
+__host__ __device__ constexpr size_t block_stage_bytes(int64_t dmax) {
+  return ((size_t)(5 * dmax + 64) + 15) & ~(size_t)15;
+}
+__host__ __device__ constexpr size_t block_vbuf_bytes(int64_t dmax) { return (size_t)4 * dmax; }
+__host__ __device__ constexpr int64_t block_max_deg(int lg) {
+  return lg == kBlockSmallLog ? kBigSplit : kChunkThreshold;
+}
+
+// Block-wide exclusive sum of one int64 per thread; returns this thread's
+// prefix and sets total. red holds kBlockThreads / 32 + 1 entries.
+__device__ __forceinline__ int64_t block_excl_sum(int64_t v, int64_t *red, int64_t &total) {
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  const int64_t inc = warp_incl_scan(v);
+  if (lane == 31) red[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const int64_t x = lane < kBlockThreads / 32 ? red[lane] : 0;
+    const int64_t xi = warp_incl_scan(x);
+    if (lane < kBlockThreads / 32) red[lane] = xi - x;
+    if (lane == kBlockThreads / 32 - 1) red[kBlockThreads / 32] = xi;
+  }
+  __syncthreads();
+  const int64_t r = red[w] + inc - v;
+  total = red[kBlockThreads / 32];
+  __syncthreads();
+  return r;
+}
+
+// Block-wide exclusive sum of one uint32 per thread (same contract as
+// block_excl_sum).
+__device__ __forceinline__ uint32_t block_excl_sum32(uint32_t v, int64_t *red, uint32_t &total) {
+  int64_t t;
+  const int64_t r = block_excl_sum((int64_t)v, red, t);
+  total = (uint32_t)t;
+  return (uint32_t)r;
+}
+
+// Decodes one chunk [cb, ce) of u's neighbourhood (count values: the first
+// a signed offset from u, then gaps) with the whole block and calls f(v)
+// for every neighbour. The chunk's bytes are copied into shared memory
+// (stage: at least ce - cb + 32 bytes, 16-byte aligned) with 16-byte loads;
+// then (1) every thread counts the value ends (bytes without the
+// continuation bit) in its slice of the bytes, (2) a block scan gives each
+// thread the index of its first value and every thread writes the values
+// ending in its slice to vbuf (count entries), each assembled without
+// branches from its last byte and up to four preceding continuation bytes,
+// (3) a block scan over the values turns them into neighbour ids, and (4)
+// f is called for every id.
+template <class F>
+__device__ __forceinline__ void block_decode_range(const GView &g, int64_t u, uint64_t cb,
+                                                   uint64_t ce, int64_t count, uint8_t *stage,
+                                                   uint32_t *vbuf, int64_t *red, F &&f) {
+  const uint64_t ws = cb & ~(uint64_t)15;
+  const int off = (int)(cb - ws), L = (int)(ce - cb);
+  const int ngroups = (off + L + 15) >> 4;
+  const uint4 *src = reinterpret_cast<const uint4 *>(g.bytes + ws);
+  for (int k = threadIdx.x; k < ngroups; k += kBlockThreads)
+    reinterpret_cast<uint4 *>(stage)[k] = __ldcs(src + k);
+  __syncthreads();
+  const uint8_t *by = stage + off;
+  const int K = (L + kBlockThreads - 1) / kBlockThreads;
+  const int lo = min((int)threadIdx.x * K, L), hi = min((int)(threadIdx.x + 1) * K, L);
+  uint32_t ends = 0;
+  for (int p = lo; p < hi; ++p) ends += !(by[p] & 0x80u);
+  uint32_t nval;
+  uint32_t idx = block_excl_sum32(ends, red, nval);
+  const int cnt = (int)min((int64_t)nval, count);
+  if (threadIdx.x == 0 && (int64_t)nval != count) latch_error(g.err, TP_ERR_CORRUPT);
+  // the four bytes before the slice (continuation bytes of a value ending in it)
+  uint32_t win = 0;  // byte p-1 in bits 0..7, p-2 in 8..15, ...
+#pragma unroll
+  for (int d = 4; d >= 1; --d) win = (win << 8) | (lo - d >= 0 ? by[lo - d] : 0u);
+  for (int p = lo; p < hi; ++p) {
+    const uint32_t b0 = by[p];
+    // continuation bytes directly before p: k = 0..4
+    const uint32_t stop = ~win & 0x80808080u;
+    const int k = stop ? (__ffs(stop) - 8) >> 3 : 4;
+    // payloads of bytes p-1 .. p-4 packed 7 bits apart, p-1 lowest
+    uint32_t pk = (win & 0x7fu) | ((win >> 1) & 0x3f80u) | ((win >> 2) & 0x1fc000u) |
+                  ((win >> 3) & 0xfe00000u);
+    // value = bytes p-k .. p, earliest byte lowest: reverse the k packed payloads
+    uint32_t v = b0 & 0x7fu;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const bool take = d < k;
+      v = take ? (v << 7) | (pk & 0x7fu) : v;
+      pk >>= 7;
+    }
+    if (!(b0 & 0x80u)) {
+      if ((int)idx < cnt) vbuf[idx] = v;
+      ++idx;
+    }
+    win = (win << 8) | b0;
+  }
+  __syncthreads();
+  // ids: id_0 = u + signed offset, id_i = id_(i-1) + gap_i
+  const int P = (cnt + kBlockThreads - 1) / kBlockThreads;
+  const int a0 = min((int)threadIdx.x * P, cnt), a1 = min((int)(threadIdx.x + 1) * P, cnt);
+  uint32_t part = 0;
+  for (int i = max(a0, 1); i < a1; ++i) part += vbuf[i];
+  uint32_t gtot;
+  uint32_t run = block_excl_sum32(part, red, gtot);
+  const uint32_t c0 = vbuf[0];
+  const int64_t id0 = (c0 & 1u) ? u - (int64_t)(c0 >> 1) : u + (int64_t)(c0 >> 1);
+  __syncthreads();  // vbuf[0] read by every thread before it is overwritten
+  const int64_t nmax = g.n - 1;
+  for (int i = a0; i < a1; ++i) {
+    if (i > 0) run += vbuf[i];
+    // streams are validated on creation; the clamp only keeps a corrupted
+    // one from reading out of bounds
+    vbuf[i] = (uint32_t)min(max(id0 + (int64_t)run, (int64_t)0), nmax);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < cnt; i += kBlockThreads) f((int32_t)vbuf[i]);
+  __syncthreads();  // stage and vbuf are reused
+}
+
+template <class V>
+__device__ __forceinline__ void blk_add(int32_t *keys, V *vals, int logc, int32_t x, V w,
+                                        int32_t *err) {
+  const uint32_t mask = (1u << logc) - 1u;
+  uint32_t h = slot_of(x, logc);
+  for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
+    int32_t k = keys[h];
+    if (k == -1) {
+      const int32_t prev = atomicCAS(&keys[h], -1, x);
+      k = prev == -1 ? x : prev;
+    }
+    if (k == x) {
+      atomicAdd(&vals[h], w);
+      return;
+    }
+  }
+  latch_error(err, TP_ERR_CORRUPT);
+}
+
+// Block-wide best (rating order) and own rating; the result is in every thread.
+__device__ __forceinline__ void block_reduce_best(Best &b, Best *wb) {
+  warp_reduce_best(b);
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  if (lane == 0) wb[w] = b;
+  __syncthreads();
+  b = lane < kBlockThreads / 32 ? wb[lane] : Best{-1, 0xffffffffu, INT32_MAX, 0};
+  warp_reduce_best(b);
+  __syncthreads();
+}
+
+template <bool COMP, int MODE, bool WT>
+__global__ void __launch_bounds__(kBlockThreads) k_rate_block(RateCtx c, int maxlog) {
+  using V = typename std::conditional<WT, unsigned long long, uint32_t>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  WarpSmem<kHugeLog> &ws = reinterpret_cast<WarpSmem<kHugeLog> *>(smem_raw)[threadIdx.x >> 5];
-  init_table(ws);
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int lane = lane_id();
-  for (int64_t item = gw; item < c.n_chunks; item += nw) {
-    // vertex index: last i with chunk_start[i] <= item
-    int64_t lo = 0, hi = c.list_n - 1;
-    while (lo < hi) {
-      int64_t mid = (lo + hi + 1) / 2;
-      if (c.chunk_start[mid] <= item) lo = mid;
-      else hi = mid - 1;
-    }
-    int64_t i = lo, j = item - c.chunk_start[i];
-    int64_t u = c.list[i];
-    if (!active<MODE>(c, u)) continue;
-    warp_neighbours<COMP>(c.g, u, j, [&](bool has, int32_t v, int64_t w) {
-      int32_t x = has ? c.label[v] : -1;
-      if (!c.g.ew) {
-        unsigned peers = __match_any_sync(kFull, x);
-        if (has && (peers & lanemask_lt()) == 0)
-          tbl_add(ws.keys, ws.vals, kHugeLog, x, __popc(peers), c.g.err);
-      } else if (has) {
-        tbl_add(ws.keys, ws.vals, kHugeLog, x, w, c.g.err);
-      }
-    });
-    __syncwarp();
-    __threadfence_block();
-    int64_t off = c.tbase + c.toff[i];
-    int lc = c.tcap[i];
-    for (int s = lane; s < (1 << kHugeLog); s += 32) {
-      int32_t x = ws.keys[s];
-      if (x >= 0) {
-        tbl_add(c.tkeys + off, c.tvals + off, lc, x, ws.vals[s], c.g.err);
-        ws.keys[s] = -1;
-        ws.vals[s] = 0;
+  int32_t *keys = reinterpret_cast<int32_t *>(smem_raw);
+  V *vals = reinterpret_cast<V *>(smem_raw + sizeof(int32_t) * ((size_t)1 << maxlog));
+  // compressed: the record's bytes (at most 5 per neighbour, + alignment),
+  // then its decoded values
+  uint8_t *stage = reinterpret_cast<uint8_t *>(vals + ((size_t)1 << maxlog));
+  uint32_t *vbuf = reinterpret_cast<uint32_t *>(stage + block_stage_bytes(block_max_deg(maxlog)));
+  __shared__ int64_t red[kBlockThreads / 32 + 1];
+  __shared__ Best wb[kBlockThreads / 32];
+  __shared__ int32_t mu[32], mt[32], mo[32];
+  __shared__ int64_t mg[32];
+  const int tid = threadIdx.x;
+  for (int64_t i = blockIdx.x; i < c.list_n; i += gridDim.x) {
+    const int64_t u = c.list[i];
+    if (!active<MODE>(c, u)) continue;  // uniform over the block
+    const int64_t d = COMP ? zip_nbr(c.g, u).deg : c.g.xadj[u + 1] - c.g.xadj[u];
+    int logc = 5;
+    while (logc < maxlog && ((int64_t)1 << logc) < d + d / 2) ++logc;
+    const int cap = 1 << logc;
+    for (int k = tid; k < cap; k += kBlockThreads) keys[k] = -1, vals[k] = 0;
+    __syncthreads();
+    if (COMP) {
+      const ZipNbr z = zip_nbr(c.g, u);  // one chunk: the big tier is below the chunking threshold
+      block_decode_range(c.g, u, z.data, z.end, z.deg, stage, vbuf, red, [&](int32_t v) {
+        blk_add<V>(keys, vals, logc, c.label[v], (V)1, c.g.err);
+      });
+    } else {
+      const int64_t b = c.g.xadj[u];
+      for (int64_t e = tid; e < d; e += kBlockThreads) {
+        const int32_t v = __ldcs(c.g.adj + b + e);
+        blk_add<V>(keys, vals, logc, c.label[v], (V)(c.g.ew ? __ldcs(c.g.ew + b + e) : 1),
+                   c.g.err);
       }
     }
-    __syncwarp();
+    __syncthreads();
+    // best label ignoring the cap, and the own rating
+    const int32_t own = c.label[u];
+    const int64_t cu = node_w(c.g, u);
+    const uint64_t hv = tie_key<MODE>(c, u);
+    Best b;
+    b.init();
+    for (int k = tid; k < cap; k += kBlockThreads) {
+      const int32_t x = keys[k];
+      if (x < 0) continue;
+      const int64_t R = (int64_t)vals[k];
+      if (x == own) {
+        b.rown = R;
+        continue;
+      }
+      const uint32_t t = MODE == M_REBAL ? 0u : tie_hash(hv, x);
+      if (better(R, t, x, b.r, b.t, b.x)) b.r = R, b.t = t, b.x = x;
+    }
+    block_reduce_best(b, wb);
+    // the winner is full: the best admissible label instead (it must improve
+    // on the own rating to matter)
+    if (MODE != M_FAV && b.x != INT32_MAX && c.lw[b.x] + cu > c.cap) {
+      const int64_t rown = b.rown;
+      b.init();
+      for (int k = tid; k < cap; k += kBlockThreads) {
+        const int32_t x = keys[k];
+        if (x < 0 || x == own) continue;
+        const int64_t R = (int64_t)vals[k];
+        if (MODE == M_LP && R <= rown) continue;
+        const uint32_t t = MODE == M_REBAL ? 0u : tie_hash(hv, x);
+        if (better(R, t, x, b.r, b.t, b.x) && c.lw[x] + cu <= c.cap) b.r = R, b.t = t, b.x = x;
+      }
+      block_reduce_best(b, wb);
+      b.rown = rown;
+    }
+    if (tid < 32) {
+      MoverBuf mb{mu, mt, mo, mg, 0};
+      finalize_warp<MODE>(c, b, u, cu, &mb);
+      if (MODE == M_LP) flush_movers(c, mb);
+    }
+    __syncthreads();
+  }
+}
+
+// Huge tier, phase 1: one block per (vertex, chunk of 1000 neighbours; the
+// compressed format's independently decodable chunks) sums the chunk's
+// ratings in a shared-memory table and adds them into the vertex's global
+// table (the paper's rating maps as flush buffers against contention).
+constexpr int kHugeStage = (5 * kChunkSize + 64 + 15) & ~15;  // one chunk's bytes + alignment
+template <bool COMP, int MODE>
+__global__ void __launch_bounds__(kBlockThreads) k_rate_huge_chunks(RateCtx c) {
+  __shared__ int32_t keys[1 << kHugeLog];
+  __shared__ unsigned long long vals[1 << kHugeLog];
+  __shared__ __align__(16) uint8_t stage[COMP ? kHugeStage : 16];
+  __shared__ uint32_t vbuf[COMP ? kChunkSize : 1];
+  __shared__ int64_t red[kBlockThreads / 32 + 1];
+  __shared__ int64_t s_vi;
+  const int tid = threadIdx.x;
+  for (int k = tid; k < (1 << kHugeLog); k += kBlockThreads) keys[k] = -1, vals[k] = 0;
+  __syncthreads();
+  for (int64_t item = blockIdx.x; item < c.n_chunks; item += gridDim.x) {
+    if (tid == 0) {  // vertex index: last i with chunk_start[i] <= item
+      int64_t lo = 0, hi = c.list_n - 1;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) / 2;
+        if (c.chunk_start[mid] <= item) lo = mid;
+        else hi = mid - 1;
+      }
+      s_vi = lo;
+    }
+    __syncthreads();
+    const int64_t i = s_vi, j = item - c.chunk_start[i];
+    const int64_t u = c.list[i];
+    __syncthreads();  // s_vi is rewritten by the next item
+    if (!active<MODE>(c, u)) continue;  // uniform over the block
+    if (COMP) {
+      const ZipNbr z = zip_nbr(c.g, u);
+      uint64_t cb, ce;
+      int64_t cnt;
+      zip_chunk(c.g, z, j, cb, ce, cnt);
+      block_decode_range(c.g, u, cb, ce, cnt, stage, vbuf, red, [&](int32_t v) {
+        blk_add<unsigned long long>(keys, vals, kHugeLog, c.label[v], 1ull, c.g.err);
+      });
+    } else {
+      const int64_t b = c.g.xadj[u] + j * kChunkSize;
+      const int64_t e = min(b + kChunkSize, c.g.xadj[u + 1]);
+      for (int64_t q = b + tid; q < e; q += kBlockThreads) {
+        const int32_t v = __ldcs(c.g.adj + q);
+        blk_add<unsigned long long>(keys, vals, kHugeLog, c.label[v],
+                                    (unsigned long long)(c.g.ew ? __ldcs(c.g.ew + q) : 1), c.g.err);
+      }
+    }
+    __syncthreads();
+    int32_t *tk = c.tkeys + c.tbase + c.toff[i];
+    int64_t *tv = c.tvals + c.tbase + c.toff[i];
+    const int lc = c.tcap[i];
+    for (int k = tid; k < (1 << kHugeLog); k += kBlockThreads) {
+      const int32_t x = keys[k];
+      if (x < 0) continue;
+      tbl_add(tk, tv, lc, x, (int64_t)vals[k], c.g.err);
+      keys[k] = -1;
+      vals[k] = 0;
+    }
+    __syncthreads();
   }
 }
 
 // Huge tier, phase 2: one block per vertex scans its global table.
+static_assert(sizeof(Best) == kSegBestBytes, "segment results are Best records");
+
+// Huge tier, phase 2: every (vertex, segment of 4096 table slots) is scanned
+// by its own block for the best label ignoring the cap and the own rating.
 template <int MODE>
-__global__ void k_rate_huge_decide(RateCtx c) {
-  __shared__ Best wb[kDecideThreads / 32];
-  const int lane = lane_id(), w = threadIdx.x >> 5;
+__global__ void __launch_bounds__(kBlockThreads) k_rate_huge_scan(RateCtx c, Best *seg_best) {
+  __shared__ Best wb[kBlockThreads / 32];
+  __shared__ int64_t s_vi;
+  for (int64_t item = blockIdx.x; item < c.n_segs; item += gridDim.x) {
+    if (threadIdx.x == 0) {  // vertex index: last i with seg_start[i] <= item
+      int64_t lo = 0, hi = c.list_n - 1;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) / 2;
+        if (c.seg_start[mid] <= item) lo = mid;
+        else hi = mid - 1;
+      }
+      s_vi = lo;
+    }
+    __syncthreads();
+    const int64_t i = s_vi;
+    __syncthreads();
+    const int64_t u = c.list[i];
+    if (!active<MODE>(c, u)) continue;
+    const int32_t own = c.label[u];
+    const uint64_t hv = tie_key<MODE>(c, u);
+    const int64_t cap = (int64_t)1 << c.tcap[i];
+    const int64_t s0 = (item - c.seg_start[i]) << kSegLog;
+    const int64_t s1 = min(s0 + ((int64_t)1 << kSegLog), cap);
+    const int32_t *tk = c.tkeys + c.tbase + c.toff[i];
+    const int64_t *tv = c.tvals + c.tbase + c.toff[i];
+    Best b;
+    b.init();
+    for (int64_t sl = s0 + threadIdx.x; sl < s1; sl += kBlockThreads) {
+      const int32_t x = tk[sl];
+      if (x < 0) continue;
+      const int64_t R = tv[sl];
+      if (x == own) {
+        b.rown = R;
+        continue;
+      }
+      const uint32_t t = MODE == M_REBAL ? 0u : tie_hash(hv, x);
+      if (better(R, t, x, b.r, b.t, b.x)) b.r = R, b.t = t, b.x = x;
+    }
+    block_reduce_best(b, wb);
+    if (threadIdx.x == 0) seg_best[item] = b;
+  }
+}
+
+// Huge tier, phase 3: one block per vertex combines its segments; if the
+// winner is full it rescans the table for the best admissible label; then
+// it clears the table and acts on the decision.
+template <int MODE>
+__global__ void __launch_bounds__(kBlockThreads) k_rate_huge_decide(RateCtx c, const Best *seg_best) {
+  __shared__ Best wb[kBlockThreads / 32];
+  __shared__ int32_t mu[32], mt[32], mo[32];
+  __shared__ int64_t mg[32];
   for (int64_t i = blockIdx.x; i < c.list_n; i += gridDim.x) {
     int64_t u = c.list[i];
     if (!active<MODE>(c, u)) continue;
     const int32_t own = c.label[u];
     const int64_t cu = node_w(c.g, u);
     const uint64_t hv = tie_key<MODE>(c, u);
-    int64_t off = c.tbase + c.toff[i];
-    int64_t cap = (int64_t)1 << c.tcap[i];
+    int32_t *tk = c.tkeys + c.tbase + c.toff[i];
+    int64_t *tv = c.tvals + c.tbase + c.toff[i];
+    const int64_t cap = (int64_t)1 << c.tcap[i];
     Best b;
     b.init();
-    for (int64_t sl = threadIdx.x; sl < cap; sl += blockDim.x) {
-      int32_t x = c.tkeys[off + sl];
-      if (x >= 0) {
-        consider<MODE>(c, b, x, c.tvals[off + sl], own, cu, hv);
-        c.tkeys[off + sl] = -1;
-        c.tvals[off + sl] = 0;
-      }
+    for (int64_t q = c.seg_start[i] + threadIdx.x; q < c.seg_start[i + 1]; q += kBlockThreads) {
+      const Best o = seg_best[q];
+      if (better(o.r, o.t, o.x, b.r, b.t, b.x)) b.r = o.r, b.t = o.t, b.x = o.x;
+      b.rown = max(b.rown, o.rown);
     }
-    warp_reduce_best(b);
-    if (lane == 0) wb[w] = b;
-    __syncthreads();
-    if (w == 0) {
-      b = lane < (int)(blockDim.x >> 5) ? wb[lane] : Best{-1, 0xffffffffu, INT32_MAX, 0};
-      warp_reduce_best(b);
-      __shared__ int32_t mu[32], mt[32], mo[32];
-      __shared__ int64_t mg[32];
+    block_reduce_best(b, wb);
+    // the winner is full: the best admissible label instead
+    if (MODE != M_FAV && b.x != INT32_MAX && c.lw[b.x] + cu > c.cap) {
+      const int64_t rown = b.rown;
+      b.init();
+      for (int64_t sl = threadIdx.x; sl < cap; sl += kBlockThreads) {
+        const int32_t x = tk[sl];
+        if (x < 0 || x == own) continue;
+        const int64_t R = tv[sl];
+        if (MODE == M_LP && R <= rown) continue;
+        const uint32_t t = MODE == M_REBAL ? 0u : tie_hash(hv, x);
+        if (better(R, t, x, b.r, b.t, b.x) && c.lw[x] + cu <= c.cap) b.r = R, b.t = t, b.x = x;
+      }
+      block_reduce_best(b, wb);
+      b.rown = rown;
+    }
+    for (int64_t sl = threadIdx.x; sl < cap; sl += kBlockThreads) tk[sl] = -1, tv[sl] = 0;
+    if (threadIdx.x < 32) {
       MoverBuf mb{mu, mt, mo, mg, 0};
       finalize_warp<MODE>(c, b, u, cu, &mb);
       if (MODE == M_LP) flush_movers(c, mb);
@@ -1223,19 +1539,30 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
     TP_LAUNCH_CHECK();
     if (prof) prof_end(PF_RATE_MID, s, per_launch * tier_round_bytes(g, T.n_mid, T.edges[TIER_MID]));
   }
-  if (T.n_big > 0) {
+  if (T.n_big + T.n_big2 > 0) {
     if (prof) prof_begin(PF_RATE_BIG, s);
-    RateCtx m = c;
-    m.list = T.big.get();
-    m.list_n = T.n_big;
-    m.toff = T.big_toff.get();
-    m.tcap = T.big_tcap.get();
-    m.tbase = 0;
-    unsigned blocks = (unsigned)std::min<int64_t>((T.n_big + kMidWarps - 1) / kMidWarps, (int64_t)sms * 16);
-    if (comp) launch(k_rate_list<true, MODE, true>, blocks, 32 * kMidWarps, 0, s, m);
-    else launch(k_rate_list<false, MODE, true>, blocks, 32 * kMidWarps, 0, s, m);
-    TP_LAUNCH_CHECK();
-    if (prof) prof_end(PF_RATE_BIG, s, per_launch * tier_round_bytes(g, T.n_big, T.edges[TIER_BIG]));
+    const bool wt = !g->unit_ew;
+    auto run = [&](const int32_t *list, int64_t cnt, int maxlog) {
+      if (!cnt) return;
+      RateCtx m = c;
+      m.list = list;
+      m.list_n = cnt;
+      const size_t sm = ((size_t)1 << maxlog) * (sizeof(int32_t) + (wt ? 8 : 4)) +
+                        (comp ? block_stage_bytes(block_max_deg(maxlog)) +
+                                    block_vbuf_bytes(block_max_deg(maxlog))
+                              : 0);
+      const int per_sm = std::max(1, (int)((size_t)(228 * 1024) / (sm + 2048)));
+      const unsigned blocks = (unsigned)std::min<int64_t>(cnt, (int64_t)sms * per_sm);
+#define TP_BLK(CM, WW) launch(k_rate_block<CM, MODE, WW>, blocks, kBlockThreads, sm, s, m, maxlog)
+      if (comp) TP_BLK(true, false);
+      else if (wt) TP_BLK(false, true);
+      else TP_BLK(false, false);
+#undef TP_BLK
+      TP_LAUNCH_CHECK();
+    };
+    run(T.big.get(), T.n_big, kBlockSmallLog);
+    run(T.big2.get(), T.n_big2, kBlockBigLog);
+    if (prof) prof_end(PF_RATE_BIG, s, per_launch * tier_round_bytes(g, T.n_big + T.n_big2, T.edges[TIER_BIG]));
   }
   if (T.n_huge > 0) {
     if (prof) prof_begin(PF_RATE_HUGE, s);
@@ -1244,16 +1571,21 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
     m.list_n = T.n_huge;
     m.toff = T.huge_toff.get();
     m.tcap = T.huge_tcap.get();
-    m.tbase = T.big_slots;
+    m.tbase = 0;
     m.chunk_start = T.huge_chunk_start.get();
     m.n_chunks = T.n_huge_chunks;
-    size_t sm = sizeof(WarpSmem<kHugeLog>) * kHugeWarps;
-    unsigned blocks = (unsigned)std::min<int64_t>((T.n_huge_chunks + kHugeWarps - 1) / kHugeWarps, (int64_t)sms * 8);
-    if (comp) launch(k_rate_huge_chunks<true, MODE>, blocks, 32 * kHugeWarps, sm, s, m);
-    else launch(k_rate_huge_chunks<false, MODE>, blocks, 32 * kHugeWarps, sm, s, m);
+    const unsigned blocks = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>(T.n_huge_chunks, (int64_t)sms * 6));
+    if (comp) launch(k_rate_huge_chunks<true, MODE>, blocks, kBlockThreads, 0, s, m);
+    else launch(k_rate_huge_chunks<false, MODE>, blocks, kBlockThreads, 0, s, m);
     TP_LAUNCH_CHECK();
-    unsigned db = (unsigned)std::min<int64_t>(T.n_huge, (int64_t)sms * 4);
-    launch(k_rate_huge_decide<MODE>, db, kDecideThreads, 0, s, m);
+    m.seg_start = T.huge_seg_start.get();
+    m.n_segs = T.n_huge_segs;
+    Best *seg_best = reinterpret_cast<Best *>(T.huge_seg_best.get());
+    const unsigned sb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(T.n_huge_segs, (int64_t)sms * 8));
+    launch(k_rate_huge_scan<MODE>, sb, kBlockThreads, 0, s, m, seg_best);
+    const unsigned db = (unsigned)std::max<int64_t>(1, std::min<int64_t>(T.n_huge, (int64_t)sms * 4));
+    launch(k_rate_huge_decide<MODE>, db, kBlockThreads, 0, s, m, (const Best *)seg_best);
     TP_LAUNCH_CHECK();
     if (prof) prof_end(PF_RATE_HUGE, s, per_launch * tier_round_bytes(g, T.n_huge, T.edges[TIER_HUGE]));
   }
@@ -1267,18 +1599,30 @@ void set_smem_limits(K kernel, size_t bytes) {
 void configure_kernels_once() {
   size_t small16 = sizeof(WarpSmem<kSmallLog>) * 16;
   size_t mid = sizeof(WarpSmem<kMidLog>) * kMidWarps;
-  size_t huge = sizeof(WarpSmem<kHugeLog>) * kHugeWarps;
 #define TP_CFG_MODE(M)                                              \
   set_smem_limits(k_rate_small<true, M>, small16);                  \
   set_smem_limits(k_rate_small<false, M>, small16);                 \
   set_smem_limits(k_rate_list<true, M, false>, mid);                \
   set_smem_limits(k_rate_list<false, M, false>, mid);               \
-  set_smem_limits(k_rate_huge_chunks<true, M>, huge);               \
-  set_smem_limits(k_rate_huge_chunks<false, M>, huge);
+
   TP_CFG_MODE(M_LP)
   TP_CFG_MODE(M_FAV)
   TP_CFG_MODE(M_REBAL)
 #undef TP_CFG_MODE
+  // the largest dynamic shared memory: weighted CSR with 16384 slots, or
+  // compressed with 16384 slots and the record staging
+  const size_t blk = std::max(((size_t)1 << kBlockBigLog) * (sizeof(int32_t) + 8),
+                              ((size_t)1 << kBlockBigLog) * (sizeof(int32_t) + 4) +
+                                  block_stage_bytes(kChunkThreshold) +
+                                  block_vbuf_bytes(kChunkThreshold));
+#define TP_CFG_BLOCK(M)                                   \
+  set_smem_limits(k_rate_block<true, M, false>, blk);     \
+  set_smem_limits(k_rate_block<false, M, false>, blk);    \
+  set_smem_limits(k_rate_block<false, M, true>, blk);
+  TP_CFG_BLOCK(M_LP)
+  TP_CFG_BLOCK(M_FAV)
+  TP_CFG_BLOCK(M_REBAL)
+#undef TP_CFG_BLOCK
 }
 
 void configure_kernels() {

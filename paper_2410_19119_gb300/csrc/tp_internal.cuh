@@ -108,28 +108,38 @@ constexpr int kLaneMaxRecord = 65;
 constexpr int64_t kLaneMaxEdgeWeight = (int64_t)1 << 26;  // weighted lane tier: ratings fit 32 bits
 constexpr int64_t kChunkThreshold = 10000;  // compressed format: chunked above this degree
 constexpr int64_t kChunkSize = 1000;        // neighbours per chunk
+constexpr int kSegLog = 12;                 // huge tables are scanned 4096 slots per block
+constexpr int kSegBestBytes = 24;           // one segment's best label (rating, tie, label, own)
+constexpr int64_t kBigSplit = 4096;         // big tier: degrees up to here use 8192-slot tables
 
 struct TierCache {
   bool built = false;
   int32_t small_max = 0, mid_max = 0, lane_max = 0;
   int64_t count[5] = {0, 0, 0, 0, 0};  // vertices per tier
   Buf<uint8_t> tier;         // n
-  Buf<int32_t> small, mid, big, huge;  // vertex lists per tier (ascending)
-  int64_t n_small = 0, n_mid = 0, n_big = 0, n_huge = 0;
-  Buf<int64_t> big_toff, huge_toff;  // global table offsets (slots), size n_tier + 1
-  Buf<int32_t> big_tcap, huge_tcap;  // log2 of the table capacity per vertex
-  int64_t big_slots = 0, huge_slots = 0;
+  // vertex lists per tier (ascending); the big tier is listed in two parts,
+  // degree <= kBigSplit (shared tables of 8192 slots) and above (16384)
+  Buf<int32_t> small, mid, big, big2, huge;
+  int64_t n_small = 0, n_mid = 0, n_big = 0, n_big2 = 0, n_huge = 0;
+  Buf<int64_t> huge_toff;  // global table offsets (slots), size n_huge + 1
+  Buf<int32_t> huge_tcap;  // log2 of the table capacity per vertex
+  int64_t huge_slots = 0;
   int64_t edges[5] = {0, 0, 0, 0, 0};  // adjacency entries per tier
   Buf<int64_t> huge_chunk_start;  // prefix of chunk counts over the huge list (n_huge + 1)
   int64_t n_huge_chunks = 0;
+  // the huge tables are scanned in segments of kSegSlots slots by many blocks
+  Buf<int64_t> huge_seg_start;    // prefix of segment counts over the huge list (n_huge + 1)
+  int64_t n_huge_segs = 0;
+  Buf<unsigned char> huge_seg_best;  // per segment: its best label (see lp.cu)
   Buf<int32_t> tkeys;  // global rating tables (big + huge), EMPTY = -1
   Buf<int64_t> tvals;
   // Later frees go to stream s (the cache may have been built on a stream
   // that no longer exists; see tp_graph::rehome).
   void rehome(cudaStream_t s) {
-    tier.s = small.s = mid.s = big.s = huge.s = s;
-    big_toff.s = huge_toff.s = big_tcap.s = huge_tcap.s = s;
+    tier.s = small.s = mid.s = big.s = big2.s = huge.s = s;
+    huge_toff.s = huge_tcap.s = s;
     huge_chunk_start.s = tkeys.s = tvals.s = s;
+    huge_seg_start.s = huge_seg_best.s = s;
   }
 };
 
