@@ -58,7 +58,7 @@ __global__ void k_count(GView g, const uint8_t *tier, const int32_t *map, int64_
     int64_t c = 0;
     if (tier[u] != TIER_HUGE) {
       int32_t a = map[u];
-      warp_neighbours<COMP>(g, u, -1, [&](bool has, int32_t v, int64_t) {
+      warp_neighbours<COMP>(g, u, -1, [&](bool has, int32_t v, int64_t, int64_t) {
         c += __popc(__ballot_sync(kFull, has && map[v] != a));
       });
     }
@@ -87,7 +87,7 @@ __global__ void k_count_chunks(GView g, const int32_t *huge, int64_t n_huge,
     int64_t u = huge[i];
     int32_t a = map[u];
     int64_t c = 0;
-    warp_neighbours<COMP>(g, u, it - chunk_start[i], [&](bool has, int32_t v, int64_t) {
+    warp_neighbours<COMP>(g, u, it - chunk_start[i], [&](bool has, int32_t v, int64_t, int64_t) {
       c += __popc(__ballot_sync(kFull, has && map[v] != a));
     });
     if (lane_id() == 0) cnt[it] = c;
@@ -98,7 +98,7 @@ template <bool COMP>
 __device__ __forceinline__ void emit(const GView &g, int64_t u, int64_t chunk, const int32_t *map,
                                      int64_t nc, int64_t pos, uint64_t *keys, uint64_t *vals) {
   int32_t a = map[u];
-  warp_neighbours<COMP>(g, u, chunk, [&](bool has, int32_t v, int64_t w) {
+  warp_neighbours<COMP>(g, u, chunk, [&](bool has, int32_t v, int64_t w, int64_t) {
     int32_t b = has ? map[v] : a;
     bool keep = has && b != a;
     unsigned m = __ballot_sync(kFull, keep);

@@ -2,28 +2,33 @@
 // "Compression Scheme" of the paper: gap + VarInt, first edge id header,
 // chunks of 1000 neighbours above degree 10000).
 //
-// The compressed decoder is warp-cooperative: a warp reads a 32-byte window
-// of the stream (one byte per lane, coalesced), finds value ends with a
-// ballot of the continuation bits, lets the lane holding the last byte of a
-// value assemble it from up to four preceding lanes by shuffles, and turns
-// gaps into neighbour ids with a warp prefix sum. Each window yields up to 32
-// neighbour ids, one per lane, delivered to the caller as a batch.
+// The compressed decoder is warp-cooperative: a warp reads a 128-byte window
+// of the stream (one aligned word per lane, coalesced), assembles every
+// value in the lane holding its last byte, and turns gaps into neighbour ids
+// with warp prefix sums. A window yields up to 128 ids, up to four per lane,
+// delivered to the caller in four batches.
 #pragma once
 #include "tp_internal.cuh"
 
 namespace tp {
 
-// Single-thread VarInt read (up to 10 bytes). Returns bytes consumed.
+// Single-thread VarInt read (up to 10 bytes). Returns bytes consumed. The
+// stream is padded with zero bytes, so all ten bytes a VarInt may span are
+// loaded at once (one memory round trip instead of one per byte).
 __device__ __forceinline__ int read_varint(const uint8_t *p, uint64_t &x) {
+  uint32_t b[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) b[i] = p[i];
   uint64_t v = 0;
-  int i = 0;
-  for (; i < 10; ++i) {
-    uint64_t b = p[i];
-    v |= (b & 0x7fu) << (7 * i);
-    if (!(b & 0x80u)) break;
+  int len = 10;
+  bool open = true;
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    if (open) v |= (uint64_t)(b[i] & 0x7fu) << (7 * i);
+    if (open && !(b[i] & 0x80u)) len = i + 1, open = false;
   }
   x = v;
-  return i + 1;
+  return len;
 }
 
 __device__ __forceinline__ uint64_t off_at(const GView &g, int64_t u) {
@@ -45,7 +50,7 @@ __device__ __forceinline__ ZipNbr zip_nbr(const GView &g, int64_t u) {
   z.begin = off_at(g, u);
   z.end = off_at(g, u + 1);
   uint64_t a, b;
-  int hl = read_varint(g.bytes + z.begin, a);
+  int hl = read_varint(g.bytes + z.begin, a);  // both headers' loads are independent
   read_varint(g.bytes + z.end, b);
   z.first = (int64_t)a;
   z.deg = (int64_t)(b - a);
@@ -73,65 +78,141 @@ __device__ __forceinline__ void zip_chunk(const GView &g, const ZipNbr &z, int64
 }
 
 // Decodes `count` neighbour ids of u from the chunk occupying bytes
-// [p, end). f(bool has, int32_t v) is called by every lane once per window.
-// Returns false (and latches TP_ERR_CORRUPT) on a malformed chunk.
+// [p, end), 128 bytes per warp step: every lane loads one aligned 32-bit
+// word (bytes before p are turned into value ends that are discarded, bytes
+// from end on into continuation bytes), and for each byte that ends a value
+// assembles the value from it and the (at most four) continuation bytes
+// before it, which lie in its own word or the previous lane's. A warp scan
+// of the values per lane gives their indices, a second one the prefix sums
+// of the gaps. f(bool has, int32_t v, int64_t idx) is called by every lane
+// four times per step (the lane's first..fourth value of the step, or
+// has = false); idx is the value's position in the chunk. Returns false
+// (and latches TP_ERR_CORRUPT) on a malformed chunk.
 template <class F>
 __device__ __forceinline__ bool warp_decode_chunk(const GView &g, int64_t u, uint64_t p,
                                                   uint64_t end, int64_t count, F &&f) {
   const int lane = lane_id();
-  int64_t done = 0, prev = 0;
-  bool first = true;
+  int64_t done = 0;
+  int64_t prev = 0;  // id of the last value of the previous step
   while (done < count) {
-    uint64_t q = p + lane;
-    uint32_t b = q < end ? (uint32_t)g.bytes[q] : 0x80u;  // past the end: never a value end
-    unsigned endmask = __ballot_sync(kFull, !(b & 0x80u));
-    int64_t rem = count - done;
-    if (__popc(endmask) > rem) {  // only on a malformed chunk: keep the first rem ends
-      unsigned m = endmask, keep = 0;
-      for (int64_t i = 0; i < rem; ++i) {
-        unsigned low = m & (0u - m);
-        keep |= low;
-        m ^= low;
-      }
-      endmask = keep;
-    }
-    if (endmask == 0) {
-      if (lane == 0) latch_error(g.err, TP_ERR_CORRUPT);
-      return false;
-    }
-    unsigned below = endmask & lanemask_lt();
-    int s = below ? 32 - __clz(below) : 0;  // first lane of my value
-    uint32_t pay = b & 0x7fu;
-    uint64_t val = 0;
+    const uint64_t base = p & ~(uint64_t)3;
+    const uint64_t q = base + 4 * (uint64_t)lane;
+    uint32_t w = q < end ? *reinterpret_cast<const uint32_t *>(g.bytes + q) : 0x80808080u;
+    // bytes before p: value ends (0x00), discarded below; from end on: continuation
+    uint32_t lead = 0;  // bytes of w before p
 #pragma unroll
-    for (int d = 0; d < 5; ++d) {
-      uint32_t pb = __shfl_up_sync(kFull, pay, d);
-      int src = lane - d;
-      if (src >= s && src >= 0) val |= (uint64_t)pb << (7 * (src - s));
+    for (int j = 0; j < 4; ++j) {
+      const uint64_t qj = q + j;
+      if (qj < p) w &= ~(0xffu << (8 * j)), lead |= 1u << j;
+      else if (qj >= end) w |= 0x80u << (8 * j);
     }
-    bool mine = (endmask >> lane) & 1u;
-    bool bad = mine && (lane - s >= 5);
-    int64_t c = 0;
-    if (mine) {
-      if (first && below == 0) {
-        c = (val & 1u) ? u - (int64_t)(val >> 1) : u + (int64_t)(val >> 1);
-      } else {
-        c = (int64_t)val;
-        bad |= val == 0;  // gaps of a sorted duplicate-free list are >= 1
+    const uint32_t prevw = __shfl_up_sync(kFull, w, 1);
+    const uint32_t prev2 = __shfl_up_sync(kFull, w, 2);
+    const uint32_t pw = lane >= 1 ? prevw : 0u;  // bytes before the window: value ends
+    const uint32_t pw2 = lane >= 2 ? prev2 : 0u;
+    const uint64_t cat = (uint64_t)w << 32 | pw;  // bytes of pw then w, in stream order
+    uint32_t val[4];
+    uint32_t ends = 0;  // real value ends of this lane (bit j: byte j)
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t bj = (w >> (8 * j)) & 0xffu;
+      // the four bytes before byte j, the nearest in bits 0..7
+      const uint32_t win = __byte_perm((uint32_t)(cat >> (8 * j)), 0, 0x0123);
+      const uint32_t stop = ~win & 0x80808080u;
+      const int k = stop ? (__ffs(stop) - 8) >> 3 : 4;
+      uint32_t pk = (win & 0x7fu) | ((win >> 1) & 0x3f80u) | ((win >> 2) & 0x1fc000u) |
+                    ((win >> 3) & 0xfe00000u);
+      uint32_t v = bj & 0x7fu;
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        v = d < k ? (v << 7) | (pk & 0x7fu) : v;
+        pk >>= 7;
+      }
+      val[j] = v;
+      const bool is_end = !(bj & 0x80u) && !((lead >> j) & 1u);
+      ends |= (uint32_t)is_end << j;
+      // a fifth continuation byte: the value is longer than a VarInt of 32 bits
+      const uint32_t fifth = j >= 1 ? (pw >> (8 * (j - 1))) & 0xffu : (pw2 >> 24) & 0xffu;
+      bad |= is_end && k == 4 && (fifth & 0x80u);
+    }
+    const uint32_t nl = __popc(ends);
+    const uint32_t incl = warp_incl_scan(nl);
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    if (total == 0 || done + total > count) bad = true;
+    // gap sums: the chunk's first value is the signed offset from u
+    int64_t gs = 0;
+    int64_t ids[4];
+    {
+      uint32_t idx = incl - nl;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (!((ends >> j) & 1u)) continue;
+        const bool first = done == 0 && idx == 0;
+        if (!first) {
+          gs += val[j];
+          bad |= val[j] == 0;  // gaps of a sorted duplicate-free list are >= 1
+        }
+        ++idx;
       }
     }
-    int64_t v = (first ? 0 : prev) + warp_incl_scan(c);
-    bad |= mine && (v < 0 || v >= g.n);
+    const int64_t gincl = warp_incl_scan(gs);
+    int64_t run = (done == 0 ? 0 : prev) + gincl - gs;
+    {
+      uint32_t idx = incl - nl;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        ids[j] = 0;
+        if (!((ends >> j) & 1u)) continue;
+        if (done == 0 && idx == 0) {
+          run = (val[j] & 1u) ? u - (int64_t)(val[j] >> 1) : u + (int64_t)(val[j] >> 1);
+          // the first value's offset feeds every later id of this step
+        } else {
+          run += val[j];
+        }
+        ids[j] = run;
+        bad |= run < 0 || run >= g.n;
+        ++idx;
+      }
+    }
+    if (done == 0) {
+      // ids after the first value were summed without its offset: add it
+      const uint32_t owner = __ffs(__ballot_sync(kFull, nl > 0)) - 1;
+      const int64_t id0 = __shfl_sync(kFull, ((ends & 1u) ? ids[0] : (ends & 2u) ? ids[1]
+                                                     : (ends & 4u) ? ids[2] : ids[3]),
+                                      owner);
+      if (lane != (int)owner) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          ids[j] += id0;
+          bad |= ((ends >> j) & 1u) && (ids[j] < 0 || ids[j] >= g.n);
+        }
+      }
+    }
     if (__any_sync(kFull, bad)) {
       if (lane == 0) latch_error(g.err, TP_ERR_CORRUPT);
       return false;
     }
-    f(mine, (int32_t)v);
-    int last = 31 - __clz(endmask);
-    prev = __shfl_sync(kFull, v, last);
-    first = false;
-    done += __popc(endmask);
-    p += (uint64_t)last + 1;
+    {
+      uint32_t idx = incl - nl;
+      uint32_t e = ends;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool has = e != 0;
+        const int b = has ? __ffs(e) - 1 : 0;
+        e &= e - 1;
+        const int64_t v = b == 0 ? ids[0] : b == 1 ? ids[1] : b == 2 ? ids[2] : ids[3];
+        f(has, (int32_t)v, done + (int64_t)idx);
+        idx += has;
+      }
+    }
+    // the last value of the step continues into the next one
+    const uint32_t lastlane = 31 - __clz(__ballot_sync(kFull, nl > 0));
+    const int hb = 31 - __clz(__shfl_sync(kFull, ends, lastlane));
+    const int64_t lastid = __shfl_sync(kFull, hb == 0 ? ids[0] : hb == 1 ? ids[1] : hb == 2 ? ids[2] : ids[3], lastlane);
+    prev = lastid;
+    done += total;
+    p = base + 4 * (uint64_t)lastlane + (uint64_t)hb + 1;
   }
   if (p != end) {
     if (lane == 0) latch_error(g.err, TP_ERR_CORRUPT);
@@ -141,15 +222,18 @@ __device__ __forceinline__ bool warp_decode_chunk(const GView &g, int64_t u, uin
 }
 
 // Visits the neighbours of u in warp-wide batches: f(bool has, int32_t v,
-// int64_t w). For CSR the batch is 32 consecutive entries; for the
-// compressed format it is one decoded window of one chunk. chunk < 0 visits
-// the whole neighbourhood; otherwise only chunk `chunk` (chunks of
-// kChunkSize entries, for CSR as well).
+// int64_t w, int64_t idx), idx = position of v in u's neighbourhood (the
+// batches are not in neighbourhood order for the compressed format). For
+// CSR a batch is 32 consecutive entries; for the compressed format a
+// decoder step calls f four times. chunk < 0 visits the whole
+// neighbourhood; otherwise only chunk `chunk` (chunks of kChunkSize
+// entries, for CSR as well).
 template <bool COMP, class F>
 __device__ __forceinline__ void warp_neighbours(const GView &g, int64_t u, int64_t chunk, F &&f) {
   const int lane = lane_id();
   if (!COMP) {
-    int64_t b = g.xadj[u], e = g.xadj[u + 1];
+    const int64_t b0 = g.xadj[u];
+    int64_t b = b0, e = g.xadj[u + 1];
     if (chunk >= 0) {
       b += chunk * kChunkSize;
       e = b + kChunkSize < e ? b + kChunkSize : e;
@@ -159,7 +243,7 @@ __device__ __forceinline__ void warp_neighbours(const GView &g, int64_t u, int64
       bool has = k < e;
       int32_t v = has ? g.adj[k] : 0;
       int64_t w = (has && g.ew) ? g.ew[k] : 1;
-      f(has, v, w);
+      f(has, v, w, k - b0);
     }
   } else {
     ZipNbr z = zip_nbr(g, u);
@@ -169,7 +253,9 @@ __device__ __forceinline__ void warp_neighbours(const GView &g, int64_t u, int64
       uint64_t cb, ce;
       int64_t cnt;
       zip_chunk(g, z, j, cb, ce, cnt);
-      if (!warp_decode_chunk(g, u, cb, ce, cnt, [&](bool has, int32_t v) { f(has, v, (int64_t)1); }))
+      const int64_t at = j * kChunkSize;
+      if (!warp_decode_chunk(g, u, cb, ce, cnt,
+                             [&](bool has, int32_t v, int64_t i) { f(has, v, (int64_t)1, at + i); }))
         return;
     }
   }

@@ -241,21 +241,42 @@ void compute_degrees(const tp_graph *g, int64_t *d_deg, cudaStream_t s) {
 // ---------------------------------------------------------------- tiers
 namespace {
 
-// Compressed graphs (off32 or off64 set) keep records longer than
-// kLaneMaxRecord bytes out of the lane tier.
+// Compressed lane-tier records longer than this take the decoder that loads
+// beyond its 80-byte window; they join the lane tier only where they are
+// common (skewed graphs: long gaps), else the warp tier rates them.
+constexpr uint64_t kLaneShortRecord = 65;
+
+// Lane-tier candidates (degree <= lane_max) and how many have long records.
+__global__ void k_lane_records(const int64_t *deg, int64_t n, int32_t lane_max,
+                               const uint32_t *off32, const uint64_t *off64,
+                               unsigned long long *cnt) {
+  unsigned long long a = 0, l = 0;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    if (deg[u] > lane_max) continue;
+    const uint64_t len = off32 ? (uint64_t)(off32[u + 1] - off32[u]) : off64[u + 1] - off64[u];
+    ++a;
+    l += len > kLaneShortRecord;
+  }
+  a = warp_sum(a);
+  l = warp_sum(l);
+  if (lane_id() == 0 && a) atomicAdd(&cnt[0], a);
+  if (lane_id() == 0 && l) atomicAdd(&cnt[1], l);
+}
+
 __global__ void k_classify(const int64_t *deg, int64_t n, int32_t lane_max, int32_t small_max,
                            int32_t mid_max, const uint32_t *off32, const uint64_t *off64,
-                           uint8_t *tier, int32_t *flag_small, int32_t *flag_mid,
-                           int32_t *flag_big, int32_t *flag_big2, int32_t *flag_huge,
-                           unsigned long long *stats) {
+                           bool long_records, uint8_t *tier, int32_t *flag_small,
+                           int32_t *flag_mid, int32_t *flag_big, int32_t *flag_big2,
+                           int32_t *flag_huge, unsigned long long *stats) {
   int64_t e[5] = {0, 0, 0, 0, 0}, c[5] = {0, 0, 0, 0, 0};
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
        u += (int64_t)gridDim.x * blockDim.x) {
     int64_t d = deg[u];
     bool lane = lane_max > 0 && d <= lane_max;
-    if (lane && (off32 || off64)) {
+    if (lane && !long_records && (off32 || off64)) {
       const uint64_t len = off32 ? (uint64_t)(off32[u + 1] - off32[u]) : off64[u + 1] - off64[u];
-      lane = len <= (uint64_t)kLaneMaxRecord;
+      lane = len <= kLaneShortRecord;
     }
     uint8_t t = lane ? TIER_LANE
                 : d <= small_max ? TIER_SMALL
@@ -343,8 +364,19 @@ void build_tiers(tp_graph *g, const tp_params &p, cudaStream_t s) {
   TP_CUDA(cudaMemsetAsync(te.get(), 0, 10 * sizeof(unsigned long long), s));
   const uint32_t *o32 = g->compressed && !g->off_is64 ? g->off32.get() : nullptr;
   const uint64_t *o64 = g->compressed && g->off_is64 ? g->off64.get() : nullptr;
+  bool long_records = false;
+  if ((o32 || o64) && lane_max > 0) {  // long lane records where more than 5% are long
+    launch(k_lane_records, grid_for(n, 256), 256, 0, s, deg.get(), n, lane_max, o32, o64, te.get());
+    unsigned long long lc[2];
+    TP_CUDA(cudaMemcpyAsync(lc, te.get(), sizeof(lc), cudaMemcpyDeviceToHost, s));
+    TP_CUDA(cudaStreamSynchronize(s));
+    long_records = lc[1] * 20 > lc[0];
+    T.lane_long = long_records;
+    TP_CUDA(cudaMemsetAsync(te.get(), 0, 2 * sizeof(unsigned long long), s));
+  }
   launch(k_classify, grid_for(n, 256), 256, 0, s, deg.get(), n, lane_max, small_max, mid_max,
-         o32, o64, T.tier.get(), fs.get(), fm.get(), fb.get(), fb2.get(), fh.get(), te.get());
+         o32, o64, long_records, T.tier.get(), fs.get(), fm.get(), fb.get(), fb2.get(), fh.get(),
+         te.get());
   TP_LAUNCH_CHECK();
   unsigned long long hte[10];
   TP_CUDA(cudaMemcpyAsync(hte, te.get(), sizeof(hte), cudaMemcpyDeviceToHost, s));
@@ -557,15 +589,14 @@ __global__ void k_unzip(GView g, const int64_t *xadj, int32_t *adj) {
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t u = warp; u < g.n; u += nw) {
-    int64_t pos = xadj[u];
-    int64_t lim = xadj[u + 1];
-    warp_neighbours<true>(g, u, -1, [&](bool has, int32_t v, int64_t) {
-      unsigned m = __ballot_sync(kFull, has);
-      int r = __popc(m & lanemask_lt());
-      if (has && pos + r < lim) adj[pos + r] = v;
-      pos += __popc(m);
+    const int64_t pos = xadj[u];
+    const int64_t deg = xadj[u + 1] - pos;
+    int64_t seen = 0;
+    warp_neighbours<true>(g, u, -1, [&](bool has, int32_t v, int64_t, int64_t idx) {
+      if (has && idx < deg) adj[pos + idx] = v;
+      seen += __popc(__ballot_sync(kFull, has));
     });
-    if (lane_id() == 0 && pos != lim) latch_error(g.err, TP_ERR_CORRUPT);
+    if (lane_id() == 0 && seen != deg) latch_error(g.err, TP_ERR_CORRUPT);
   }
 }
 

@@ -221,7 +221,7 @@ __device__ void rate_vertex_warp(const RateCtx &c, int64_t u, int32_t *keys, int
   b.init();
   // every lane adds its neighbour's label to the table (shared-memory
   // atomics are far cheaper than grouping equal labels across lanes first)
-  warp_neighbours<COMP>(c.g, u, -1, [&](bool has, int32_t v, int64_t w) {
+  warp_neighbours<COMP>(c.g, u, -1, [&](bool has, int32_t v, int64_t w, int64_t) {
     if (has) tbl_add(keys, vals, logcap, c.label[v], w, c.g.err);
   });
   __syncwarp();
@@ -349,12 +349,15 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
 
 // Decodes u's compressed record into its shared-memory column: the raw
 // values (first the signed first neighbour, then the gaps) go to
-// col[i * 32]; returns the degree. The record (<= kLaneMaxRecord bytes) is
+// col[i * 32]; returns the degree. The record's first 80 bytes are
 // loaded at once as five 16-byte groups from its 16-byte aligned start, so
-// no load waits on another, and consumed a 32-bit word at a time. Bytes
+// no load waits on another (a longer record, up to 165 bytes at degree 32
+// with five-byte gaps, loads its further groups as the decoder reaches
+// them), and consumed a 32-bit word at a time. Bytes
 // before the record are turned into value ends and, like the header, are
 // written to slot 0, which the first neighbour then overwrites; bytes after
 // it are turned into continuation bytes, so they end no value.
+template <bool LONG>
 __device__ __forceinline__ int lane_decode(const GView &g, uint64_t b, uint64_t e, uint32_t *col) {
   constexpr int G = 5;  // 80-byte window
   const uint64_t ws = b & ~(uint64_t)15;
@@ -363,12 +366,17 @@ __device__ __forceinline__ int lane_decode(const GView &g, uint64_t b, uint64_t 
   uint4 q[G];
 #pragma unroll
   for (int j = 0; j < G; ++j) q[j] = 16 * j < endp ? __ldcs(src + j) : make_uint4(0, 0, 0, 0);
-  int fi = 0;  // words of q[0] already taken
+  int fi = 0;         // words of q[0] already taken
+  int nextg = G;      // next 16-byte group to load (records longer than the window)
   auto pop = [&]() -> uint32_t {
     const uint32_t w = fi == 0 ? q[0].x : fi == 1 ? q[0].y : fi == 2 ? q[0].z : q[0].w;
     if (++fi == 4) {
 #pragma unroll
       for (int j = 0; j + 1 < G; ++j) q[j] = q[j + 1];
+      if (LONG) {
+        q[G - 1] = 16 * nextg < endp ? __ldcs(src + nextg) : make_uint4(0, 0, 0, 0);
+        ++nextg;
+      }
       fi = 0;
     }
     return w;
@@ -730,7 +738,9 @@ __device__ __forceinline__ void lane_batch(const RateCtx &c, bool has, int32_t u
 template <bool W>
 __host__ __device__ constexpr int lane_warps() { return W ? 4 : kLaneWarps; }
 
-template <bool COMP, int MODE, bool W>
+// LONG: some compressed records exceed the 80-byte window (skewed graphs);
+// a separate instantiation keeps the common kernel free of that path.
+template <bool COMP, int MODE, bool W, bool LONG = false>
 __global__ void __launch_bounds__(lane_warps<W>() * 32, W ? 1 : kLaneBlocksPerSM)
     k_rate_lane(RateCtx c) {
   static_assert(!(COMP && W), "weighted levels are CSR");
@@ -801,7 +811,12 @@ __global__ void __launch_bounds__(lane_warps<W>() * 32, W ? 1 : kLaneBlocksPerSM
         if (COMP) {
           uint64_t rb, re;
           lane_record(c.g, wrec, q + lane, u, rb, re);
-          deg = lane_decode(c.g, rb, re, col);
+          // records beyond the 80-byte window (rare except on skewed graphs)
+          // take the decoder that loads further groups
+          if (LONG && __any_sync(__activemask(), (re - (rb & ~(uint64_t)15)) > 80))
+            deg = lane_decode<true>(c.g, rb, re, col);
+          else
+            deg = lane_decode<false>(c.g, rb, re, col);
         } else {
           deg = min((int)(c.g.xadj[u + 1] - c.g.xadj[u]), kLaneMaxDeg);
         }
@@ -1495,7 +1510,8 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
     if (g->unit_ew) {
       unsigned blocks = (unsigned)std::min<int64_t>(
           (g->n + 256 * kLaneWarps - 1) / (256 * kLaneWarps), (int64_t)sms * kLaneBlocksPerSM);
-      if (comp) launch(k_rate_lane<true, LM, false>, blocks, 32 * kLaneWarps, 0, s, c);
+      if (comp && T.lane_long) launch(k_rate_lane<true, LM, false, true>, blocks, 32 * kLaneWarps, 0, s, c);
+      else if (comp) launch(k_rate_lane<true, LM, false>, blocks, 32 * kLaneWarps, 0, s, c);
       else launch(k_rate_lane<false, LM, false>, blocks, 32 * kLaneWarps, 0, s, c);
     } else {  // weighted levels are CSR
       constexpr int WW = lane_warps<true>();

@@ -69,7 +69,7 @@ __global__ void k_static_cut(GView g, const int32_t *part, unsigned long long *a
   int64_t sum = 0;
   for (int64_t u = warp; u < g.n; u += nw) {
     int32_t pu = part[u];
-    warp_neighbours<COMP>(g, u, -1, [&](bool has, int32_t v, int64_t w) {
+    warp_neighbours<COMP>(g, u, -1, [&](bool has, int32_t v, int64_t w, int64_t) {
       if (has && part[v] != pu) sum += w;
     });
   }

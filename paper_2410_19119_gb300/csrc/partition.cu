@@ -70,7 +70,7 @@ __global__ void k_cut(GView g, const uint8_t *tier, const int32_t *part, unsigne
   for (int64_t u = warp; u < g.n; u += nw) {
     if (tier[u] == TIER_LANE || tier[u] == TIER_SMALL) continue;
     int32_t pu = part[u];
-    warp_neighbours<COMP>(g, u, -1, [&](bool has, int32_t v, int64_t w) {
+    warp_neighbours<COMP>(g, u, -1, [&](bool has, int32_t v, int64_t w, int64_t) {
       if (has && part[v] != pu) acc += w;
     });
   }

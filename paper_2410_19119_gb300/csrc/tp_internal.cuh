@@ -102,9 +102,6 @@ struct Buf {
 // a rating never depends on its tier).
 enum : uint8_t { TIER_SMALL = 0, TIER_MID = 1, TIER_BIG = 2, TIER_HUGE = 3, TIER_LANE = 4 };
 constexpr int kLaneMaxDeg = 32;  // lane tier: one lane per vertex
-// Compressed lane tier: records of at most this many bytes, so a record fits
-// an 80-byte window from its 16-byte aligned start.
-constexpr int kLaneMaxRecord = 65;
 constexpr int64_t kLaneMaxEdgeWeight = (int64_t)1 << 26;  // weighted lane tier: ratings fit 32 bits
 constexpr int64_t kChunkThreshold = 10000;  // compressed format: chunked above this degree
 constexpr int64_t kChunkSize = 1000;        // neighbours per chunk
@@ -115,6 +112,7 @@ constexpr int64_t kBigSplit = 4096;         // big tier: degrees up to here use 
 struct TierCache {
   bool built = false;
   int32_t small_max = 0, mid_max = 0, lane_max = 0;
+  bool lane_long = false;  // compressed lane records may exceed 80 bytes (skewed graphs)
   int64_t count[5] = {0, 0, 0, 0, 0};  // vertices per tier
   Buf<uint8_t> tier;         // n
   // vertex lists per tier (ascending); the big tier is listed in two parts,
