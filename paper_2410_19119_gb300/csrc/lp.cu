@@ -79,6 +79,8 @@ struct RateCtx {
   int64_t bucket_nb;
   // per listed vertex: record start << 8 | record length (compressed graphs)
   const uint64_t *bucket_rec;
+  // this round's sub-round + 1 of every vertex (null: hash on the fly)
+  const uint8_t *sub_byte;
 };
 
 __device__ __forceinline__ int64_t node_w(const GView &g, int64_t u) { return g.vw ? g.vw[u] : 1; }
@@ -87,7 +89,9 @@ __device__ __forceinline__ uint64_t rk_of(const RateCtx &c) { return c.rk_dev ? 
 
 template <int MODE>
 __device__ __forceinline__ bool active(const RateCtx &c, int64_t u) {
-  if (MODE == M_LP) return sub_round_of(hstep(rk_of(c), (uint64_t)u), c.S) == c.s;
+  if (MODE == M_LP)
+    return c.sub_byte ? c.sub_byte[u] == c.s + 1
+                      : sub_round_of(hstep(rk_of(c), (uint64_t)u), c.S) == c.s;
   if (MODE == M_FAV) return c.label[u] == u && c.lw[u] == node_w(c.g, u);
   return c.label[u] == c.blk;
 }
@@ -1188,10 +1192,13 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_huge_chunks(RateCtx c) {
 }
 
 // Huge tier, phase 2: one block per vertex scans its global table.
-static_assert(sizeof(Best) == kSegBestBytes, "segment results are Best records");
+static_assert(2 * sizeof(Best) == kSegBestBytes, "segment results are two Best records");
 
 // Huge tier, phase 2: every (vertex, segment of 4096 table slots) is scanned
-// by its own block for the best label ignoring the cap and the own rating.
+// by its own block for its best label ignoring the cap (with the own
+// rating) and for its best admissible label; it then clears its slots.
+// Admissibility is checked only for a label that beats the thread's best
+// admissible one so far, so few label weights are read.
 template <int MODE>
 __global__ void __launch_bounds__(kBlockThreads) k_rate_huge_scan(RateCtx c, Best *seg_best) {
   __shared__ Best wb[kBlockThreads / 32];
@@ -1212,33 +1219,43 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_huge_scan(RateCtx c, Bes
     const int64_t u = c.list[i];
     if (!active<MODE>(c, u)) continue;
     const int32_t own = c.label[u];
+    const int64_t cu = node_w(c.g, u);
     const uint64_t hv = tie_key<MODE>(c, u);
     const int64_t cap = (int64_t)1 << c.tcap[i];
     const int64_t s0 = (item - c.seg_start[i]) << kSegLog;
     const int64_t s1 = min(s0 + ((int64_t)1 << kSegLog), cap);
-    const int32_t *tk = c.tkeys + c.tbase + c.toff[i];
-    const int64_t *tv = c.tvals + c.tbase + c.toff[i];
-    Best b;
+    int32_t *tk = c.tkeys + c.tbase + c.toff[i];
+    int64_t *tv = c.tvals + c.tbase + c.toff[i];
+    Best b, a;
     b.init();
+    a.init();
     for (int64_t sl = s0 + threadIdx.x; sl < s1; sl += kBlockThreads) {
       const int32_t x = tk[sl];
       if (x < 0) continue;
       const int64_t R = tv[sl];
+      tk[sl] = -1;
+      tv[sl] = 0;
       if (x == own) {
         b.rown = R;
         continue;
       }
       const uint32_t t = MODE == M_REBAL ? 0u : tie_hash(hv, x);
       if (better(R, t, x, b.r, b.t, b.x)) b.r = R, b.t = t, b.x = x;
+      if (MODE != M_FAV && better(R, t, x, a.r, a.t, a.x) && c.lw[x] + cu <= c.cap)
+        a.r = R, a.t = t, a.x = x;
     }
     block_reduce_best(b, wb);
-    if (threadIdx.x == 0) seg_best[item] = b;
+    if (MODE != M_FAV) block_reduce_best(a, wb);
+    if (threadIdx.x == 0) {
+      seg_best[2 * item] = b;
+      seg_best[2 * item + 1] = a;
+    }
   }
 }
 
-// Huge tier, phase 3: one block per vertex combines its segments; if the
-// winner is full it rescans the table for the best admissible label; then
-// it clears the table and acts on the decision.
+// Huge tier, phase 3: one block per vertex combines its segments: the best
+// label if it is admissible, else the best admissible one; then it acts on
+// the decision.
 template <int MODE>
 __global__ void __launch_bounds__(kBlockThreads) k_rate_huge_decide(RateCtx c, const Best *seg_best) {
   __shared__ Best wb[kBlockThreads / 32];
@@ -1247,36 +1264,24 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_huge_decide(RateCtx c, c
   for (int64_t i = blockIdx.x; i < c.list_n; i += gridDim.x) {
     int64_t u = c.list[i];
     if (!active<MODE>(c, u)) continue;
-    const int32_t own = c.label[u];
     const int64_t cu = node_w(c.g, u);
-    const uint64_t hv = tie_key<MODE>(c, u);
-    int32_t *tk = c.tkeys + c.tbase + c.toff[i];
-    int64_t *tv = c.tvals + c.tbase + c.toff[i];
-    const int64_t cap = (int64_t)1 << c.tcap[i];
-    Best b;
+    Best b, a;
     b.init();
+    a.init();
     for (int64_t q = c.seg_start[i] + threadIdx.x; q < c.seg_start[i + 1]; q += kBlockThreads) {
-      const Best o = seg_best[q];
+      const Best o = seg_best[2 * q], oa = seg_best[2 * q + 1];
       if (better(o.r, o.t, o.x, b.r, b.t, b.x)) b.r = o.r, b.t = o.t, b.x = o.x;
       b.rown = max(b.rown, o.rown);
+      if (better(oa.r, oa.t, oa.x, a.r, a.t, a.x)) a.r = oa.r, a.t = oa.t, a.x = oa.x;
     }
     block_reduce_best(b, wb);
-    // the winner is full: the best admissible label instead
+    block_reduce_best(a, wb);
     if (MODE != M_FAV && b.x != INT32_MAX && c.lw[b.x] + cu > c.cap) {
-      const int64_t rown = b.rown;
-      b.init();
-      for (int64_t sl = threadIdx.x; sl < cap; sl += kBlockThreads) {
-        const int32_t x = tk[sl];
-        if (x < 0 || x == own) continue;
-        const int64_t R = tv[sl];
-        if (MODE == M_LP && R <= rown) continue;
-        const uint32_t t = MODE == M_REBAL ? 0u : tie_hash(hv, x);
-        if (better(R, t, x, b.r, b.t, b.x) && c.lw[x] + cu <= c.cap) b.r = R, b.t = t, b.x = x;
-      }
-      block_reduce_best(b, wb);
-      b.rown = rown;
+      // the winner is full: the best admissible label (for a move it must
+      // also improve on the own rating, which finalize_warp checks)
+      a.rown = b.rown;
+      b = a;
     }
-    for (int64_t sl = threadIdx.x; sl < cap; sl += kBlockThreads) tk[sl] = -1, tv[sl] = 0;
     if (threadIdx.x < 32) {
       MoverBuf mb{mu, mt, mo, mg, 0};
       finalize_warp<MODE>(c, b, u, cu, &mb);
@@ -1676,9 +1681,10 @@ ApproveCtx approve_ctx(tp_graph *g, const LpState &st, LpWork &w) {
 constexpr int kBucketSpan = 2048;
 constexpr int kBucketChunks = kBucketSpan / 32;
 
-// Pass 0 hashes every vertex once and keeps its sub-round (+1; 0: not in the
-// lane tier) in sub[]; pass 1 reads it back. Lanes of a 32-vertex chunk with
-// the same sub-round are grouped with one match instruction.
+// Pass 0 hashes every vertex once and keeps its sub-round + 1 in sub_byte
+// (every rating tier tests it instead of hashing again) and counts the lane
+// tier; pass 1 lists the lane tier. Lanes of a 32-vertex chunk with the
+// same sub-round are grouped with one match instruction.
 // With offsets (compressed graphs), pass 1 also stores each listed vertex's
 // record start << 8 | record length in rec (lane-tier records are <= 65 bytes).
 __global__ void __launch_bounds__(256) k_bucket(const uint8_t *tier, int64_t n, uint64_t rk_in,
@@ -1700,10 +1706,13 @@ __global__ void __launch_bounds__(256) k_bucket(const uint8_t *tier, int64_t n, 
     int32_t sub = -1;
     if (u < n) {
       if (fill) {
-        sub = (int32_t)sub_byte[u] - 1;
+        sub = tier[u] == TIER_LANE ? (int32_t)sub_byte[u] - 1 : -1;
       } else {
-        if (tier[u] == TIER_LANE) sub = sub_round_of(hstep(rk, (uint64_t)u), S);
-        sub_byte[u] = (uint8_t)(sub + 1);
+        // every vertex's sub-round is kept (the other tiers test it); only
+        // the lane tier is listed
+        const int32_t sr = sub_round_of(hstep(rk, (uint64_t)u), S);
+        sub_byte[u] = (uint8_t)(sr + 1);
+        sub = tier[u] == TIER_LANE ? sr : -1;
       }
     }
     sub_of[q] = sub;
@@ -1753,7 +1762,7 @@ void lp_bucket(tp_graph *g, LpWork &w, uint64_t rk, int32_t S, const tp_params &
                cudaStream_t stream, const uint64_t *rk_dev) {
   build_tiers(g, p, stream);
   w.bucket_S = 0;
-  if (S > 32 || g->tiers.count[TIER_LANE] == 0) return;
+  if (S > 32) return;
   const int64_t nblocks = (g->n + kBucketSpan - 1) / kBucketSpan;
   if (!w.bucket.get()) w.bucket.alloc(std::max<int64_t>(w.n, 1), stream);
   if (!w.bucket_sub.get()) w.bucket_sub.alloc(std::max<int64_t>(w.n, 1), stream);
@@ -1876,6 +1885,7 @@ void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t
     c.bucket_off = w.bucket_off.get();
     c.bucket_nb = w.bucket_nblocks;
     c.bucket_rec = g->compressed ? w.bucket_rec.get() : nullptr;
+    c.sub_byte = w.bucket_sub.get();
   }
   rate_tiers<M_LP>(g, c, p, stream);
   prof_begin(PF_APPROVE, stream);

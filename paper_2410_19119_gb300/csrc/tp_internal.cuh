@@ -106,7 +106,7 @@ constexpr int64_t kLaneMaxEdgeWeight = (int64_t)1 << 26;  // weighted lane tier:
 constexpr int64_t kChunkThreshold = 10000;  // compressed format: chunked above this degree
 constexpr int64_t kChunkSize = 1000;        // neighbours per chunk
 constexpr int kSegLog = 12;                 // huge tables are scanned 4096 slots per block
-constexpr int kSegBestBytes = 24;           // one segment's best label (rating, tie, label, own)
+constexpr int kSegBestBytes = 48;           // one segment's best label and best admissible label
 constexpr int64_t kBigSplit = 4096;         // big tier: degrees up to here use 8192-slot tables
 
 struct TierCache {
