@@ -323,7 +323,7 @@ __global__ void k_table_caps(const int32_t *list, int64_t cnt, const int64_t *de
 __global__ void k_table_segs(const int32_t *logcap, int64_t cnt, int64_t *segs) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
        i += (int64_t)gridDim.x * blockDim.x)
-    segs[i] = logcap[i] > kSegLog ? (int64_t)1 << (logcap[i] - kSegLog) : 1;
+    segs[i] = logcap[i] - 1 > kSegLog ? (int64_t)1 << (logcap[i] - 1 - kSegLog) : 1;  // list = half
 }
 
 __global__ void k_fill_table(int32_t *keys, int64_t *vals, int64_t n) {
@@ -434,6 +434,9 @@ void build_tiers(tp_graph *g, const tp_params &p, cudaStream_t s) {
   if (total) {
     T.tkeys.alloc(total, s);
     T.tvals.alloc(total, s);
+    T.tlist.alloc(total / 2 + 1, s);
+    T.tcount.alloc(std::max<int64_t>(T.n_huge, 1), s);
+    TP_CUDA(cudaMemsetAsync(T.tcount.get(), 0, sizeof(int32_t) * std::max<int64_t>(T.n_huge, 1), s));
     launch(k_fill_table, grid_for(total, 256), 256, 0, s, T.tkeys.get(), T.tvals.get(), total);
     TP_LAUNCH_CHECK();
   }

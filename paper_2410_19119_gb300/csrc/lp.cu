@@ -65,6 +65,7 @@ struct RateCtx {
   int64_t list_n;
   int32_t *tkeys;
   int64_t *tvals;
+  int32_t *tlist, *tcount;  // filled slots per huge table
   const int64_t *toff;
   const int32_t *tcap;
   int64_t tbase;  // slot offset of this tier's tables inside tkeys/tvals
@@ -121,6 +122,27 @@ __device__ __forceinline__ void tbl_add(int32_t *keys, int64_t *vals, int logcap
     }
   }
   latch_error(err, TP_ERR_CORRUPT);  // more distinct labels than the degree allows
+}
+
+// tbl_add that returns the slot it filled (-1 if x was there already).
+__device__ __forceinline__ int32_t tbl_add_claim(int32_t *keys, int64_t *vals, int logcap, int32_t x,
+                                                 int64_t w, int32_t *err) {
+  uint32_t mask = (1u << logcap) - 1u, h = slot_of(x, logcap);
+  for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
+    int32_t k = *(volatile int32_t *)&keys[h];
+    int32_t filled = -1;
+    if (k == -1) {
+      const int32_t prev = atomicCAS(&keys[h], -1, x);
+      if (prev == -1) filled = (int32_t)h;
+      k = prev == -1 ? x : prev;
+    }
+    if (k == x) {
+      atomicAdd((unsigned long long *)&vals[h], (unsigned long long)w);
+      return filled;
+    }
+  }
+  latch_error(err, TP_ERR_CORRUPT);
+  return -1;
 }
 
 struct Best {
@@ -1141,6 +1163,8 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_huge_chunks(RateCtx c) {
   __shared__ uint32_t vbuf[COMP ? kChunkSize : 1];
   __shared__ int64_t red[kBlockThreads / 32 + 1];
   __shared__ int64_t s_vi;
+  __shared__ int32_t claimed[1 << kHugeLog];
+  __shared__ int32_t s_nclaim, s_base;
   const int tid = threadIdx.x;
   for (int k = tid; k < (1 << kHugeLog); k += kBlockThreads) keys[k] = -1, vals[k] = 0;
   __syncthreads();
@@ -1179,14 +1203,23 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_huge_chunks(RateCtx c) {
     __syncthreads();
     int32_t *tk = c.tkeys + c.tbase + c.toff[i];
     int64_t *tv = c.tvals + c.tbase + c.toff[i];
+    int32_t *tl = c.tlist + (c.tbase + c.toff[i]) / 2;
     const int lc = c.tcap[i];
+    if (tid == 0) s_nclaim = 0;
+    __syncthreads();
     for (int k = tid; k < (1 << kHugeLog); k += kBlockThreads) {
       const int32_t x = keys[k];
       if (x < 0) continue;
-      tbl_add(tk, tv, lc, x, (int64_t)vals[k], c.g.err);
+      const int32_t h = tbl_add_claim(tk, tv, lc, x, (int64_t)vals[k], c.g.err);
+      if (h >= 0) claimed[atomicAdd(&s_nclaim, 1)] = h;
       keys[k] = -1;
       vals[k] = 0;
     }
+    __syncthreads();
+    // the slots this chunk filled join the hub's list with one counter update
+    if (tid == 0 && s_nclaim) s_base = atomicAdd(c.tcount + i, s_nclaim);
+    __syncthreads();
+    for (int j = tid; j < s_nclaim; j += kBlockThreads) tl[s_base + j] = claimed[j];
     __syncthreads();
   }
 }
@@ -1221,15 +1254,22 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_huge_scan(RateCtx c, Bes
     const int32_t own = c.label[u];
     const int64_t cu = node_w(c.g, u);
     const uint64_t hv = tie_key<MODE>(c, u);
-    const int64_t cap = (int64_t)1 << c.tcap[i];
+    // a table filled to an eighth or more is read in slot order (8192 slots
+    // per segment); a sparser one through its list of filled slots (4096
+    // list entries per segment)
+    const int64_t filled = c.tcount[i], cap = (int64_t)1 << c.tcap[i];
+    const bool dense = 8 * filled >= cap;
     const int64_t s0 = (item - c.seg_start[i]) << kSegLog;
-    const int64_t s1 = min(s0 + ((int64_t)1 << kSegLog), cap);
+    const int64_t s1 = dense ? min(2 * (s0 + ((int64_t)1 << kSegLog)), cap)
+                             : min(s0 + ((int64_t)1 << kSegLog), filled);
     int32_t *tk = c.tkeys + c.tbase + c.toff[i];
     int64_t *tv = c.tvals + c.tbase + c.toff[i];
+    const int32_t *tl = c.tlist + (c.tbase + c.toff[i]) / 2;
     Best b, a;
     b.init();
     a.init();
-    for (int64_t sl = s0 + threadIdx.x; sl < s1; sl += kBlockThreads) {
+    for (int64_t j = (dense ? 2 * s0 : s0) + threadIdx.x; j < s1; j += kBlockThreads) {
+      const int32_t sl = dense ? (int32_t)j : tl[j];
       const int32_t x = tk[sl];
       if (x < 0) continue;
       const int64_t R = tv[sl];
@@ -1282,6 +1322,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_huge_decide(RateCtx c, c
       a.rown = b.rown;
       b = a;
     }
+    if (threadIdx.x == 0) c.tcount[i] = 0;  // the segments cleared the table
     if (threadIdx.x < 32) {
       MoverBuf mb{mu, mt, mo, mg, 0};
       finalize_warp<MODE>(c, b, u, cu, &mb);
@@ -1503,6 +1544,8 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
   c.tier = T.tier.get();
   c.tkeys = T.tkeys.get();
   c.tvals = T.tvals.get();
+  c.tlist = T.tlist.get();
+  c.tcount = T.tcount.get();
   const int sms = num_sms();
   const bool comp = g->compressed;
   const bool prof = MODE == M_LP && prof_active();

@@ -129,14 +129,18 @@ struct TierCache {
   Buf<int64_t> huge_seg_start;    // prefix of segment counts over the huge list (n_huge + 1)
   int64_t n_huge_segs = 0;
   Buf<unsigned char> huge_seg_best;  // per segment: its best label (see lp.cu)
-  Buf<int32_t> tkeys;  // global rating tables (big + huge), EMPTY = -1
+  Buf<int32_t> tkeys;  // global rating tables (huge tier), EMPTY = -1
   Buf<int64_t> tvals;
+  // per hub: the slots its table has filled (region toff/2 of half the
+  // table's size) and how many, so scans read filled slots only
+  Buf<int32_t> tlist;
+  Buf<int32_t> tcount;
   // Later frees go to stream s (the cache may have been built on a stream
   // that no longer exists; see tp_graph::rehome).
   void rehome(cudaStream_t s) {
     tier.s = small.s = mid.s = big.s = big2.s = huge.s = s;
     huge_toff.s = huge_tcap.s = s;
-    huge_chunk_start.s = tkeys.s = tvals.s = s;
+    huge_chunk_start.s = tkeys.s = tvals.s = tlist.s = tcount.s = s;
     huge_seg_start.s = huge_seg_best.s = s;
   }
 };
