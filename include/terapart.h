@@ -71,8 +71,11 @@ typedef struct {
   int32_t tier_small;    /* max degree rated with the small shared table (64) */
   int32_t tier_mid;      /* max degree rated with the large shared table (512; at most 512) */
   int32_t warps_per_block; /* warps per block in the small tier (8) */
-  int32_t use_graphs;    /* reserved, no effect */
-  int32_t graph_n;       /* reserved, no effect */
+  int32_t use_graphs;    /* 1: levels of at most graph_n vertices replay whole LP
+                            rounds from a CUDA graph; 0: every round launches its
+                            kernels directly (results are the same) */
+  int32_t graph_n;       /* largest level (vertices, at most 2^19) whose rounds
+                            are replayed from a CUDA graph (default 2^19) */
 } tp_params;
 
 typedef struct {

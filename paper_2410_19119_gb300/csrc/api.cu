@@ -75,7 +75,7 @@ void tp_params_default(tp_params *p) {
   p->tier_mid = 512;
   p->warps_per_block = 8;
   p->use_graphs = 1;
-  p->graph_n = 1 << 16;
+  p->graph_n = 1 << 19;
 }
 
 const char *tp_status_string(tp_status s) {

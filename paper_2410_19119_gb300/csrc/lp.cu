@@ -82,7 +82,27 @@ struct RateCtx {
   const uint64_t *bucket_rec;
   // this round's sub-round + 1 of every vertex (null: hash on the fly)
   const uint8_t *sub_byte;
+  // bucket mode of the warp/block tiers: this tier's list positions grouped
+  // by sub-round (null: scan the whole list and test each vertex)
+  const int32_t *bpos;
+  const int64_t *boff;  // this tier's S + 1 offsets into bpos
+  // huge tier in bucket mode: prefix of chunk / segment counts over bpos and
+  // the items (hub position << 32 | chunk or segment index)
+  const int64_t *hc_pre, *hs_pre, *hc_item, *hs_item;
+  // all tiers' buckets (rate_tiers slices them per tier)
+  const int32_t *tb_pos;
+  const int64_t *tb_off;
+  int64_t tb_base[LpWork::kTiers];
 };
+
+// Range of list entries (bucket mode: of bpos) a tier kernel walks.
+__device__ __forceinline__ void tier_range(const RateCtx &c, int64_t &b, int64_t &e) {
+  if (c.bpos) b = c.boff[c.s], e = c.boff[c.s + 1];
+  else b = 0, e = c.list_n;
+}
+// List position of entry k and whether its vertex is active this sub-round.
+template <int MODE>
+__device__ __forceinline__ bool tier_entry(const RateCtx &c, int64_t k, int64_t &pos, int64_t &u);
 
 __device__ __forceinline__ int64_t node_w(const GView &g, int64_t u) { return g.vw ? g.vw[u] : 1; }
 
@@ -95,6 +115,13 @@ __device__ __forceinline__ bool active(const RateCtx &c, int64_t u) {
                       : sub_round_of(hstep(rk_of(c), (uint64_t)u), c.S) == c.s;
   if (MODE == M_FAV) return c.label[u] == u && c.lw[u] == node_w(c.g, u);
   return c.label[u] == c.blk;
+}
+
+template <int MODE>
+__device__ __forceinline__ bool tier_entry(const RateCtx &c, int64_t k, int64_t &pos, int64_t &u) {
+  pos = c.bpos ? c.bpos[k] : k;
+  u = c.list[pos];
+  return c.bpos ? true : active<MODE>(c, u);
 }
 
 template <int MODE>
@@ -313,9 +340,11 @@ __global__ void k_rate_small(RateCtx c) {
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   if (c.list) {
-    for (int64_t i = gw; i < c.list_n; i += nw) {
-      const int64_t u = c.list[i];
-      if (active<MODE>(c, u))
+    int64_t kb, ke;
+    tier_range(c, kb, ke);
+    for (int64_t k = kb + gw; k < ke; k += nw) {
+      int64_t i, u;
+      if (tier_entry<MODE>(c, k, i, u))
         rate_vertex_warp<COMP, MODE>(c, u, ws.keys, ws.vals, kSmallLog, true, &mb);
     }
   } else {
@@ -890,9 +919,11 @@ __global__ void k_rate_list(RateCtx c) {
   MoverBuf mb{mu[w], mt[w], mo[w], mg[w], 0};
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = gw; i < c.list_n; i += nw) {
-    int64_t u = c.list[i];
-    if (!active<MODE>(c, u)) continue;
+  int64_t kb, ke;
+  tier_range(c, kb, ke);
+  for (int64_t k = kb + gw; k < ke; k += nw) {
+    int64_t i, u;
+    if (!tier_entry<MODE>(c, k, i, u)) continue;
     if (GLOBAL) {
       int64_t off = c.tbase + c.toff[i];
       rate_vertex_warp<COMP, MODE>(c, u, c.tkeys + off, c.tvals + off, c.tcap[i], false, &mb);
@@ -1084,9 +1115,11 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_block(RateCtx c, int max
   __shared__ int32_t mu[32], mt[32], mo[32];
   __shared__ int64_t mg[32];
   const int tid = threadIdx.x;
-  for (int64_t i = blockIdx.x; i < c.list_n; i += gridDim.x) {
-    const int64_t u = c.list[i];
-    if (!active<MODE>(c, u)) continue;  // uniform over the block
+  int64_t kb, ke;
+  tier_range(c, kb, ke);
+  for (int64_t k = kb + blockIdx.x; k < ke; k += gridDim.x) {
+    int64_t i, u;
+    if (!tier_entry<MODE>(c, k, i, u)) continue;  // uniform over the block
     const int64_t d = COMP ? zip_nbr(c.g, u).deg : c.g.xadj[u + 1] - c.g.xadj[u];
     int logc = 5;
     while (logc < maxlog && ((int64_t)1 << logc) < d + d / 2) ++logc;
@@ -1168,21 +1201,33 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_huge_chunks(RateCtx c) {
   const int tid = threadIdx.x;
   for (int k = tid; k < (1 << kHugeLog); k += kBlockThreads) keys[k] = -1, vals[k] = 0;
   __syncthreads();
-  for (int64_t item = blockIdx.x; item < c.n_chunks; item += gridDim.x) {
-    if (tid == 0) {  // vertex index: last i with chunk_start[i] <= item
-      int64_t lo = 0, hi = c.list_n - 1;
-      while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) / 2;
-        if (c.chunk_start[mid] <= item) lo = mid;
-        else hi = mid - 1;
+  // bucket mode: this sub-round's chunk items; else every chunk, skipping
+  // inactive hubs (the hub of an item found by binary search)
+  const int64_t ib = c.bpos ? c.hc_pre[c.boff[c.s]] : 0;
+  const int64_t ie = c.bpos ? c.hc_pre[c.boff[c.s + 1]] : c.n_chunks;
+  for (int64_t item = ib + blockIdx.x; item < ie; item += gridDim.x) {
+    int64_t i, j;
+    if (c.bpos) {
+      const int64_t it = c.hc_item[item];
+      i = it >> 32;
+      j = it & 0xffffffffLL;
+    } else {
+      if (tid == 0) {  // vertex index: last i with chunk_start[i] <= item
+        int64_t lo = 0, hi = c.list_n - 1;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi + 1) / 2;
+          if (c.chunk_start[mid] <= item) lo = mid;
+          else hi = mid - 1;
+        }
+        s_vi = lo;
       }
-      s_vi = lo;
+      __syncthreads();
+      i = s_vi;
+      j = item - c.chunk_start[i];
+      __syncthreads();  // s_vi is rewritten by the next item
     }
-    __syncthreads();
-    const int64_t i = s_vi, j = item - c.chunk_start[i];
     const int64_t u = c.list[i];
-    __syncthreads();  // s_vi is rewritten by the next item
-    if (!active<MODE>(c, u)) continue;  // uniform over the block
+    if (!c.bpos && !active<MODE>(c, u)) continue;  // uniform over the block
     if (COMP) {
       const ZipNbr z = zip_nbr(c.g, u);
       uint64_t cb, ce;
@@ -1236,21 +1281,31 @@ template <int MODE>
 __global__ void __launch_bounds__(kBlockThreads) k_rate_huge_scan(RateCtx c, Best *seg_best) {
   __shared__ Best wb[kBlockThreads / 32];
   __shared__ int64_t s_vi;
-  for (int64_t item = blockIdx.x; item < c.n_segs; item += gridDim.x) {
-    if (threadIdx.x == 0) {  // vertex index: last i with seg_start[i] <= item
-      int64_t lo = 0, hi = c.list_n - 1;
-      while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) / 2;
-        if (c.seg_start[mid] <= item) lo = mid;
-        else hi = mid - 1;
+  const int64_t ib = c.bpos ? c.hs_pre[c.boff[c.s]] : 0;
+  const int64_t ie = c.bpos ? c.hs_pre[c.boff[c.s + 1]] : c.n_segs;
+  for (int64_t item = ib + blockIdx.x; item < ie; item += gridDim.x) {
+    int64_t i, sg;
+    if (c.bpos) {
+      const int64_t it = c.hs_item[item];
+      i = it >> 32;
+      sg = it & 0xffffffffLL;
+    } else {
+      if (threadIdx.x == 0) {  // vertex index: last i with seg_start[i] <= item
+        int64_t lo = 0, hi = c.list_n - 1;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi + 1) / 2;
+          if (c.seg_start[mid] <= item) lo = mid;
+          else hi = mid - 1;
+        }
+        s_vi = lo;
       }
-      s_vi = lo;
+      __syncthreads();
+      i = s_vi;
+      sg = item - c.seg_start[i];
+      __syncthreads();
     }
-    __syncthreads();
-    const int64_t i = s_vi;
-    __syncthreads();
     const int64_t u = c.list[i];
-    if (!active<MODE>(c, u)) continue;
+    if (!c.bpos && !active<MODE>(c, u)) continue;
     const int32_t own = c.label[u];
     const int64_t cu = node_w(c.g, u);
     const uint64_t hv = tie_key<MODE>(c, u);
@@ -1259,7 +1314,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_huge_scan(RateCtx c, Bes
     // list entries per segment)
     const int64_t filled = c.tcount[i], cap = (int64_t)1 << c.tcap[i];
     const bool dense = 8 * filled >= cap;
-    const int64_t s0 = (item - c.seg_start[i]) << kSegLog;
+    const int64_t s0 = sg << kSegLog;
     const int64_t s1 = dense ? min(2 * (s0 + ((int64_t)1 << kSegLog)), cap)
                              : min(s0 + ((int64_t)1 << kSegLog), filled);
     int32_t *tk = c.tkeys + c.tbase + c.toff[i];
@@ -1286,9 +1341,10 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_huge_scan(RateCtx c, Bes
     }
     block_reduce_best(b, wb);
     if (MODE != M_FAV) block_reduce_best(a, wb);
-    if (threadIdx.x == 0) {
-      seg_best[2 * item] = b;
-      seg_best[2 * item + 1] = a;
+    if (threadIdx.x == 0) {  // the hub's segment sg, where the decision reads it
+      const int64_t q = c.seg_start[i] + sg;
+      seg_best[2 * q] = b;
+      seg_best[2 * q + 1] = a;
     }
   }
 }
@@ -1301,9 +1357,11 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_huge_decide(RateCtx c, c
   __shared__ Best wb[kBlockThreads / 32];
   __shared__ int32_t mu[32], mt[32], mo[32];
   __shared__ int64_t mg[32];
-  for (int64_t i = blockIdx.x; i < c.list_n; i += gridDim.x) {
-    int64_t u = c.list[i];
-    if (!active<MODE>(c, u)) continue;
+  int64_t kb, ke;
+  tier_range(c, kb, ke);
+  for (int64_t k = kb + blockIdx.x; k < ke; k += gridDim.x) {
+    int64_t i, u;
+    if (!tier_entry<MODE>(c, k, i, u)) continue;
     const int64_t cu = node_w(c.g, u);
     Best b, a;
     b.init();
@@ -1549,6 +1607,17 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
   const int sms = num_sms();
   const bool comp = g->compressed;
   const bool prof = MODE == M_LP && prof_active();
+  // bucket mode (M_LP with this round's tier buckets): tier t walks its
+  // sub-round's positions only
+  auto bucketed = [&](RateCtx &m, int t) {
+    if (MODE == M_LP && c.tb_pos) {
+      m.bpos = c.tb_pos + c.tb_base[t];
+      m.boff = c.tb_off + (int64_t)t * (c.S + 1);
+    } else {
+      m.bpos = nullptr;
+      m.boff = nullptr;
+    }
+  };
   const double per_launch = MODE == M_LP && c.S > 0 ? 1.0 / c.S : 0.0;
   const int64_t n_lane = MODE == M_REBAL ? 0 : T.count[TIER_LANE];
   const int64_t n_small = T.count[TIER_SMALL] + (MODE == M_REBAL ? T.count[TIER_LANE] : 0);
@@ -1580,6 +1649,7 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
       m.list = T.small.get();
       m.list_n = T.n_small;
       items = T.n_small;
+      bucketed(m, 0);
     } else {
       m.list = nullptr;
     }
@@ -1596,6 +1666,7 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
     RateCtx m = c;
     m.list = T.mid.get();
     m.list_n = T.n_mid;
+    bucketed(m, 1);
     size_t sm = sizeof(WarpSmem<kMidLog>) * kMidWarps;
     unsigned blocks = (unsigned)std::min<int64_t>((T.n_mid + kMidWarps - 1) / kMidWarps, (int64_t)sms * 8);
     if (comp) launch(k_rate_list<true, MODE, false>, blocks, 32 * kMidWarps, sm, s, m);
@@ -1606,11 +1677,12 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
   if (T.n_big + T.n_big2 > 0) {
     if (prof) prof_begin(PF_RATE_BIG, s);
     const bool wt = !g->unit_ew;
-    auto run = [&](const int32_t *list, int64_t cnt, int maxlog) {
+    auto run = [&](const int32_t *list, int64_t cnt, int maxlog, int t) {
       if (!cnt) return;
       RateCtx m = c;
       m.list = list;
       m.list_n = cnt;
+      bucketed(m, t);
       const size_t sm = ((size_t)1 << maxlog) * (sizeof(int32_t) + (wt ? 8 : 4)) +
                         (comp ? block_stage_bytes(block_max_deg(maxlog)) +
                                     block_vbuf_bytes(block_max_deg(maxlog))
@@ -1624,8 +1696,8 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
 #undef TP_BLK
       TP_LAUNCH_CHECK();
     };
-    run(T.big.get(), T.n_big, kBlockSmallLog);
-    run(T.big2.get(), T.n_big2, kBlockBigLog);
+    run(T.big.get(), T.n_big, kBlockSmallLog, 2);
+    run(T.big2.get(), T.n_big2, kBlockBigLog, 3);
     if (prof) prof_end(PF_RATE_BIG, s, per_launch * tier_round_bytes(g, T.n_big + T.n_big2, T.edges[TIER_BIG]));
   }
   if (T.n_huge > 0) {
@@ -1633,6 +1705,7 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
     RateCtx m = c;
     m.list = T.huge.get();
     m.list_n = T.n_huge;
+    bucketed(m, 4);
     m.toff = T.huge_toff.get();
     m.tcap = T.huge_tcap.get();
     m.tbase = 0;
@@ -1799,10 +1872,143 @@ __global__ void __launch_bounds__(256) k_bucket(const uint8_t *tier, int64_t n, 
   }
 }
 
+// Tier buckets: count a list's vertices per sub-round (from sub_byte).
+__global__ void k_tier_count(const int32_t *list, int64_t n, const uint8_t *sub_byte, int32_t S,
+                             int64_t *cnt) {
+  __shared__ int32_t sc[32];
+  if (threadIdx.x < 32) sc[threadIdx.x] = 0;
+  __syncthreads();
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&sc[sub_byte[list[k]] - 1], 1);
+  __syncthreads();
+  if (threadIdx.x < S && sc[threadIdx.x])
+    atomicAdd((unsigned long long *)&cnt[threadIdx.x], (unsigned long long)sc[threadIdx.x]);
+}
+
+// Offsets of every tier's sub-rounds (one block): off[t * (S + 1) + s].
+__global__ void k_tier_offsets(const int64_t *cnt, int32_t S, int tiers, int64_t *off, int64_t *cur) {
+  if (threadIdx.x >= tiers) return;
+  const int t = threadIdx.x;
+  int64_t run = 0;
+  for (int s = 0; s < S; ++s) {
+    const int64_t c = cnt[t * S + s];  // cnt and cur may be the same array
+    off[t * (S + 1) + s] = run;
+    cur[t * S + s] = run;
+    run += c;
+  }
+  off[t * (S + 1) + S] = run;
+}
+
+// Scatters a list's positions into its sub-round buckets: each block counts
+// its slice per sub-round, reserves the ranges with one atomic each, then
+// places its entries (the order inside a bucket does not matter).
+constexpr int kTierSlice = 4096;
+__global__ void k_tier_scatter(const int32_t *list, int64_t n, const uint8_t *sub_byte, int32_t S,
+                               int64_t *cur, int32_t *pos) {
+  __shared__ int32_t sc[32];
+  __shared__ int64_t base[32];
+  for (int64_t lo = (int64_t)blockIdx.x * kTierSlice; lo < n; lo += (int64_t)gridDim.x * kTierSlice) {
+    const int64_t hi = min(lo + kTierSlice, n);
+    if (threadIdx.x < 32) sc[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) atomicAdd(&sc[sub_byte[list[k]] - 1], 1);
+    __syncthreads();
+    if (threadIdx.x < S) {
+      base[threadIdx.x] = sc[threadIdx.x]
+                              ? (int64_t)atomicAdd((unsigned long long *)&cur[threadIdx.x],
+                                                   (unsigned long long)sc[threadIdx.x])
+                              : 0;
+      sc[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+      const int s = sub_byte[list[k]] - 1;
+      pos[base[s] + atomicAdd(&sc[s], 1)] = (int32_t)k;
+    }
+    __syncthreads();
+  }
+}
+
+// Huge tier: chunk and segment counts of the hubs in bucket order.
+__global__ void k_huge_counts(const int32_t *bpos, int64_t nh, const int64_t *chunk_start,
+                              const int64_t *seg_start, int64_t *hc, int64_t *hs) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nh;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = bpos[k];
+    hc[k] = chunk_start[p + 1] - chunk_start[p];
+    hs[k] = seg_start[p + 1] - seg_start[p];
+  }
+}
+
+// Huge tier: the items of every hub (warp per hub), hub position << 32 | index.
+__global__ void k_huge_items(const int32_t *bpos, int64_t nh, const int64_t *pre,
+                             int64_t *item) {
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t k = gw; k < nh; k += nw) {
+    const int64_t p = bpos[k];
+    for (int64_t j = pre[k] + lane_id(); j < pre[k + 1]; j += 32) item[j] = p << 32 | (j - pre[k]);
+  }
+}
+
 }  // namespace
 
+// Buckets the warp and block tiers' lists of this round by sub-round.
+static void tier_buckets(tp_graph *g, LpWork &w, int32_t S, cudaStream_t stream) {
+  TierCache &T = g->tiers;
+  const int32_t *lists[LpWork::kTiers] = {T.small.get(), T.mid.get(), T.big.get(), T.big2.get(),
+                                          T.huge.get()};
+  const int64_t lens[LpWork::kTiers] = {T.n_small, T.n_mid, T.n_big, T.n_big2, T.n_huge};
+  int64_t total = 0;
+  for (int t = 0; t < LpWork::kTiers; ++t) w.tb_base[t] = total, total += lens[t];
+  w.tb_valid = false;
+  if (total == 0) return;
+  if ((int64_t)w.tb_pos.n < total) w.tb_pos.alloc(total, stream);
+  if ((int64_t)w.tb_off.n < LpWork::kTiers * 33) {
+    w.tb_off.alloc(LpWork::kTiers * 33, stream);
+    w.tb_cur.alloc(LpWork::kTiers * 32, stream);
+  }
+  TP_CUDA(cudaMemsetAsync(w.tb_cur.get(), 0, sizeof(int64_t) * LpWork::kTiers * S, stream));
+  const int sms = num_sms();
+  for (int t = 0; t < LpWork::kTiers; ++t)
+    if (lens[t])
+      launch(k_tier_count, grid_for(lens[t], 256, (int64_t)sms * 4), 256, 0, stream, lists[t],
+             lens[t], w.bucket_sub.get(), S, w.tb_cur.get() + (int64_t)t * S);
+  launch(k_tier_offsets, 1, 32, 0, stream, w.tb_cur.get(), S, LpWork::kTiers, w.tb_off.get(),
+         w.tb_cur.get());
+  for (int t = 0; t < LpWork::kTiers; ++t)
+    if (lens[t])
+      launch(k_tier_scatter, grid_for(lens[t], kTierSlice, (int64_t)sms * 4), 256, 0, stream,
+             lists[t], lens[t], w.bucket_sub.get(), S, w.tb_cur.get() + (int64_t)t * S,
+             w.tb_pos.get() + w.tb_base[t]);
+  TP_LAUNCH_CHECK();
+  if (T.n_huge) {
+    const int64_t nh = T.n_huge;
+    if ((int64_t)w.hc_pre.n < nh + 1) {
+      w.hc_pre.alloc(nh + 1, stream);
+      w.hs_pre.alloc(nh + 1, stream);
+    }
+    if ((int64_t)w.hc_item.n < std::max<int64_t>(T.n_huge_chunks, 1))
+      w.hc_item.alloc(std::max<int64_t>(T.n_huge_chunks, 1), stream);
+    if ((int64_t)w.hs_item.n < std::max<int64_t>(T.n_huge_segs, 1))
+      w.hs_item.alloc(std::max<int64_t>(T.n_huge_segs, 1), stream);
+    const int32_t *hp = w.tb_pos.get() + w.tb_base[4];
+    launch(k_huge_counts, grid_for(nh, 256), 256, 0, stream, hp, nh, T.huge_chunk_start.get(),
+           T.huge_seg_start.get(), w.hc_pre.get(), w.hs_pre.get());
+    exclusive_scan_i64(w.hc_pre.get(), w.hc_pre.get(), nh, stream);
+    exclusive_scan_i64(w.hs_pre.get(), w.hs_pre.get(), nh, stream);
+    launch(k_huge_items, grid_for(nh * 32, 256), 256, 0, stream, hp, nh, w.hc_pre.get(),
+           w.hc_item.get());
+    launch(k_huge_items, grid_for(nh * 32, 256), 256, 0, stream, hp, nh, w.hs_pre.get(),
+           w.hs_item.get());
+    TP_LAUNCH_CHECK();
+  }
+  w.tb_valid = true;
+}
+
 void lp_bucket(tp_graph *g, LpWork &w, uint64_t rk, int32_t S, const tp_params &p,
-               cudaStream_t stream, const uint64_t *rk_dev) {
+               cudaStream_t stream, const uint64_t *rk_dev, bool tiers) {
   build_tiers(g, p, stream);
   w.bucket_S = 0;
   if (S > 32) return;
@@ -1823,6 +2029,8 @@ void lp_bucket(tp_graph *g, LpWork &w, uint64_t rk, int32_t S, const tp_params &
   TP_LAUNCH_CHECK();
   w.bucket_S = S;
   w.bucket_nblocks = nblocks;
+  w.tb_valid = false;
+  if (tiers) tier_buckets(g, w, S, stream);
 }
 
 void LpWork::init(int64_t n_vertices, int64_t n_labels, cudaStream_t s) {
@@ -1929,6 +2137,15 @@ void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t
     c.bucket_nb = w.bucket_nblocks;
     c.bucket_rec = g->compressed ? w.bucket_rec.get() : nullptr;
     c.sub_byte = w.bucket_sub.get();
+    if (w.tb_valid) {
+      c.tb_pos = w.tb_pos.get();
+      c.tb_off = w.tb_off.get();
+      for (int t = 0; t < LpWork::kTiers; ++t) c.tb_base[t] = w.tb_base[t];
+      c.hc_pre = w.hc_pre.get();
+      c.hs_pre = w.hs_pre.get();
+      c.hc_item = w.hc_item.get();
+      c.hs_item = w.hs_item.get();
+    }
   }
   rate_tiers<M_LP>(g, c, p, stream);
   prof_begin(PF_APPROVE, stream);
@@ -2022,15 +2239,16 @@ bool lp_rounds_graph(tp_graph *g, const LpState &st, LpWork &w, uint64_t seed, u
 void lp_rounds(tp_graph *g, const LpState &st, LpWork &w, uint64_t seed, uint64_t tag, uint64_t a,
                uint64_t b0, int32_t rounds, int32_t S, const tp_params &p, cudaStream_t stream) {
   if (rounds <= 0) return;
-  if (g->n <= kRoundGraphMaxN && !prof_active() &&
+  if (p.use_graphs && g->n <= std::min<int64_t>(p.graph_n, kRoundGraphMaxN) && !prof_active() &&
       lp_rounds_graph(g, st, w, seed, tag, a, b0, rounds, S, p, stream))
     return;
   ApprovalGraph ag(approve_ctx(g, st, w), w.n, w.counters.get());
   for (int32_t r = 0; r < rounds; ++r) {
     uint64_t rk = round_key(seed, tag, a, b0 + (uint64_t)r);
-    lp_bucket(g, w, rk, S, p, stream);
+    lp_bucket(g, w, rk, S, p, stream, nullptr, true);
     for (int32_t s = 0; s < S; ++s) lp_subround(g, st, w, rk, S, s, p, stream, ag.exec);
     w.bucket_S = 0;
+    w.tb_valid = false;
   }
 }
 

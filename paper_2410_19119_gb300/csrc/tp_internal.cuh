@@ -381,6 +381,18 @@ struct LpWork {
   Buf<int64_t> bucket_off;   // S * nblocks + 1 offsets (sub-round major)
   int64_t bucket_nblocks = 0;
   int32_t bucket_S = 0;      // S of the current buckets (0: none)
+  // the other tiers' lists (small, mid, big, big2, huge) grouped by sub-round:
+  // tb_pos holds list positions, tb_off[t * (S + 1) + s] where sub-round s of
+  // tier t starts in tb_pos (tier t's entries begin at tb_base[t])
+  static constexpr int kTiers = 5;
+  Buf<int32_t> tb_pos;       // sum of the tier list lengths
+  Buf<int64_t> tb_off;       // kTiers * (S + 1)
+  Buf<int64_t> tb_cur;       // kTiers * S cursors
+  int64_t tb_base[kTiers] = {0, 0, 0, 0, 0};
+  bool tb_valid = false;
+  // huge tier, in bucket order of its hubs: prefix of chunk and segment
+  // counts (n_huge + 1) and the items themselves (hub position << 32 | index)
+  Buf<int64_t> hc_pre, hs_pre, hc_item, hs_item;
   void init(int64_t n_vertices, int64_t n_labels, cudaStream_t s);
 };
 // approval (nullable): a CUDA graph of this level's approval kernels to
@@ -388,9 +400,10 @@ struct LpWork {
 void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t S, int32_t s,
                  const tp_params &p, cudaStream_t stream, cudaGraphExec_t approval = nullptr,
                  const uint64_t *rk_dev = nullptr);
-// Buckets the lane-tier vertices of round key rk by sub-round (A3).
+// Buckets the lane-tier vertices of round key rk by sub-round (A3), and with
+// tiers = true also the other tiers' lists (not inside a stream capture).
 void lp_bucket(tp_graph *g, LpWork &w, uint64_t rk, int32_t S, const tp_params &p,
-               cudaStream_t stream, const uint64_t *rk_dev = nullptr);
+               cudaStream_t stream, const uint64_t *rk_dev = nullptr, bool tiers = false);
 void lp_rounds(tp_graph *g, const LpState &st, LpWork &w, uint64_t seed, uint64_t tag, uint64_t a,
                uint64_t b0, int32_t rounds, int32_t S, const tp_params &p, cudaStream_t stream);
 // ev_begin / ev_end (nullable) are recorded around the LP rounds alone.

@@ -35,6 +35,33 @@ def _star_path(leaves=25000):
     return xadj, np.array(adj, np.int32)
 
 
+def _multi_star(hubs=4, leaves=10500):
+    # several hubs above the chunking threshold (huge tier, each in its own
+    # sub-round most of the time), their leaves on one path, hubs in a clique
+    n = hubs * (leaves + 1)
+    nb = [set() for _ in range(n)]
+
+    def link(a, b):
+        nb[a].add(b)
+        nb[b].add(a)
+
+    for h in range(hubs):
+        base = h * (leaves + 1)
+        for v in range(base + 1, base + leaves + 1):
+            link(base, v)
+        for h2 in range(h + 1, hubs):
+            link(base, h2 * (leaves + 1))
+    leaves_all = [v for v in range(n) if v % (leaves + 1) != 0]
+    for a, b in zip(leaves_all[:-1], leaves_all[1:]):
+        link(a, b)
+    xadj = np.zeros(n + 1, np.int64)
+    adj = []
+    for u in range(n):
+        adj += sorted(nb[u])
+        xadj[u + 1] = len(adj)
+    return xadj, np.array(adj, np.int32)
+
+
 GRAPHS = {
     "gnm": lambda: synth.gnm(3000, 24000, 3),
     "rgg": lambda: synth.rgg2d(5000, 16.0, 2),
@@ -333,6 +360,45 @@ def test_degree_boundaries(compressed):
     g.check()
 
 
+@pytest.mark.parametrize("compressed", [False, True])
+def test_direct_rounds_with_several_hubs(compressed):
+    """Several chunked hubs rated in sub-round buckets (their chunk and table
+    segment items listed per round) against the oracle."""
+    xadj, adj = _multi_star()
+    og = oracle.Graph(xadj, adj)
+    g = tp.graph_from_csr(xadj, adj)
+    if compressed:
+        g = g.compress()
+    for use_graphs in (0, 1):
+        p = tp.default_params(seed=3, use_graphs=use_graphs)
+        want = oracle.cluster(og, 40, oracle.Params(seed=3), 0)
+        assert np.array_equal(_host(tp.lp_cluster(g, 40, p, 0)), want), use_graphs
+        want, wst = oracle.partition(og, 6, 0.03, oracle.Params(seed=3))
+        part, st = tp.partition(g, 6, 0.03, p)
+        assert np.array_equal(_host(part), want) and st["cut"] == wst["cut"], use_graphs
+    g.check()
+
+
+@pytest.mark.parametrize("compressed", [False, True])
+def test_direct_rounds_equal_oracle(graph, compressed):
+    """Rounds launched kernel by kernel (as on levels above 2^19 vertices,
+    with every tier's vertices bucketed by sub-round once per round) give the
+    same clustering and partition as the oracle; use_graphs = 0 forces that
+    path on these small graphs."""
+    name, xadj, adj = graph
+    og = oracle.Graph(xadj, adj)
+    g = tp.graph_from_csr(xadj, adj)
+    if compressed:
+        g = g.compress()
+    p = tp.default_params(seed=5, use_graphs=0)
+    want = oracle.cluster(og, 30, oracle.Params(seed=5), 0)
+    assert np.array_equal(_host(tp.lp_cluster(g, 30, p, 0)), want), name
+    want, wst = oracle.partition(og, 8, 0.03, oracle.Params(seed=5))
+    part, st = tp.partition(g, 8, 0.03, p)
+    assert np.array_equal(_host(part), want) and st["cut"] == wst["cut"], name
+    g.check()
+
+
 def test_performance_knobs_do_not_change_results():
     xadj, adj = synth.rmat(14, 16, seed=6)
     og = oracle.Graph(xadj, adj)
@@ -344,7 +410,8 @@ def test_performance_knobs_do_not_change_results():
         p = tp.default_params(seed=9, tier_lane=int(rng.choice([0, 8, 16, 32])),
                               tier_small=int(rng.choice([1, 16, 32, 64])),
                               tier_mid=int(rng.choice([64, 200, 1000])),
-                              warps_per_block=int(rng.choice([2, 4, 8, 16])))
+                              warps_per_block=int(rng.choice([2, 4, 8, 16])),
+                              use_graphs=int(rng.choice([0, 1])))
         for gg in (g, z):
             part, _ = tp.partition(gg, 12, 0.03, p)
             assert np.array_equal(_host(part), want), trial
