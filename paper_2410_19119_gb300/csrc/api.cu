@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <memory>
 #include <mutex>
 #include <system_error>
 #include <thread>
@@ -22,6 +23,9 @@ void export_csr(const tp_graph *g, int64_t *xadj, int32_t *adj, int64_t *vw, int
 void export_compressed(const tp_graph *g, uint8_t *bytes, uint64_t *off, cudaStream_t s);
 void partition(tp_graph *g0, int32_t k, int64_t eps_ppm, const tp_params &p, int32_t *d_part,
                tp_stats *st, cudaStream_t s);
+void partition_union(const std::vector<const tp_graph *> &gs, const std::vector<int32_t> &idx,
+                     const int32_t *k, int64_t eps_ppm, const tp_params &p,
+                     int32_t *const *d_part, tp_stats *stats, cudaStream_t s);
 
 namespace {
 void pool_setup_once() {
@@ -272,12 +276,13 @@ tp_status tp_partition(const tp_graph *g, int32_t k, double eps, const tp_params
   });
 }
 
-// Batched mode: many independent graphs overlap on the device. Every graph
-// runs exactly the tp_partition path on a stream of its worker, so each
-// result is bit-identical to partitioning that graph alone; only the
-// scheduling differs. `concurrency` host workers each own a CUDA stream and
-// take the next graph from a shared counter, largest graphs first so the
-// batch does not end on one big straggler.
+// Batched mode: the graphs are partitioned together, one union graph per
+// level (batch.cu), so kernels are launched per level rather than per graph
+// and every graph's result equals tp_partition of that graph alone. Graphs
+// with k = 1 or no vertices are trivial; compressed inputs are decompressed
+// first (the result does not depend on the representation). Large batches
+// are cut into groups (in input order) that bound a union's size; up to
+// `concurrency` groups run at once, each on a stream of its own worker.
 tp_status tp_partition_batch(int32_t count, tp_graph *const *graphs, const int32_t *k, double eps,
                              const tp_params *p, int32_t *const *d_part, tp_stats *stats,
                              tp_status *status, int32_t concurrency) {
@@ -298,43 +303,93 @@ tp_status tp_partition_batch(int32_t count, tp_graph *const *graphs, const int32
     return e.code;
   }
   const int64_t eps_ppm = eps_ppm_of(eps);
-  std::vector<int32_t> order((size_t)count);
-  for (int32_t i = 0; i < count; ++i) order[(size_t)i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-    return graphs[a]->n + graphs[a]->m2 > graphs[b]->n + graphs[b]->m2;
-  });
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return TP_ERR_CUDA;
   std::vector<tp_status> st((size_t)count, TP_OK);
+  // groups of non-trivial graphs in input order, each a union of bounded size
+  // (graphs of a union are one grid row each: at most 2^15 per group)
+  constexpr int64_t kGroupN = (int64_t)1 << 28, kGroupM = (int64_t)1 << 30, kGroupG = 1 << 15;
+  std::vector<std::vector<int32_t>> groups;
+  std::vector<int32_t> trivial;
+  {
+    int64_t gn = 0, gm = 0;
+    for (int32_t i = 0; i < count; ++i) {
+      const tp_graph *g = graphs[i];
+      if (k[i] == 1 || g->n == 0) {
+        trivial.push_back(i);
+        continue;
+      }
+      if (groups.empty() || gn + g->n > kGroupN || gm + g->m2 > kGroupM ||
+          (int64_t)groups.back().size() == kGroupG) {
+        groups.emplace_back();
+        gn = gm = 0;
+      }
+      groups.back().push_back(i);
+      gn += g->n;
+      gm += g->m2;
+    }
+  }
+  std::vector<const tp_graph *> gs(graphs, graphs + count);
   std::atomic<int32_t> next{0};
-  auto worker = [&] {
+  const int32_t ngroups = (int32_t)groups.size();
+  auto worker = [&](bool first) {
     cudaStream_t s = nullptr;
     if (cudaSetDevice(dev) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
       (void)cudaGetLastError();
-      for (int32_t i; (i = next.fetch_add(1)) < count;) st[(size_t)order[(size_t)i]] = TP_ERR_CUDA;
+      for (int32_t t; (t = next.fetch_add(1)) < ngroups;)
+        for (int32_t i : groups[(size_t)t]) st[(size_t)i] = TP_ERR_CUDA;
       return;
     }
-    for (int32_t i; (i = next.fetch_add(1)) < count;) {
-      const int32_t g = order[(size_t)i];
-      st[(size_t)g] = guard([&] {
-        partition(graphs[g], k[g], eps_ppm, q, d_part[g], stats ? &stats[g] : nullptr, s);
+    if (first) {  // trivial graphs: every vertex in block 0
+      for (int32_t i : trivial) {
+        st[(size_t)i] = guard([&] {
+          const tp_graph *g = graphs[i];
+          if (g->n) TP_CUDA(cudaMemsetAsync(d_part[i], 0, g->n * sizeof(int32_t), s));
+          if (stats) {
+            tp_stats &S = stats[i];
+            S = tp_stats{};
+            S.l_max = block_cap(g->total_vw, k[i], eps_ppm);
+            S.u_max = cluster_cap(g->total_vw, k[i], eps_ppm);
+            S.levels = 1;
+            S.level_n[0] = g->n;
+            S.level_m2[0] = g->m2;
+            S.max_block_weight = k[i] == 1 ? g->total_vw : 0;
+            S.balanced = S.max_block_weight <= S.l_max;
+            const int64_t perfect = (g->total_vw + k[i] - 1) / k[i];
+            S.imbalance = perfect > 0 ? (double)S.max_block_weight / (double)perfect - 1.0 : 0.0;
+          }
+        });
+      }
+    }
+    for (int32_t t; (t = next.fetch_add(1)) < ngroups;) {
+      const std::vector<int32_t> &grp = groups[(size_t)t];
+      tp_status r = guard([&] {
+        std::vector<const tp_graph *> local = gs;
+        std::vector<std::unique_ptr<tp_graph>> tmp;  // CSR copies of compressed inputs
+        for (int32_t i : grp)
+          if (graphs[i]->compressed) {
+            tmp.emplace_back(decompress(graphs[i], s));
+            local[(size_t)i] = tmp.back().get();
+          }
+        partition_union(local, grp, k, eps_ppm, q, d_part, stats, s);
+        TP_CUDA(cudaStreamSynchronize(s));
       });
+      for (int32_t i : grp) st[(size_t)i] = r;
     }
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
   };
-  const int32_t nthreads = std::min(concurrency, std::min(count, 256));
+  const int32_t nthreads = std::max(1, std::min(concurrency, std::min(ngroups, 64)));
   std::vector<std::thread> pool;
-  pool.reserve((size_t)nthreads - 1);
   for (int32_t t = 1; t < nthreads; ++t) {
     try {
-      pool.emplace_back(worker);
+      pool.emplace_back(worker, false);
     } catch (const std::system_error &) {
-      break;  // fewer threads: the shared counter still hands out every graph
+      break;  // fewer threads: the shared counter still hands out every group
     }
   }
-  worker();
+  worker(true);
   for (std::thread &t : pool) t.join();
   tp_status first = TP_OK;
   for (int32_t i = 0; i < count; ++i) {

@@ -32,6 +32,13 @@ __global__ void k_map(const int32_t *C, const int64_t *rank, const int64_t *vw, 
   }
 }
 
+// Batched graphs: coarse offset of every graph (the rank of its first vertex).
+__global__ void k_seg_rank(const int64_t *rank, const int64_t *voff, int64_t nseg, int64_t *coff) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= nseg;
+       i += (int64_t)gridDim.x * blockDim.x)
+    coff[i] = rank[voff[i]];
+}
+
 __device__ __forceinline__ bool thread_tier(uint8_t t) { return t == TIER_LANE || t == TIER_SMALL; }
 
 // Per-vertex count of inter-cluster entries, one thread per low-degree vertex.
@@ -175,7 +182,8 @@ __global__ void k_reduce(const uint64_t *keys, const uint64_t *vals, const int64
 
 }  // namespace
 
-tp_graph *contract(const tp_graph *g, const int32_t *C, int32_t *d_map, cudaStream_t s) {
+tp_graph *contract(const tp_graph *g, const int32_t *C, int32_t *d_map, cudaStream_t s,
+                   const int64_t *seg_voff, int64_t nseg, int64_t *seg_coff) {
   int64_t n = g->n;
   tp_graph *cg = new_graph();
   try {
@@ -195,6 +203,10 @@ tp_graph *contract(const tp_graph *g, const int32_t *C, int32_t *d_map, cudaStre
     TP_LAUNCH_CHECK();
     Buf<int64_t> rank(n + 1, s);
     exclusive_scan_i32_to_i64(flag.get(), rank.get(), n, s);
+    if (seg_voff) {
+      launch(k_seg_rank, grid_for(nseg + 1, 256), 256, 0, s, rank.get(), seg_voff, nseg, seg_coff);
+      TP_LAUNCH_CHECK();
+    }
     int64_t nc = read_scalar(rank.get() + n, s);
     cg->n = nc;
     Buf<int32_t> own_map;

@@ -14,7 +14,9 @@
 //      kk0 * L_max and kk1 * L_max and the same prefix approval as k-way LP;
 //   4. the cut of the induced subgraph.
 // The attempt with the smallest cut (lowest attempt on ties) wins; the tree
-// is processed depth by depth, all nodes of a depth in one launch.
+// is processed depth by depth, all nodes of a depth in one launch. Batched
+// graphs form a forest: every graph's root carries the hash key offset and
+// L_max its graph would use alone, so each tree's result is that graph's.
 #include <algorithm>
 #include <vector>
 
@@ -41,9 +43,10 @@ struct IPCtx {
   const int32_t *ladj;
   const int64_t *lew;  // null: unit
   const int32_t *noff, *nkk;
+  const int32_t *nkey;    // per node: the block offset its graph alone would give it (hash key)
+  const int64_t *nlmax;  // per node: its graph's L_max
   int32_t T;
   uint64_t seed;
-  int64_t l_max;
   int32_t rounds, S;
   // scratch, T * n entries each
   int32_t *ord, *disc, *claimer, *cnt, *side, *mvx0, *mvx1, *ok0, *ok1;
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(kIPThreads, 1) k_bisect(IPCtx c) {
   uint8_t *sub = c.sub + R;
   const int32_t *vs = c.vlist + nb;
   const int32_t kk = c.nkk[j], k0 = (kk + 1) / 2, k1 = kk / 2;
-  const uint64_t key = ((uint64_t)(uint32_t)c.noff[j] << 32) | (uint32_t)kk;
+  const uint64_t key = ((uint64_t)(uint32_t)c.nkey[j] << 32) | (uint32_t)kk;
   const int lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   auto cw = [&](int64_t x) -> int64_t { return c.vw ? c.vw[vs[x]] : 1; };
   if (ns == 0) {
@@ -300,7 +303,7 @@ __global__ void __launch_bounds__(kIPThreads, 1) k_bisect(IPCtx c) {
   for (int64_t x = threadIdx.x; x < ns; x += blockDim.x) W += cw(x);
   W = bsum(W);
   const int64_t target0 = (int64_t)(((__int128)W * k0) / kk);
-  const int64_t caps[2] = {(int64_t)k0 * c.l_max, (int64_t)k1 * c.l_max};
+  const int64_t caps[2] = {(int64_t)k0 * c.nlmax[j], (int64_t)k1 * c.nlmax[j]};
   {
     int64_t carry = 0, w0 = 0;
     for (int64_t q0 = 0; q0 < ns; q0 += blockDim.x) {
@@ -466,18 +469,39 @@ void initial_partition(const tp_graph *g, int32_t k, int64_t l_max, const tp_par
   TP_REQUIRE(!g->compressed, TP_ERR_INVALID);
   const int64_t n = g->n;
   if (n == 0) return;
+  if (k <= 1) {
+    launch(k_fill_i32, grid_for(n, 256), 256, 0, s, d_part, n, 0);
+    TP_LAUNCH_CHECK();
+    return;
+  }
+  initial_partition_roots(g, {IPRoot{0, 0, k, l_max}}, nullptr, p, d_part, s);
+}
+
+void initial_partition_roots(const tp_graph *g, const std::vector<IPRoot> &roots,
+                             const int32_t *d_node_of, const tp_params &p, int32_t *d_part,
+                             cudaStream_t s) {
+  TP_REQUIRE(!g->compressed, TP_ERR_INVALID);
+  const int64_t n = g->n;
+  if (n == 0 || roots.empty()) return;
   launch(k_fill_i32, grid_for(n, 256), 256, 0, s, d_part, n, 0);
   TP_LAUNCH_CHECK();
-  if (k <= 1) return;
   const int32_t T = std::max(1, p.ip_attempts);
   Buf<int32_t> node_of(n, s), next_node(n, s), vlist(n, s), loc(n, s);
-  launch(k_fill_i32, grid_for(n, 256), 256, 0, s, node_of.get(), n, 0);
+  if (d_node_of)
+    TP_CUDA(cudaMemcpyAsync(node_of.get(), d_node_of, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  else
+    launch(k_fill_i32, grid_for(n, 256), 256, 0, s, node_of.get(), n, 0);
   Buf<int32_t> ord(T * n, s), disc(T * n, s), claimer(T * n, s), cnt(T * n, s), side(T * n, s),
       mvx0(T * n, s), mvx1(T * n, s), ok0(T * n, s), ok1(T * n, s);
   Buf<int64_t> mvg0(T * n, s), mvg1(T * n, s);
   Buf<uint8_t> sub(T * n, s);
   Buf<uint64_t> keys(n, s);
-  std::vector<int32_t> off = {0}, kks = {k};
+  std::vector<int32_t> off, kks, hkey;
+  std::vector<int64_t> lmx;
+  for (const IPRoot &r : roots) {
+    TP_REQUIRE(r.k >= 2, TP_ERR_INVALID);
+    off.push_back(r.off), kks.push_back(r.k), hkey.push_back(r.key), lmx.push_back(r.l_max);
+  }
   while (!off.empty()) {
     const int32_t nodes = (int32_t)off.size();
     // vertex lists per node
@@ -512,18 +536,33 @@ void initial_partition(const tp_graph *g, int32_t k, int64_t l_max, const tp_par
       TP_LAUNCH_CHECK();
     }
     // children of every node at the next depth (-1: leaf, assign the block)
-    std::vector<int32_t> c0(nodes), c1(nodes), noff, nkk;
+    std::vector<int32_t> c0(nodes), c1(nodes), noff, nkk, nkey;
+    std::vector<int64_t> nlmx;
     for (int32_t jn = 0; jn < nodes; ++jn) {
       int32_t k0 = (kks[jn] + 1) / 2, k1 = kks[jn] / 2;
       c0[jn] = -1, c1[jn] = -1;
-      if (k0 >= 2) c0[jn] = (int32_t)noff.size(), noff.push_back(off[jn]), nkk.push_back(k0);
-      if (k1 >= 2) c1[jn] = (int32_t)noff.size(), noff.push_back(off[jn] + k0), nkk.push_back(k1);
+      if (k0 >= 2) {
+        c0[jn] = (int32_t)noff.size();
+        noff.push_back(off[jn]), nkk.push_back(k0), nkey.push_back(hkey[jn]), nlmx.push_back(lmx[jn]);
+      }
+      if (k1 >= 2) {
+        c1[jn] = (int32_t)noff.size();
+        noff.push_back(off[jn] + k0), nkk.push_back(k1), nkey.push_back(hkey[jn] + k0);
+        nlmx.push_back(lmx[jn]);
+      }
     }
-    Buf<int32_t> d_off(nodes, s), d_kk(nodes, s), d_c0(nodes, s), d_c1(nodes, s);
-    TP_CUDA(cudaMemcpyAsync(d_off.get(), off.data(), nodes * 4, cudaMemcpyHostToDevice, s));
-    TP_CUDA(cudaMemcpyAsync(d_kk.get(), kks.data(), nodes * 4, cudaMemcpyHostToDevice, s));
-    TP_CUDA(cudaMemcpyAsync(d_c0.get(), c0.data(), nodes * 4, cudaMemcpyHostToDevice, s));
-    TP_CUDA(cudaMemcpyAsync(d_c1.get(), c1.data(), nodes * 4, cudaMemcpyHostToDevice, s));
+    // one upload of the node table: off, kk, key, child0, child1 (int32), l_max
+    std::vector<int32_t> tbl32((size_t)5 * nodes);
+    for (int32_t jn = 0; jn < nodes; ++jn) {
+      tbl32[jn] = off[jn], tbl32[nodes + jn] = kks[jn], tbl32[2 * nodes + jn] = hkey[jn];
+      tbl32[3 * nodes + jn] = c0[jn], tbl32[4 * nodes + jn] = c1[jn];
+    }
+    Buf<int32_t> d_tbl(5 * nodes, s);
+    Buf<int64_t> d_lmax(nodes, s);
+    TP_CUDA(cudaMemcpyAsync(d_tbl.get(), tbl32.data(), tbl32.size() * 4, cudaMemcpyHostToDevice, s));
+    TP_CUDA(cudaMemcpyAsync(d_lmax.get(), lmx.data(), nodes * 8, cudaMemcpyHostToDevice, s));
+    const int32_t *d_off = d_tbl.get(), *d_kk = d_tbl.get() + nodes, *d_key = d_tbl.get() + 2 * nodes;
+    const int32_t *d_c0 = d_tbl.get() + 3 * nodes, *d_c1 = d_tbl.get() + 4 * nodes;
     Buf<int64_t> cut((int64_t)nodes * T, s);
     IPCtx c;
     c.n = n;
@@ -538,11 +577,12 @@ void initial_partition(const tp_graph *g, int32_t k, int64_t l_max, const tp_par
     c.lxadj = lxadj.get();
     c.ladj = ladj.get();
     c.lew = weighted ? lew.get() : nullptr;
-    c.noff = d_off.get();
-    c.nkk = d_kk.get();
+    c.noff = d_off;
+    c.nkk = d_kk;
+    c.nkey = d_key;
+    c.nlmax = d_lmax.get();
     c.T = T;
     c.seed = p.seed;
-    c.l_max = l_max;
     c.rounds = p.refine_rounds;
     c.S = p.sub_rounds;
     c.ord = ord.get(), c.disc = disc.get(), c.claimer = claimer.get(), c.cnt = cnt.get();
@@ -554,12 +594,14 @@ void initial_partition(const tp_graph *g, int32_t k, int64_t l_max, const tp_par
     launch(k_bisect, (unsigned)(nodes * T), kIPThreads, 0, s, c);
     TP_LAUNCH_CHECK();
     launch(k_fill_i32, grid_for(n, 256), 256, 0, s, next_node.get(), n, -1);
-    launch(k_pick, (unsigned)nodes, 256, 0, s, c, d_c0.get(), d_c1.get(), next_node.get(), d_part);
+    launch(k_pick, (unsigned)nodes, 256, 0, s, c, d_c0, d_c1, next_node.get(), d_part);
     TP_LAUNCH_CHECK();
     std::swap(node_of, next_node);
     TP_CUDA(cudaStreamSynchronize(s));  // host vectors above outlive their copies
     off.swap(noff);
     kks.swap(nkk);
+    hkey.swap(nkey);
+    lmx.swap(nlmx);
   }
 }
 

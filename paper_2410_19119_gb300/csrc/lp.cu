@@ -55,11 +55,14 @@ struct RateCtx {
   unsigned long long *counters;
   // M_FAV output
   int32_t *fav;
-  // M_REBAL
+  // M_REBAL (batched graphs: rb_best and blk_of hold one entry per graph)
   int32_t blk, k;
   int64_t *rb_loss;
   int32_t *rb_t;
   long long *rb_best;
+  const int32_t *blk_of;
+  // batched graphs (seg.gid == null: one graph)
+  SegLp seg;
   // lists and global tables
   const int32_t *list;
   int64_t list_n;
@@ -108,13 +111,25 @@ __device__ __forceinline__ int64_t node_w(const GView &g, int64_t u) { return g.
 
 __device__ __forceinline__ uint64_t rk_of(const RateCtx &c) { return c.rk_dev ? *c.rk_dev : c.rk; }
 
+// Batched graphs: u's number inside its own graph, its cap, and the
+// favourite key of a vertex without favourite (one per graph).
+__device__ __forceinline__ int64_t local_id(const RateCtx &c, int64_t u) {
+  return c.seg.gid ? u - c.seg.vb[c.seg.gid[u]] : u;
+}
+__device__ __forceinline__ int64_t cap_of(const RateCtx &c, int64_t u) {
+  return c.seg.gid ? c.seg.cap[c.seg.gid[u]] : c.cap;
+}
+__device__ __forceinline__ int32_t no_fav(const RateCtx &c, int64_t u) {
+  return (int32_t)(c.g.n + (c.seg.gid ? c.seg.gid[u] : 0));
+}
+
 template <int MODE>
 __device__ __forceinline__ bool active(const RateCtx &c, int64_t u) {
   if (MODE == M_LP)
     return c.sub_byte ? c.sub_byte[u] == c.s + 1
-                      : sub_round_of(hstep(rk_of(c), (uint64_t)u), c.S) == c.s;
+                      : sub_round_of(hstep(rk_of(c), (uint64_t)local_id(c, u)), c.S) == c.s;
   if (MODE == M_FAV) return c.label[u] == u && c.lw[u] == node_w(c.g, u);
-  return c.label[u] == c.blk;
+  return c.label[u] == (c.blk_of ? c.blk_of[c.seg.gid[u]] : c.blk);
 }
 
 template <int MODE>
@@ -124,9 +139,25 @@ __device__ __forceinline__ bool tier_entry(const RateCtx &c, int64_t k, int64_t 
   return c.bpos ? true : active<MODE>(c, u);
 }
 
+// The tie order of vertex u: tie_of(k, x) is the tie hash of label x as u's
+// graph numbers it (its label base folded into the additive constant, so
+// (x - base) + gamma costs one add, as x + gamma does for one graph).
+struct TieKey {
+  uint64_t hv, add;
+};
+__device__ __forceinline__ uint32_t tie_of(const TieKey &k, int32_t x) {
+  return (uint32_t)(mix64(k.hv ^ ((uint64_t)(int64_t)x + k.add)) >> 32);
+}
 template <int MODE>
-__device__ __forceinline__ uint64_t tie_key(const RateCtx &c, int64_t u) {
-  return MODE == M_REBAL ? 0 : hstep(hstep(rk_of(c), (uint64_t)u), kTagTie);
+__device__ __forceinline__ TieKey tie_key(const RateCtx &c, int64_t u) {
+  if (MODE == M_REBAL) return TieKey{0, 0};
+  int64_t vb = 0, lb = 0;
+  if (c.seg.gid) {
+    const int32_t g = c.seg.gid[u];
+    vb = c.seg.vb[g];
+    lb = c.seg.lb[g];
+  }
+  return TieKey{hstep(hstep(rk_of(c), (uint64_t)(u - vb)), kTagTie), kGamma - (uint64_t)lb};
 }
 
 __device__ __forceinline__ uint32_t slot_of(int32_t x, int logcap) {
@@ -180,18 +211,6 @@ struct Best {
   __device__ __forceinline__ void init() { r = -1, t = 0xffffffffu, x = INT32_MAX, rown = 0; }
 };
 
-template <int MODE>
-__device__ __forceinline__ void consider(const RateCtx &c, Best &b, int32_t x, int64_t R,
-                                         int32_t own, int64_t cu, uint64_t hv) {
-  if (x == own) {
-    b.rown = R;
-    return;
-  }
-  if (MODE != M_FAV && c.lw[x] + cu > c.cap) return;
-  uint32_t t = MODE == M_REBAL ? 0u : tie_hash(hv, x);
-  if (better(R, t, x, b.r, b.t, b.x)) b.r = R, b.t = t, b.x = x;
-}
-
 __device__ __forceinline__ void warp_reduce_best(Best &b) {
   warp_best(b.r, b.t, b.x);
   b.rown = warp_max(b.rown);
@@ -238,15 +257,24 @@ __device__ __forceinline__ void finalize_warp(const RateCtx &c, const Best &b, i
       if (++mb->cnt == 32) flush_movers(c, *mb);
     }
   } else if (MODE == M_FAV) {
-    if (lane == 0) c.fav[u] = b.r > 0 ? b.x : (int32_t)c.g.n;
+    if (lane == 0) c.fav[u] = b.r > 0 ? b.x : no_fav(c, u);
   } else {
+    // the graph's blocks are lb .. lb + k - 1 (one graph: 0 .. k - 1)
+    int32_t blk = c.blk, k = c.k, lb = 0;
+    long long *best = c.rb_best;
+    if (c.seg.gid) {
+      const int32_t g = c.seg.gid[u];
+      blk = c.blk_of[g], k = c.seg.k[g], lb = (int32_t)c.seg.lb[g];
+      best += g;
+    }
+    const int64_t cap = cap_of(c, u);
     int32_t tz = -1;
     if (b.r <= 0) {  // no admissible neighbouring block: smallest admissible block
-      for (int32_t base = 0; base < c.k && tz < 0; base += 32) {
-        int32_t t = base + lane;
-        bool ok = t < c.k && t != c.blk && c.lw[t] + cu <= c.cap;
+      for (int32_t base = 0; base < k && tz < 0; base += 32) {
+        int32_t t = lb + base + lane;
+        bool ok = base + lane < k && t != blk && c.lw[t] + cu <= cap;
         unsigned m = __ballot_sync(kFull, ok);
-        if (m) tz = base + __ffs(m) - 1;
+        if (m) tz = lb + base + __ffs(m) - 1;
       }
     }
     if (lane == 0) {
@@ -255,7 +283,7 @@ __device__ __forceinline__ void finalize_warp(const RateCtx &c, const Best &b, i
       if (tt >= 0) {
         int64_t loss = b.rown - (b.r > 0 ? b.r : 0);
         c.rb_loss[u] = loss;
-        atomicMin(c.rb_best, (long long)loss);
+        atomicMin(best, (long long)loss);
       }
     }
   }
@@ -268,8 +296,8 @@ __device__ void rate_vertex_warp(const RateCtx &c, int64_t u, int32_t *keys, int
                                  int logcap, bool allow_fast, MoverBuf *mb) {
   const int lane = lane_id();
   const int32_t own = c.label[u];
-  const int64_t cu = node_w(c.g, u);
-  const uint64_t hv = tie_key<MODE>(c, u);
+  const int64_t cu = node_w(c.g, u), capu = cap_of(c, u);
+  const TieKey hv = tie_key<MODE>(c, u);
   Best b;
   b.init();
   // every lane adds its neighbour's label to the table (shared-memory
@@ -288,13 +316,13 @@ __device__ void rate_vertex_warp(const RateCtx &c, int64_t u, int32_t *keys, int
       b.rown = vals[i];
       continue;
     }
-    const uint32_t t = MODE == M_REBAL ? 0u : tie_hash(hv, x);
+    const uint32_t t = MODE == M_REBAL ? 0u : tie_of(hv, x);
     if (better(vals[i], t, x, b.r, b.t, b.x)) b.r = vals[i], b.t = t, b.x = x;
   }
   warp_reduce_best(b);
   // the winner is full: the best admissible label instead (for a move it
   // must also improve on the own rating)
-  if (MODE != M_FAV && b.x != INT32_MAX && c.lw[b.x] + cu > c.cap) {
+  if (MODE != M_FAV && b.x != INT32_MAX && c.lw[b.x] + cu > capu) {
     const int64_t rown = b.rown;
     b.init();
     for (int i = lane; i < cap; i += 32) {
@@ -302,8 +330,8 @@ __device__ void rate_vertex_warp(const RateCtx &c, int64_t u, int32_t *keys, int
       if (x < 0 || x == own) continue;
       const int64_t R = vals[i];
       if (MODE == M_LP && R <= rown) continue;
-      const uint32_t t = MODE == M_REBAL ? 0u : tie_hash(hv, x);
-      if (better(R, t, x, b.r, b.t, b.x) && c.lw[x] + cu <= c.cap) b.r = R, b.t = t, b.x = x;
+      const uint32_t t = MODE == M_REBAL ? 0u : tie_of(hv, x);
+      if (better(R, t, x, b.r, b.t, b.x) && c.lw[x] + cu <= capu) b.r = R, b.t = t, b.x = x;
     }
     warp_reduce_best(b);
     b.rown = rown;
@@ -545,7 +573,7 @@ __device__ __forceinline__ void emit_lane(const RateCtx &c, bool has, int32_t u,
                                           int32_t rown, int64_t cu, const LaneCand &best,
                                           Movers &mb, int &nmv) {
   if (MODE == M_FAV) {
-    if (has) c.fav[u] = best.r > 0 ? best.x : (int32_t)c.g.n;
+    if (has) c.fav[u] = best.r > 0 ? best.x : no_fav(c, u);
   } else {
     const bool mv = has && best.r > rown;
     const unsigned mm = __ballot_sync(kFull, mv);
@@ -602,16 +630,17 @@ __device__ __forceinline__ void lane_batch(const RateCtx &c, bool has, int32_t u
     const int64_t cu = has ? node_w(c.g, u) : 1;
     LaneCand best{-1, 0xffffffffu, INT32_MAX};
     if (MODE == M_FAV ? rmax > 0 : rmax > rown) {
-      const uint64_t hv = tie_key<MODE>(c, u);
+      const TieKey hv = tie_key<MODE>(c, u);
+      const int64_t capu = cap_of(c, u);
       // the best candidate overall is tied at the top rating
       LaneCand b1{-1, 0xffffffffu, INT32_MAX};
       for (int k = 0; k < ncand; ++k) {
         if ((int32_t)wcol[k * 32] != rmax) continue;
         const int32_t x = ccol[k * 32];
-        const LaneCand cand{rmax, tie_hash(hv, x), x};
+        const LaneCand cand{rmax, tie_of(hv, x), x};
         if (lane_better(cand, b1)) b1 = cand;
       }
-      if (MODE == M_FAV || c.lw[b1.x] + cu <= c.cap) {
+      if (MODE == M_FAV || c.lw[b1.x] + cu <= capu) {
         best = b1;
       } else {
         // the winner is full: the best admissible candidate that improves
@@ -619,8 +648,8 @@ __device__ __forceinline__ void lane_batch(const RateCtx &c, bool has, int32_t u
           const int32_t r = (int32_t)wcol[k * 32];
           const int32_t x = ccol[k * 32];
           if (r <= rown || x == b1.x) continue;
-          const LaneCand cand{r, tie_hash(hv, x), x};
-          if (lane_better(cand, best) && c.lw[x] + cu <= c.cap) best = cand;
+          const LaneCand cand{r, tie_of(hv, x), x};
+          if (lane_better(cand, best) && c.lw[x] + cu <= capu) best = cand;
         }
       }
     }
@@ -667,16 +696,17 @@ __device__ __forceinline__ void lane_batch(const RateCtx &c, bool has, int32_t u
     const int64_t cu = has ? node_w(c.g, u) : 1;
     LaneCand best{-1, 0xffffffffu, INT32_MAX};
     if (MODE == M_FAV ? rmax > 0 : rmax > rown) {
-      const uint64_t hv = tie_key<MODE>(c, u);
+      const TieKey hv = tie_key<MODE>(c, u);
+      const int64_t capu = cap_of(c, u);
       // the best candidate overall is tied at the top rating
       LaneCand b1{-1, 0xffffffffu, INT32_MAX};
       for (int k = 0; k < ncand; ++k) {
         if ((int32_t)cnt[k * 32] != rmax) continue;
         const int32_t x = ccol[k * 32];
-        const LaneCand cand{rmax, tie_hash(hv, x), x};
+        const LaneCand cand{rmax, tie_of(hv, x), x};
         if (lane_better(cand, b1)) b1 = cand;
       }
-      if (MODE == M_FAV || c.lw[b1.x] + cu <= c.cap) {
+      if (MODE == M_FAV || c.lw[b1.x] + cu <= capu) {
         best = b1;
       } else {
         // the winner is full: the best admissible candidate that improves
@@ -684,8 +714,8 @@ __device__ __forceinline__ void lane_batch(const RateCtx &c, bool has, int32_t u
           const int32_t r = (int32_t)cnt[k * 32];
           const int32_t x = ccol[k * 32];
           if (r <= rown || x == b1.x) continue;
-          const LaneCand cand{r, tie_hash(hv, x), x};
-          if (lane_better(cand, best) && c.lw[x] + cu <= c.cap) best = cand;
+          const LaneCand cand{r, tie_of(hv, x), x};
+          if (lane_better(cand, best) && c.lw[x] + cu <= capu) best = cand;
         }
       }
     }
@@ -721,23 +751,26 @@ __device__ __forceinline__ void lane_batch(const RateCtx &c, bool has, int32_t u
     rown -= N - deg;  // the padding counted as own label
     const int64_t cu = has ? node_w(c.g, u) : 1;
     const bool go = MODE == M_FAV ? rmax > 0 : rmax > rown;
-    uint64_t hv = 0;
+    TieKey hv{0, 0};
+    bool have_hv = false;
     LaneCand b1{rmax, 0u, x1};
     if (go && ntop >= 2) {
       hv = tie_key<MODE>(c, u);
-      const LaneCand c1{rmax, tie_hash(hv, x1), x1}, c2{rmax, tie_hash(hv, x2), x2};
+      have_hv = true;
+      const LaneCand c1{rmax, tie_of(hv, x1), x1}, c2{rmax, tie_of(hv, x2), x2};
       b1 = lane_better(c1, c2) ? c1 : c2;
     }
     const bool many = go && ntop >= 3;
     bool full = false;
-    if (go && MODE != M_FAV) full = c.lw[b1.x] + cu > c.cap;
+    const int64_t capu = go && MODE != M_FAV ? cap_of(c, u) : 0;
+    if (go && MODE != M_FAV) full = c.lw[b1.x] + cu > capu;
     // rare: three or more labels tied at the top, or the winner is full;
     // the sorted labels go to this lane's column and the runs are walked
     if (__any_sync(kFull, many || full)) {
 #pragma unroll
       for (int i = 0; i < N; ++i) ccol[i * 32] = a[i];
       if (many || full) {
-        if (!hv) hv = tie_key<MODE>(c, u);
+        if (!have_hv) hv = tie_key<MODE>(c, u);
         const int own_run = rown + (N - deg);  // the own label's entries, padding included
         LaneCand bb{-1, 0xffffffffu, INT32_MAX};
         for (int i = 0; i < N;) {
@@ -755,13 +788,13 @@ __device__ __forceinline__ void lane_batch(const RateCtx &c, bool has, int32_t u
           } else {  // the best admissible label that improves
             if (r <= rown) continue;
           }
-          const LaneCand cand{r, tie_hash(hv, x), x};
-          if (lane_better(cand, bb) && (!full || MODE == M_FAV || c.lw[x] + cu <= c.cap))
+          const LaneCand cand{r, tie_of(hv, x), x};
+          if (lane_better(cand, bb) && (!full || MODE == M_FAV || c.lw[x] + cu <= capu))
             bb = cand;
         }
         if (!full) {
           b1 = bb;
-          if (MODE != M_FAV) full = c.lw[b1.x] + cu > c.cap;
+          if (MODE != M_FAV) full = c.lw[b1.x] + cu > capu;
           if (full) {  // the top-tied winner is full: look again for an admissible one
             bb = LaneCand{-1, 0xffffffffu, INT32_MAX};
             for (int i = 0; i < N;) {
@@ -775,8 +808,8 @@ __device__ __forceinline__ void lane_batch(const RateCtx &c, bool has, int32_t u
               const int32_t r = j - i;
               i = j;
               if (r <= rown) continue;
-              const LaneCand cand{r, tie_hash(hv, x), x};
-              if (lane_better(cand, bb) && c.lw[x] + cu <= c.cap) bb = cand;
+              const LaneCand cand{r, tie_of(hv, x), x};
+              if (lane_better(cand, bb) && c.lw[x] + cu <= capu) bb = cand;
             }
           }
         }
@@ -1142,8 +1175,8 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_block(RateCtx c, int max
     __syncthreads();
     // best label ignoring the cap, and the own rating
     const int32_t own = c.label[u];
-    const int64_t cu = node_w(c.g, u);
-    const uint64_t hv = tie_key<MODE>(c, u);
+    const int64_t cu = node_w(c.g, u), capu = cap_of(c, u);
+    const TieKey hv = tie_key<MODE>(c, u);
     Best b;
     b.init();
     for (int k = tid; k < cap; k += kBlockThreads) {
@@ -1154,13 +1187,13 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_block(RateCtx c, int max
         b.rown = R;
         continue;
       }
-      const uint32_t t = MODE == M_REBAL ? 0u : tie_hash(hv, x);
+      const uint32_t t = MODE == M_REBAL ? 0u : tie_of(hv, x);
       if (better(R, t, x, b.r, b.t, b.x)) b.r = R, b.t = t, b.x = x;
     }
     block_reduce_best(b, wb);
     // the winner is full: the best admissible label instead (it must improve
     // on the own rating to matter)
-    if (MODE != M_FAV && b.x != INT32_MAX && c.lw[b.x] + cu > c.cap) {
+    if (MODE != M_FAV && b.x != INT32_MAX && c.lw[b.x] + cu > capu) {
       const int64_t rown = b.rown;
       b.init();
       for (int k = tid; k < cap; k += kBlockThreads) {
@@ -1168,8 +1201,8 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_block(RateCtx c, int max
         if (x < 0 || x == own) continue;
         const int64_t R = (int64_t)vals[k];
         if (MODE == M_LP && R <= rown) continue;
-        const uint32_t t = MODE == M_REBAL ? 0u : tie_hash(hv, x);
-        if (better(R, t, x, b.r, b.t, b.x) && c.lw[x] + cu <= c.cap) b.r = R, b.t = t, b.x = x;
+        const uint32_t t = MODE == M_REBAL ? 0u : tie_of(hv, x);
+        if (better(R, t, x, b.r, b.t, b.x) && c.lw[x] + cu <= capu) b.r = R, b.t = t, b.x = x;
       }
       block_reduce_best(b, wb);
       b.rown = rown;
@@ -1307,8 +1340,8 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_huge_scan(RateCtx c, Bes
     const int64_t u = c.list[i];
     if (!c.bpos && !active<MODE>(c, u)) continue;
     const int32_t own = c.label[u];
-    const int64_t cu = node_w(c.g, u);
-    const uint64_t hv = tie_key<MODE>(c, u);
+    const int64_t cu = node_w(c.g, u), capu = cap_of(c, u);
+    const TieKey hv = tie_key<MODE>(c, u);
     // a table filled to an eighth or more is read in slot order (8192 slots
     // per segment); a sparser one through its list of filled slots (4096
     // list entries per segment)
@@ -1334,9 +1367,9 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_huge_scan(RateCtx c, Bes
         b.rown = R;
         continue;
       }
-      const uint32_t t = MODE == M_REBAL ? 0u : tie_hash(hv, x);
+      const uint32_t t = MODE == M_REBAL ? 0u : tie_of(hv, x);
       if (better(R, t, x, b.r, b.t, b.x)) b.r = R, b.t = t, b.x = x;
-      if (MODE != M_FAV && better(R, t, x, a.r, a.t, a.x) && c.lw[x] + cu <= c.cap)
+      if (MODE != M_FAV && better(R, t, x, a.r, a.t, a.x) && c.lw[x] + cu <= capu)
         a.r = R, a.t = t, a.x = x;
     }
     block_reduce_best(b, wb);
@@ -1374,7 +1407,7 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_huge_decide(RateCtx c, c
     }
     block_reduce_best(b, wb);
     block_reduce_best(a, wb);
-    if (MODE != M_FAV && b.x != INT32_MAX && c.lw[b.x] + cu > c.cap) {
+    if (MODE != M_FAV && b.x != INT32_MAX && c.lw[b.x] + cu > cap_of(c, u)) {
       // the winner is full: the best admissible label (for a move it must
       // also improve on the own rating, which finalize_warp checks)
       a.rown = b.rown;
@@ -1403,9 +1436,15 @@ struct ApproveCtx {
   int64_t *lw;
   int64_t cap;
   const int64_t *vw;
+  // batched graphs: graph of every label and every graph's cap (null: one graph)
+  const int32_t *lgid;
+  const int64_t *gcap;
 };
 
 __device__ __forceinline__ int64_t vwt(const ApproveCtx &a, int64_t u) { return a.vw ? a.vw[u] : 1; }
+__device__ __forceinline__ int64_t target_cap(const ApproveCtx &a, int32_t t) {
+  return a.lgid ? a.gcap[a.lgid[t]] : a.cap;
+}
 
 // A: targets that fit take every mover; the others become contested and
 // count their movers (the first one also lists the target).
@@ -1414,7 +1453,7 @@ __global__ void k_approve_fit(ApproveCtx a) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nm;
        i += (int64_t)gridDim.x * blockDim.x) {
     int32_t t = a.mv_t[i];
-    bool fits = a.lw[t] + a.in_w[t] <= a.cap;
+    bool fits = a.lw[t] + a.in_w[t] <= target_cap(a, t);
     a.mv_ok[i] = fits;
     if (!fits && atomicAdd(&a.ccnt[t], 1) == 0) {
       unsigned long long j = atomicAdd(&a.counters[1], 1ull);
@@ -1530,7 +1569,7 @@ __global__ void k_approve_contested(ApproveCtx a) {
   for (int64_t j = blockIdx.x; j < nt; j += gridDim.x) {
     int32_t t = a.ctarget[j];
     int64_t base = a.cbase[t], cnt = a.ccnt[t];
-    int64_t rem = a.cap - a.lw[t];
+    int64_t rem = target_cap(a, t) - a.lw[t];
     __syncthreads();  // every thread has read ccnt before it is reset below
     if (threadIdx.x == 0) a.ccnt[t] = 0, a.cfill[t] = 0;
     auto item = [&](int64_t q, uint64_t &hi, uint32_t &lo, int64_t &w) {
@@ -1785,6 +1824,8 @@ ApproveCtx approve_ctx(tp_graph *g, const LpState &st, LpWork &w) {
   a.lw = st.lw;
   a.cap = st.cap;
   a.vw = g->unit_vw ? nullptr : g->vw.get();
+  a.lgid = st.seg.gid ? st.seg.lgid : nullptr;
+  a.gcap = st.seg.cap;
   return a;
 }
 
@@ -1803,11 +1844,13 @@ constexpr int kBucketChunks = kBucketSpan / 32;
 // same sub-round are grouped with one match instruction.
 // With offsets (compressed graphs), pass 1 also stores each listed vertex's
 // record start << 8 | record length in rec (lane-tier records are <= 65 bytes).
+// Batched graphs (gid non-null): a vertex hashes its number inside its graph.
 __global__ void __launch_bounds__(256) k_bucket(const uint8_t *tier, int64_t n, uint64_t rk_in,
                                                 const uint64_t *rk_dev, int32_t S, bool fill,
                                                 int64_t *cnt, int32_t *bucket, uint8_t *sub_byte,
                                                 const uint32_t *o32, const uint64_t *o64,
-                                                uint64_t *rec) {
+                                                uint64_t *rec, const int32_t *gid,
+                                                const int64_t *vb) {
   __shared__ int32_t chunk_cnt[kBucketChunks][32];  // [chunk][sub-round], S <= 32
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const int64_t nblocks = gridDim.x;
@@ -1826,7 +1869,8 @@ __global__ void __launch_bounds__(256) k_bucket(const uint8_t *tier, int64_t n, 
       } else {
         // every vertex's sub-round is kept (the other tiers test it); only
         // the lane tier is listed
-        const int32_t sr = sub_round_of(hstep(rk, (uint64_t)u), S);
+        const int64_t lu = gid ? u - vb[gid[u]] : u;
+        const int32_t sr = sub_round_of(hstep(rk, (uint64_t)lu), S);
         sub_byte[u] = (uint8_t)(sr + 1);
         sub = tier[u] == TIER_LANE ? sr : -1;
       }
@@ -2008,7 +2052,9 @@ static void tier_buckets(tp_graph *g, LpWork &w, int32_t S, cudaStream_t stream)
 }
 
 void lp_bucket(tp_graph *g, LpWork &w, uint64_t rk, int32_t S, const tp_params &p,
-               cudaStream_t stream, const uint64_t *rk_dev, bool tiers) {
+               cudaStream_t stream, const uint64_t *rk_dev, bool tiers, const SegLp *seg) {
+  const int32_t *gid = seg ? seg->gid : nullptr;
+  const int64_t *vb = seg ? seg->vb : nullptr;
   build_tiers(g, p, stream);
   w.bucket_S = 0;
   if (S > 32) return;
@@ -2022,10 +2068,10 @@ void lp_bucket(tp_graph *g, LpWork &w, uint64_t rk, int32_t S, const tp_params &
   const uint64_t *o64 = zrec && g->off_is64 ? g->off64.get() : nullptr;
   uint64_t *rec = zrec ? w.bucket_rec.get() : nullptr;
   launch(k_bucket, (unsigned)nblocks, 256, 0, stream, g->tiers.tier.get(), g->n, rk, rk_dev, S,
-         false, w.bucket_off.get(), w.bucket.get(), w.bucket_sub.get(), o32, o64, rec);
+         false, w.bucket_off.get(), w.bucket.get(), w.bucket_sub.get(), o32, o64, rec, gid, vb);
   exclusive_scan_i64(w.bucket_off.get(), w.bucket_off.get(), S * nblocks, stream);
   launch(k_bucket, (unsigned)nblocks, 256, 0, stream, g->tiers.tier.get(), g->n, rk, rk_dev, S,
-         true, w.bucket_off.get(), w.bucket.get(), w.bucket_sub.get(), o32, o64, rec);
+         true, w.bucket_off.get(), w.bucket.get(), w.bucket_sub.get(), o32, o64, rec, gid, vb);
   TP_LAUNCH_CHECK();
   w.bucket_S = S;
   w.bucket_nblocks = nblocks;
@@ -2121,6 +2167,7 @@ void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t
   c.label = st.label;
   c.lw = st.lw;
   c.cap = st.cap;
+  c.seg = st.seg;
   c.rk = rk;
   c.rk_dev = rk_dev;
   c.S = S;
@@ -2205,7 +2252,7 @@ bool lp_rounds_graph(tp_graph *g, const LpState &st, LpWork &w, uint64_t seed, u
   bool ok = true;
   try {
     launch(k_round_key, 1u, 1u, 0, cs, seed, tag, a, b0, d_r.get(), d_rk.get());
-    lp_bucket(g, w, 0, S, p, cs, d_rk.get());
+    lp_bucket(g, w, 0, S, p, cs, d_rk.get(), false, &st.seg);
     for (int32_t s = 0; s < S; ++s) lp_subround(g, st, w, 0, S, s, p, cs, nullptr, d_rk.get());
     w.bucket_S = 0;
   } catch (...) {
@@ -2245,7 +2292,7 @@ void lp_rounds(tp_graph *g, const LpState &st, LpWork &w, uint64_t seed, uint64_
   ApprovalGraph ag(approve_ctx(g, st, w), w.n, w.counters.get());
   for (int32_t r = 0; r < rounds; ++r) {
     uint64_t rk = round_key(seed, tag, a, b0 + (uint64_t)r);
-    lp_bucket(g, w, rk, S, p, stream, nullptr, true);
+    lp_bucket(g, w, rk, S, p, stream, nullptr, true, &st.seg);
     for (int32_t s = 0; s < S; ++s) lp_subround(g, st, w, rk, S, s, p, stream, ag.exec);
     w.bucket_S = 0;
     w.tb_valid = false;
@@ -2287,11 +2334,14 @@ __global__ void k_th_prep(const uint64_t *keys, const uint64_t *vals, const int6
   }
 }
 
-// bins, straddlers and group heads
+// bins, straddlers and group heads (batched graphs: a group lies in one
+// graph, whose U is gU[gid[vertex]])
 __global__ void k_th_heads(const int64_t *excl, const int64_t *rs, const int64_t *wt, int64_t m,
-                           int64_t U, int64_t *head) {
+                           int64_t U_one, const uint64_t *vals, const int32_t *gid,
+                           const int64_t *gU, int64_t *head) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t U = gid ? gU[gid[vals[i]]] : U_one;
     int64_t P = excl[i] - excl[rs[i]];
     int64_t bin = P / U;
     bool str = P + wt[i] > (bin + 1) * U;
@@ -2321,7 +2371,7 @@ __global__ void k_th_assign(const int64_t *head_raw, const int64_t *head_scan,
 }  // namespace
 
 void favourites(tp_graph *g, const int32_t *C, const int64_t *Wc, uint64_t rk, int32_t *fav,
-                const tp_params &p, cudaStream_t s) {
+                const tp_params &p, cudaStream_t s, const SegLp *seg) {
   configure_kernels();
   launch(k_fav_init, grid_for(g->n, 256), 256, 0, s, fav, g->n);
   TP_LAUNCH_CHECK();
@@ -2330,15 +2380,17 @@ void favourites(tp_graph *g, const int32_t *C, const int64_t *Wc, uint64_t rk, i
   c.lw = Wc;
   c.rk = rk;
   c.fav = fav;
+  if (seg) c.seg = *seg;
   rate_tiers<M_FAV>(g, c, p, s);
 }
 
 void two_hop(tp_graph *g, int32_t *C, const int64_t *Wc, int64_t U, uint64_t seed, int32_t level,
-             const tp_params &p, cudaStream_t s) {
+             const tp_params &p, cudaStream_t s, const SegLp *seg) {
   int64_t n = g->n;
   if (n == 0) return;
+  const bool sg = seg && seg->gid;
   Buf<int32_t> fav(n, s), flag(n, s);
-  favourites(g, C, Wc, round_key(seed, kTagTwoHop, (uint64_t)level, 0), fav.get(), p, s);
+  favourites(g, C, Wc, round_key(seed, kTagTwoHop, (uint64_t)level, 0), fav.get(), p, s, seg);
   launch(k_th_flags, grid_for(n, 256), 256, 0, s, fav.get(), n, flag.get());
   TP_LAUNCH_CHECK();
   Buf<int64_t> pos(n + 1, s);
@@ -2349,7 +2401,10 @@ void two_hop(tp_graph *g, int32_t *C, const int64_t *Wc, int64_t U, uint64_t see
   launch(k_th_gather, grid_for(n, 256), 256, 0, s, fav.get(), flag.get(), pos.get(), n, keys.get(),
                                                  vals.get());
   TP_LAUNCH_CHECK();
-  radix_sort_pairs(keys.get(), vals.get(), m, bits_for((uint64_t)n), s);
+  // keys: favourites (vertex ids) and the no-favourite key n (per graph:
+  // n + graph), so no group spans two graphs
+  radix_sort_pairs(keys.get(), vals.get(), m,
+                   bits_for((uint64_t)n + (sg ? (uint64_t)seg->ngraphs : 0)), s);
   Buf<int64_t> wt(m, s), rs(m, s), excl(m + 1, s), head(m, s), hs(m, s);
   launch(k_th_prep, grid_for(m, 256), 256, 0, s, keys.get(), vals.get(),
                                                g->unit_vw ? nullptr : g->vw.get(), m, wt.get(),
@@ -2357,7 +2412,8 @@ void two_hop(tp_graph *g, int32_t *C, const int64_t *Wc, int64_t U, uint64_t see
   TP_LAUNCH_CHECK();
   inclusive_max_scan_i64(rs.get(), rs.get(), m, s);
   exclusive_scan_i64(wt.get(), excl.get(), m, s);
-  launch(k_th_heads, grid_for(m, 256), 256, 0, s, excl.get(), rs.get(), wt.get(), m, U, head.get());
+  launch(k_th_heads, grid_for(m, 256), 256, 0, s, excl.get(), rs.get(), wt.get(), m, U, vals.get(),
+         sg ? seg->gid : nullptr, sg ? seg->cap : nullptr, head.get());
   TP_LAUNCH_CHECK();
   inclusive_max_scan_i64(head.get(), hs.get(), m, s);
   launch(k_th_assign, grid_for(m, 256), 256, 0, s, head.get(), hs.get(), vals.get(), m, C);
@@ -2365,7 +2421,7 @@ void two_hop(tp_graph *g, int32_t *C, const int64_t *Wc, int64_t U, uint64_t see
 }
 
 void lp_cluster(tp_graph *g, int64_t U, const tp_params &p, int32_t level, int32_t *d_cluster,
-                cudaStream_t s, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+                cudaStream_t s, cudaEvent_t ev_begin, cudaEvent_t ev_end, const SegLp *seg) {
   int64_t n = g->n;
   if (n == 0) return;
   Buf<int64_t> Wc(n, s);
@@ -2375,20 +2431,26 @@ void lp_cluster(tp_graph *g, int64_t U, const tp_params &p, int32_t level, int32
   LpWork w;
   w.init(n, n, s);
   LpState st{d_cluster, Wc.get(), n, U};
-  prof_scope(level == 0);
+  if (seg) {  // labels are vertices: a label's graph and base are its vertex's
+    st.seg = *seg;
+    st.seg.lgid = seg->gid;
+    st.seg.lb = seg->vb;
+  }
+  prof_scope(level == 0 && !seg);
   if (ev_begin) TP_CUDA(cudaEventRecord(ev_begin, s));
   lp_rounds(g, st, w, p.seed, kTagCluster, (uint64_t)level, 0, p.cluster_rounds, p.sub_rounds, p, s);
   if (ev_end) TP_CUDA(cudaEventRecord(ev_end, s));
   prof_scope(false);
-  if (p.two_hop) two_hop(g, d_cluster, Wc.get(), U, p.seed, level, p, s);
+  if (p.two_hop) two_hop(g, d_cluster, Wc.get(), U, p.seed, level, p, s, seg ? &st.seg : nullptr);
 }
 
 void lp_refine(tp_graph *g, int32_t k, int64_t l_max, const tp_params &p, int32_t level,
-               int32_t *d_part, int64_t *d_B, cudaStream_t s) {
+               int32_t *d_part, int64_t *d_B, cudaStream_t s, const SegLp *seg) {
   if (g->n == 0) return;
   LpWork w;
   w.init(g->n, k, s);
   LpState st{d_part, d_B, k, l_max};
+  if (seg) st.seg = *seg;
   lp_rounds(g, st, w, p.seed, kTagRefine, (uint64_t)level, 0, p.refine_rounds, p.sub_rounds, p, s);
 }
 
@@ -2463,6 +2525,104 @@ void rebalance_moves(tp_graph *g, int32_t k, int64_t l_max, int32_t *d_part, int
       *balanced = 0;
       return;
     }
+  }
+}
+
+namespace {
+
+// Batched rebalancing, step 1 (one block per graph of the union): the
+// smallest overloaded block of every graph still rebalancing, or -1; resets
+// the graph's best loss and vertex and counts the graphs with one.
+__global__ void k_find_over_seg(const int64_t *B, SegLp seg, const int32_t *graphs, int64_t ng,
+                                const int32_t *stuck, int32_t *blk_of, long long *best,
+                                int32_t *best_u, int32_t *n_over) {
+  __shared__ int32_t bmin;
+  for (int64_t j = blockIdx.x; j < ng; j += gridDim.x) {
+    const int32_t i = graphs[j];
+    if (threadIdx.x == 0) bmin = INT32_MAX;
+    __syncthreads();
+    const int64_t lb = seg.lb[i], cap = seg.cap[i];
+    if (!stuck[i])
+      for (int32_t b = threadIdx.x; b < seg.k[i]; b += blockDim.x)
+        if (B[lb + b] > cap) atomicMin(&bmin, b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const bool over = bmin != INT32_MAX;
+      blk_of[i] = over ? (int32_t)(lb + bmin) : -1;
+      best[i] = INT64_MAX;
+      best_u[i] = INT32_MAX;
+      if (over) atomicAdd(n_over, 1);
+    }
+    __syncthreads();
+  }
+}
+
+// Step 2: per graph, the smallest vertex among those of least loss.
+__global__ void k_rb_pick_seg(const int32_t *part, const int32_t *gid, const int32_t *blk_of,
+                              const int32_t *rb_t, const int64_t *rb_loss, const long long *best,
+                              int64_t n, int32_t *best_u) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t g = gid[u], blk = blk_of[g];
+    if (blk >= 0 && part[u] == blk && rb_t[u] >= 0 && rb_loss[u] == best[g])
+      atomicMin(&best_u[g], (int32_t)u);
+  }
+}
+
+// Step 3 (one thread per graph): make the move, or retire a graph without one.
+__global__ void k_rb_apply_seg(const int32_t *graphs, int64_t ng, const int32_t *blk_of,
+                               const int32_t *best_u, const int32_t *rb_t, const int64_t *vw,
+                               int32_t *part, int64_t *B, int32_t *stuck) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < ng;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = graphs[j];
+    if (blk_of[i] < 0) continue;
+    const int32_t u = best_u[i];
+    if (u == INT32_MAX) {
+      stuck[i] = 1;
+      continue;
+    }
+    const int32_t t = rb_t[u], b = part[u];
+    const int64_t w = vw ? vw[u] : 1;
+    B[b] -= w;
+    B[t] += w;
+    part[u] = t;
+  }
+}
+
+}  // namespace
+
+void rebalance_moves_seg(tp_graph *g, const SegLp &seg, const int32_t *d_graphs, int64_t ng,
+                         int32_t *d_part, int64_t *d_B, const tp_params &p, cudaStream_t s) {
+  configure_kernels();
+  const int64_t n = g->n, G = seg.ngraphs;
+  if (n == 0 || ng == 0) return;
+  Buf<int32_t> blk_of(G, s), best_u(G, s), stuck(G, s), n_over(1, s);
+  Buf<long long> best(G, s);
+  Buf<int32_t> rb_t(n, s);
+  Buf<int64_t> rb_loss(n, s);
+  TP_CUDA(cudaMemsetAsync(stuck.get(), 0, G * sizeof(int32_t), s));
+  const unsigned gb = (unsigned)std::min<int64_t>(ng, (int64_t)num_sms() * 8);
+  for (;;) {
+    TP_CUDA(cudaMemsetAsync(n_over.get(), 0, sizeof(int32_t), s));
+    launch(k_find_over_seg, gb, 128, 0, s, d_B, seg, d_graphs, ng, stuck.get(), blk_of.get(),
+           best.get(), best_u.get(), n_over.get());
+    TP_LAUNCH_CHECK();
+    if (read_scalar(n_over.get(), s) == 0) return;
+    RateCtx c{};
+    c.label = d_part;
+    c.lw = d_B;
+    c.seg = seg;
+    c.blk_of = blk_of.get();
+    c.rb_loss = rb_loss.get();
+    c.rb_t = rb_t.get();
+    c.rb_best = best.get();
+    rate_tiers<M_REBAL>(g, c, p, s);
+    launch(k_rb_pick_seg, grid_for(n, 256), 256, 0, s, d_part, seg.gid, blk_of.get(), rb_t.get(),
+           rb_loss.get(), best.get(), n, best_u.get());
+    launch(k_rb_apply_seg, grid_for(ng, 256), 256, 0, s, d_graphs, ng, blk_of.get(), best_u.get(),
+           rb_t.get(), g->unit_vw ? nullptr : g->vw.get(), d_part, d_B, stuck.get());
+    TP_LAUNCH_CHECK();
   }
 }
 

@@ -206,8 +206,9 @@ __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
   return z ^ (z >> 31);
 }
+constexpr uint64_t kGamma = 0x9e3779b97f4a7c15ULL;  // golden-gamma offset of hstep
 __host__ __device__ __forceinline__ uint64_t hstep(uint64_t h, uint64_t x) {
-  return mix64(h ^ (x + 0x9e3779b97f4a7c15ULL));
+  return mix64(h ^ (x + kGamma));
 }
 __host__ __device__ __forceinline__ uint64_t round_key(uint64_t seed, uint64_t tag, uint64_t a,
                                                        uint64_t b) {
@@ -354,11 +355,26 @@ void compute_degrees(const tp_graph *g, int64_t *d_deg, cudaStream_t s);  // n e
 void build_tiers(tp_graph *g, const tp_params &p, cudaStream_t s);
 
 // ---------------------------------------------------------------- LP (lp.cu)
+// Batched graphs: one union graph holds many graphs side by side (each a
+// contiguous vertex range, labels of a graph only ever its own), and every
+// per-vertex decision is taken exactly as for that graph alone: hashes see
+// the graph's own vertex and label numbers, caps are the graph's. Tables are
+// indexed by the graph's position in the batch. gid == null: one graph.
+struct SegLp {
+  const int32_t *gid = nullptr;   // graph of every vertex
+  const int32_t *lgid = nullptr;  // graph of every label
+  const int64_t *vb = nullptr;    // per graph: its first vertex in this union
+  const int64_t *lb = nullptr;    // per graph: its first label
+  const int64_t *cap = nullptr;   // per graph: the label-weight cap
+  const int32_t *k = nullptr;     // per graph: its blocks (refinement, rebalancing)
+  int64_t ngraphs = 0;            // table entries
+};
 struct LpState {
   int32_t *label;
   int64_t *lw;
   int64_t nlabels;
-  int64_t cap;  // uniform cap for every label
+  int64_t cap;  // uniform cap for every label (one graph)
+  SegLp seg{};
 };
 // Workspace for sub-rounds on one graph (per-label counters + mover lists).
 struct LpWork {
@@ -403,27 +419,55 @@ void lp_subround(tp_graph *g, const LpState &st, LpWork &w, uint64_t rk, int32_t
 // Buckets the lane-tier vertices of round key rk by sub-round (A3), and with
 // tiers = true also the other tiers' lists (not inside a stream capture).
 void lp_bucket(tp_graph *g, LpWork &w, uint64_t rk, int32_t S, const tp_params &p,
-               cudaStream_t stream, const uint64_t *rk_dev = nullptr, bool tiers = false);
+               cudaStream_t stream, const uint64_t *rk_dev = nullptr, bool tiers = false,
+               const SegLp *seg = nullptr);
 void lp_rounds(tp_graph *g, const LpState &st, LpWork &w, uint64_t seed, uint64_t tag, uint64_t a,
                uint64_t b0, int32_t rounds, int32_t S, const tp_params &p, cudaStream_t stream);
 // ev_begin / ev_end (nullable) are recorded around the LP rounds alone.
+// seg (batched graphs): vb, cap (U of every graph) and gid; lgid and lb are
+// taken equal to gid and vb (labels are vertices).
 void lp_cluster(tp_graph *g, int64_t U, const tp_params &p, int32_t level, int32_t *d_cluster,
-                cudaStream_t s, cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
+                cudaStream_t s, cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr,
+                const SegLp *seg = nullptr);
+// seg (batched graphs): labels are global block ids, lgid maps them to graphs,
+// lb is every graph's first block, cap its L_max, k its block count; k is then
+// the total number of blocks.
 void lp_refine(tp_graph *g, int32_t k, int64_t l_max, const tp_params &p, int32_t level,
-               int32_t *d_part, int64_t *d_B, cudaStream_t s);
-// Per-vertex favourite cluster of singletons (two-hop): fav[u] = best label or n.
+               int32_t *d_part, int64_t *d_B, cudaStream_t s, const SegLp *seg = nullptr);
+// Per-vertex favourite cluster of singletons (two-hop): fav[u] = best label or
+// n (batched graphs: n + the vertex's graph).
 void favourites(tp_graph *g, const int32_t *C, const int64_t *Wc, uint64_t rk, int32_t *fav,
-                const tp_params &p, cudaStream_t s);
+                const tp_params &p, cudaStream_t s, const SegLp *seg = nullptr);
 void two_hop(tp_graph *g, int32_t *C, const int64_t *Wc, int64_t U, uint64_t seed, int32_t level,
-             const tp_params &p, cudaStream_t s);
+             const tp_params &p, cudaStream_t s, const SegLp *seg = nullptr);
 void rebalance_moves(tp_graph *g, int32_t k, int64_t l_max, int32_t *d_part, int64_t *d_B,
                      int *balanced, const tp_params &p, cudaStream_t s);
+// Rebalancing of batched graphs (seg as for lp_refine): every graph with an
+// overloaded block makes, per iteration, the move rebalance_moves would make
+// next for it alone; a graph leaves when balanced or when no move is left.
+// d_graphs: the ng batch positions of the union's graphs.
+void rebalance_moves_seg(tp_graph *g, const SegLp &seg, const int32_t *d_graphs, int64_t ng,
+                         int32_t *d_part, int64_t *d_B, const tp_params &p, cudaStream_t s);
 
 // ---------------------------------------------------------------- contraction / IP / metrics
-tp_graph *contract(const tp_graph *g, const int32_t *C, int32_t *d_map, cudaStream_t s);
+// seg_voff (nullable, nseg + 1 vertex offsets of batched graphs): seg_coff
+// receives the coarse offsets (coarse ids of a graph stay contiguous).
+tp_graph *contract(const tp_graph *g, const int32_t *C, int32_t *d_map, cudaStream_t s,
+                   const int64_t *seg_voff = nullptr, int64_t nseg = 0,
+                   int64_t *seg_coff = nullptr);
 tp_graph *decompress(const tp_graph *z, cudaStream_t s);
 void initial_partition(const tp_graph *g, int32_t k, int64_t l_max, const tp_params &p,
                        int32_t *d_part, cudaStream_t s);
+// Roots of a bisection forest (batched graphs): root j owns the vertices with
+// node_of[u] == j and assigns blocks off .. off + k - 1; key is the block
+// offset its graph alone would use (it seeds the hashes), l_max its graph's.
+struct IPRoot {
+  int32_t off, key, k;
+  int64_t l_max;
+};
+void initial_partition_roots(const tp_graph *g, const std::vector<IPRoot> &roots,
+                             const int32_t *d_node_of, const tp_params &p, int32_t *d_part,
+                             cudaStream_t s);
 void block_weights(const tp_graph *g, const int32_t *part, int32_t k, int64_t *d_B,
                    cudaStream_t s);
 int64_t edge_cut(const tp_graph *g, const int32_t *part, cudaStream_t s);
