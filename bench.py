@@ -309,8 +309,9 @@ def run_lp_only(args, w):
 
 def run_batch(args, w):
     """Batched mode: the whole batch per step through tp_partition_batch with
-    autotuned knobs and stream count, against the plain single-graph path
-    (the same graphs partitioned one after another on one stream)."""
+    autotuned knobs (one union graph per level), against the plain
+    single-graph path (the same graphs partitioned one after another on one
+    stream)."""
     import torch
 
     import paper_2410_19119_gb300 as tp
@@ -336,17 +337,17 @@ def run_batch(args, w):
     total_n = sum(len(x) - 1 for x, _ in csr)
     total_m2 = sum(len(a) for _, a in csr)
     t0 = time.perf_counter()
-    params, conc, table = autotune.autotune(graphs, ks, EPS, seed=w["seed"])
+    params, table = autotune.autotune(graphs, ks, EPS, seed=w["seed"])
     tune_s = time.perf_counter() - t0
     for _ in range(args.warmup):
-        tp.partition_batch(graphs, ks, EPS, params, concurrency=conc)
+        tp.partition_batch(graphs, ks, EPS, params)
     torch.cuda.synchronize()
     l0 = tp.launch_count()
     times = []
     for _ in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        out = tp.partition_batch(graphs, ks, EPS, params, concurrency=conc)
+        out = tp.partition_batch(graphs, ks, EPS, params)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     launches = tp.launch_count() - l0
@@ -369,8 +370,7 @@ def run_batch(args, w):
         dist.destroy_process_group()
     if rank != 0:
         return
-    knobs = {f: getattr(params, f) for f in ("tier_lane", "tier_small", "tier_mid",
-                                             "warps_per_block")}
+    knobs = {f: getattr(params, f) for f, _ in autotune.KNOBS}
     line = {
         "metric": METRIC, "value": len(graphs) * ws / batch_s, "unit": "graphs/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_s * 1e3,
@@ -381,7 +381,7 @@ def run_batch(args, w):
         "batch_ms": batch_s * 1e3, "plain_single_graph_ms": plain_s * 1e3,
         "speedup_vs_plain": plain_s / batch_s, "identical_to_plain": same,
         "lp_level0_edges_per_s": 5.0 * total_m2 / batch_s,
-        "autotune": {"knobs": knobs, "concurrency": conc, "seconds": tune_s,
+        "autotune": {"knobs": knobs, "seconds": tune_s,
                      "trials": len(table)},
         "generate_s": gen_s, "gpu_launches": launches // max(args.steps, 1),
         "sum_cut": sum(st["cut"] for _, st in out),

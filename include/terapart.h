@@ -76,6 +76,8 @@ typedef struct {
                             kernels directly (results are the same) */
   int32_t graph_n;       /* largest level (vertices, at most 2^19) whose rounds
                             are replayed from a CUDA graph (default 2^19) */
+  int32_t table_slack;   /* hash-table slots per neighbour in the warp tiers,
+                            rounded up to a power of two (2; 1..8) */
 } tp_params;
 
 typedef struct {
@@ -260,17 +262,23 @@ tp_status tp_partition(const tp_graph *g, int32_t k, double eps, const tp_params
 
 /* Batched mode: partitions count independent graphs, graph i into k[i]
  * blocks written to the device buffer d_part[i] (graphs[i]->n entries),
- * with the shared eps and params p (NULL: defaults). Each graph runs the
- * tp_partition path unchanged, so every result equals tp_partition of that
- * graph alone; the call only overlaps the graphs on the device, using
- * `concurrency` host threads that each create, use and destroy one CUDA
- * stream on the calling thread's device (graphs are handed out largest
- * first). The paper partitions one graph at a time; this is the serving
- * side of the method (many small graphs keep the GPU busy only together).
+ * with the shared eps and params p (NULL: defaults). The graphs are laid
+ * side by side in one union graph per level and every step of the
+ * multilevel scheme runs once over the union, each vertex hashing its own
+ * graph's ids and checked against its own graph's caps, so every result
+ * equals tp_partition of that graph alone (stats: the graph's own cut,
+ * levels and sizes; the timings and peak_bytes are the group's). Graphs with
+ * k = 1 or no vertices are trivial; compressed inputs are decompressed
+ * first. Batches beyond 2^28 vertices, 2^30 adjacency entries or 2^15
+ * graphs are cut into groups in input order; up to `concurrency` groups run
+ * at once, each on a CUDA stream that a host thread creates, uses and
+ * destroys on the calling thread's device. The paper partitions one graph
+ * at a time; this is the serving side of the method (many small graphs keep
+ * the GPU busy only together).
  *  - stats (nullable, count entries) and status (nullable, count entries)
  *    receive each graph's stats and status.
- *  - A handle may appear only once (graphs cache per-level state while they
- *    are partitioned); every graph must live on the calling thread's device.
+ *  - A handle may appear only once; every graph must live on the calling
+ *    thread's device.
  *  - Blocks until all graphs are done; returns TP_OK or the first failing
  *    graph's status (in graph order); TP_ERR_INVALID for bad arguments
  *    before any work starts. */

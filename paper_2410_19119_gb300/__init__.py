@@ -290,8 +290,10 @@ def partition(g: Graph, k, eps=0.03, params=None, out=None, stream=None):
 
 
 
-def partition_batch(graphs, ks, eps=0.03, params=None, concurrency=16, outs=None):
-    """Batched mode: partitions independent graphs concurrently (tp_partition_batch).
+def partition_batch(graphs, ks, eps=0.03, params=None, concurrency=1, outs=None):
+    """Batched mode: partitions independent graphs together (tp_partition_batch),
+    one union graph per level; concurrency bounds how many unions (groups of a
+    very large batch) run at once.
 
     Each result equals partition(graphs[i], ks[i], eps, params). Returns a list
     of (part int32 CUDA tensor, stats dict) in input order; raises on the first

@@ -26,7 +26,8 @@ class Params(ctypes.Structure):
     _fields_ = [("seed", u64), ("cluster_rounds", i32), ("refine_rounds", i32),
                 ("sub_rounds", i32), ("c_lim", i32), ("ip_attempts", i32), ("two_hop", i32),
                 ("max_levels", i32), ("tier_lane", i32), ("tier_small", i32), ("tier_mid", i32),
-                ("warps_per_block", i32), ("use_graphs", i32), ("graph_n", i32)]
+                ("warps_per_block", i32), ("use_graphs", i32), ("graph_n", i32),
+                ("table_slack", i32)]
 
 
 class Stats(ctypes.Structure):

@@ -3,31 +3,36 @@
 The knobs only decide which kernel rates a vertex and how work is laid out:
 the degree bounds of the lane and warp tiers (tier_lane, tier_small,
 tier_mid), the warps per block of the warp-per-vertex kernels
-(warps_per_block, which also sets how many 128-slot shared hash tables a
-block holds) and the number of concurrent streams of tp_partition_batch.
-None of them changes a result (integer sums commute and the rating order is
-total), so the tuner may pick any of them by time alone. It times
-partition_batch on a sample of the batch that spans its size range, for each
-candidate, and keeps the fastest: first the stream count with the default
-knobs, then every knob combination at that stream count.
+(warps_per_block) and the hash-table capacity of the warp tiers
+(table_slack: slots per neighbour, so the table a vertex fills and scans has
+the least power of two >= slack * degree slots). None of them changes a
+result (integer sums commute and the rating order is total), so the tuner
+may pick any of them by time alone.
+
+A batch is partitioned as one union graph per level, so the tuner times
+partition_batch on a sample that is itself a union spanning the batch's size
+range (every stride-th graph in size order), and improves one knob at a time
+from the defaults (coordinate descent, one pass): for each knob in turn it
+tries every value with the others held, and keeps the fastest.
 """
-import itertools
 import time
 
 from . import default_params, partition_batch
 
-TIER_LANE = (0, 16, 32)
-TIER_SMALL = (32, 64)
-TIER_MID = (128, 512)
-WARPS_PER_BLOCK = (4, 8)
-CONCURRENCY = (8, 16, 32)
+KNOBS = (
+    ("tier_lane", (0, 16, 32)),
+    ("tier_small", (32, 64)),
+    ("tier_mid", (128, 256, 512)),
+    ("warps_per_block", (4, 8)),
+    ("table_slack", (1, 2, 4)),
+)
 
 
 def candidates():
-    """Every knob combination the tuner tries."""
-    for lane, small, mid, wpb in itertools.product(TIER_LANE, TIER_SMALL, TIER_MID,
-                                                   WARPS_PER_BLOCK):
-        yield {"tier_lane": lane, "tier_small": small, "tier_mid": mid, "warps_per_block": wpb}
+    """Every single-knob variation the tuner may try."""
+    for name, values in KNOBS:
+        for v in values:
+            yield {name: v}
 
 
 def sample_indices(graphs, size):
@@ -39,28 +44,40 @@ def sample_indices(graphs, size):
     return [order[int(j * step)] for j in range(size)]
 
 
-def autotune(graphs, ks, eps=0.03, seed=1, sample=96, repeats=1, concurrency=CONCURRENCY):
-    """Returns (params, concurrency, table): the fastest knob set on the sample,
-    the matching stream count, and every (knobs, concurrency, seconds) timed."""
+def autotune(graphs, ks, eps=0.03, seed=1, sample=512, repeats=1):
+    """Returns (params, table): the fastest knob set found on the sample and
+    every (knobs, seconds) timed."""
     import torch
 
     idx = sample_indices(graphs, sample)
     gs, kk = [graphs[i] for i in idx], [ks[i] for i in idx]
     table = []
+    seen = {}
 
-    def timed(knobs, conc):
+    def timed(knobs):
+        key = tuple(sorted(knobs.items()))
+        if key in seen:
+            return seen[key]
         p = default_params(seed=seed, **knobs)
-        partition_batch(gs, kk, eps, p, concurrency=conc)  # warm-up (allocations)
+        partition_batch(gs, kk, eps, p)  # warm-up (allocations, tier caches)
         dt = float("inf")
         for _ in range(repeats):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            partition_batch(gs, kk, eps, p, concurrency=conc)
+            partition_batch(gs, kk, eps, p)
             torch.cuda.synchronize()
             dt = min(dt, time.perf_counter() - t0)
-        table.append((dict(knobs), conc, dt))
+        table.append((dict(knobs), dt))
+        seen[key] = dt
         return dt
 
-    conc = min(concurrency, key=lambda c: timed({}, c))
-    knobs = min(candidates(), key=lambda kn: timed(kn, conc))
-    return default_params(seed=seed, **knobs), conc, table
+    d = default_params()
+    best = {name: getattr(d, name) for name, _ in KNOBS}
+    best_t = timed(best)
+    for name, values in KNOBS:
+        for v in values:
+            trial = dict(best, **{name: v})
+            t = timed(trial)
+            if t < best_t:
+                best, best_t = trial, t
+    return default_params(seed=seed, **best), table

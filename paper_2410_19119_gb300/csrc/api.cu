@@ -80,6 +80,7 @@ void tp_params_default(tp_params *p) {
   p->warps_per_block = 8;
   p->use_graphs = 1;
   p->graph_n = 1 << 19;
+  p->table_slack = 2;
 }
 
 const char *tp_status_string(tp_status s) {

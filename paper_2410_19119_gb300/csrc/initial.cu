@@ -26,6 +26,8 @@ namespace tp {
 
 namespace {
 
+// Threads per attempt: 1024 for large nodes or few attempts in flight,
+// 256 or 128 when many small nodes share the GPU (several CTAs per SM).
 constexpr int kIPThreads = 1024;
 
 struct IPCtx {
@@ -55,27 +57,30 @@ struct IPCtx {
   int64_t *cut;  // nodes * T
 };
 
+template <int NT>
 __device__ __forceinline__ int64_t bscan_excl(int64_t v, int64_t &total) {
-  __shared__ int64_t ws[kIPThreads / 32];
+  constexpr int NW = NT / 32;
+  __shared__ int64_t ws[NW];
   int l = lane_id(), w = threadIdx.x >> 5;
   int64_t incl = warp_incl_scan(v);
   if (l == 31) ws[w] = incl;
   __syncthreads();
   if (w == 0) {
-    int64_t x = l < kIPThreads / 32 ? ws[l] : 0;
+    int64_t x = l < NW ? ws[l] : 0;
     x = warp_incl_scan(x);
-    if (l < kIPThreads / 32) ws[l] = x;
+    if (l < NW) ws[l] = x;
   }
   __syncthreads();
   int64_t off = w > 0 ? ws[w - 1] : 0;
-  total = ws[kIPThreads / 32 - 1];
+  total = ws[NW - 1];
   __syncthreads();
   return off + incl - v;
 }
 
+template <int NT>
 __device__ __forceinline__ int64_t bsum(int64_t v) {
   int64_t t;
-  bscan_excl(v, t);
+  bscan_excl<NT>(v, t);
   return t;
 }
 
@@ -207,13 +212,14 @@ __global__ void k_local_fill(const int64_t *xadj, const int32_t *adj, const int6
 }
 
 // Exclusive scan of x[0..len) in place, block-wide; returns the total.
+template <int NT>
 __device__ int64_t block_scan_array(int32_t *x, int64_t len) {
   int64_t carry = 0;
   for (int64_t q0 = 0; q0 < len; q0 += blockDim.x) {
     const int64_t q = q0 + threadIdx.x;
     const int64_t v = q < len ? x[q] : 0;
     int64_t tot;
-    const int64_t ex = bscan_excl(v, tot);
+    const int64_t ex = bscan_excl<NT>(v, tot);
     if (q < len) x[q] = (int32_t)(carry + ex);
     carry += tot;
   }
@@ -221,7 +227,8 @@ __device__ int64_t block_scan_array(int32_t *x, int64_t len) {
   return carry;
 }
 
-__global__ void __launch_bounds__(kIPThreads, 1) k_bisect(IPCtx c) {
+template <int NT>
+__global__ void __launch_bounds__(NT, kIPThreads / NT) k_bisect(IPCtx c) {
   const int32_t j = blockIdx.x / c.T, a = blockIdx.x % c.T;
   const int64_t nb = c.nstart[j], ns = c.nstart[j + 1] - nb;
   const int64_t R = (int64_t)a * c.n + nb;  // scratch region of this attempt
@@ -267,7 +274,7 @@ __global__ void __launch_bounds__(kIPThreads, 1) k_bisect(IPCtx c) {
       if (lane == 0) cnt[i - fb] = k;
     }
     __syncthreads();
-    const int64_t carry = block_scan_array(cnt, fe - fb);
+    const int64_t carry = block_scan_array<NT>(cnt, fe - fb);
     // claimed neighbours in frontier order, then adjacency order
     for (int64_t i = fb + warp; i < fe; i += nwarps) {
       int64_t pos = tail + cnt[i - fb];
@@ -290,7 +297,7 @@ __global__ void __launch_bounds__(kIPThreads, 1) k_bisect(IPCtx c) {
       int64_t x = x0 + threadIdx.x;
       int64_t f = x < ns && !disc[x];
       int64_t tot;
-      int64_t ex = bscan_excl(f, tot);
+      int64_t ex = bscan_excl<NT>(f, tot);
       if (f) ord[tail + carry + ex] = (int32_t)x;
       carry += tot;
     }
@@ -301,7 +308,7 @@ __global__ void __launch_bounds__(kIPThreads, 1) k_bisect(IPCtx c) {
   __shared__ int64_t sh_nact;
   int64_t W = 0;
   for (int64_t x = threadIdx.x; x < ns; x += blockDim.x) W += cw(x);
-  W = bsum(W);
+  W = bsum<NT>(W);
   const int64_t target0 = (int64_t)(((__int128)W * k0) / kk);
   const int64_t caps[2] = {(int64_t)k0 * c.nlmax[j], (int64_t)k1 * c.nlmax[j]};
   {
@@ -310,7 +317,7 @@ __global__ void __launch_bounds__(kIPThreads, 1) k_bisect(IPCtx c) {
       int64_t q = q0 + threadIdx.x;
       int64_t w = q < ns ? cw(ord[q]) : 0;
       int64_t tot;
-      int64_t incl = carry + bscan_excl(w, tot) + w;
+      int64_t incl = carry + bscan_excl<NT>(w, tot) + w;
       if (q < ns) {
         bool in0 = incl <= target0;
         side[ord[q]] = in0 ? 0 : 1;
@@ -318,7 +325,7 @@ __global__ void __launch_bounds__(kIPThreads, 1) k_bisect(IPCtx c) {
       }
       carry += tot;
     }
-    w0 = bsum(w0);
+    w0 = bsum<NT>(w0);
     if (threadIdx.x == 0) lw[0] = w0, lw[1] = W - w0;
     __syncthreads();
   }
@@ -336,7 +343,7 @@ __global__ void __launch_bounds__(kIPThreads, 1) k_bisect(IPCtx c) {
           const int64_t x = x0 + threadIdx.x;
           const int64_t f = x < ns && sub[x] == s;
           int64_t tot;
-          const int64_t ex = bscan_excl(f, tot);
+          const int64_t ex = bscan_excl<NT>(f, tot);
           if (f) cnt[carry + ex] = (int32_t)x;
           carry += tot;
         }
@@ -409,7 +416,7 @@ __global__ void __launch_bounds__(kIPThreads, 1) k_bisect(IPCtx c) {
       if (in && side[y] != sx) cutv += w;
     });
   }
-  cutv = bsum(cutv);
+  cutv = bsum<NT>(cutv);
   if (threadIdx.x == 0) c.cut[blockIdx.x] = cutv / 2;
 }
 
@@ -511,7 +518,13 @@ void initial_partition_roots(const tp_graph *g, const std::vector<IPRoot> &roots
     TP_LAUNCH_CHECK();
     radix_sort_pairs(keys.get(), nullptr, n, 64, s);
     exclusive_scan_i64(nstart.get(), nstart.get(), nodes, s);
-    int64_t m = read_scalar(nstart.get() + nodes, s);
+    std::vector<int64_t> hstart((size_t)nodes + 1);
+    TP_CUDA(cudaMemcpyAsync(hstart.data(), nstart.get(), (nodes + 1) * sizeof(int64_t),
+                            cudaMemcpyDeviceToHost, s));
+    TP_CUDA(cudaStreamSynchronize(s));
+    const int64_t m = hstart[(size_t)nodes];
+    int64_t max_ns = 0;
+    for (int32_t jn = 0; jn < nodes; ++jn) max_ns = std::max(max_ns, hstart[jn + 1] - hstart[jn]);
     if (m) {
       launch(k_node_lists, grid_for(m, 256), 256, 0, s, keys.get(), nstart.get(), m, vlist.get(), loc.get());
       TP_LAUNCH_CHECK();
@@ -591,7 +604,12 @@ void initial_partition_roots(const tp_graph *g, const std::vector<IPRoot> &roots
     c.mvg0 = mvg0.get(), c.mvg1 = mvg1.get();
     c.sub = sub.get();
     c.cut = cut.get();
-    launch(k_bisect, (unsigned)(nodes * T), kIPThreads, 0, s, c);
+    // small nodes with enough attempts in flight: smaller CTAs, several per SM
+    const int64_t ctas = (int64_t)nodes * T;
+    const bool many = ctas >= 4LL * num_sms();
+    if (many && max_ns <= 512) launch(k_bisect<128>, (unsigned)ctas, 128, 0, s, c);
+    else if (many && max_ns <= 4096) launch(k_bisect<256>, (unsigned)ctas, 256, 0, s, c);
+    else launch(k_bisect<kIPThreads>, (unsigned)ctas, kIPThreads, 0, s, c);
     TP_LAUNCH_CHECK();
     launch(k_fill_i32, grid_for(n, 256), 256, 0, s, next_node.get(), n, -1);
     launch(k_pick, (unsigned)nodes, 256, 0, s, c, d_c0, d_c1, next_node.get(), d_part);

@@ -4,17 +4,22 @@
 // Rating (Section "Rating Maps", Algorithm 2): a vertex's ratings R[C[v]] +=
 // w(u,v) accumulate in a hash table. The paper's split into a first phase
 // with small per-thread tables and a second phase for "bumped" high-degree
-// vertices becomes four degree tiers, each a different kernel:
-//   small (deg <= tier_small): one warp per vertex, 128-slot shared table, and
-//          for one-window unit-weight neighbourhoods no table at all (lanes
-//          with equal labels are grouped by __match_any_sync);
-//   mid   (deg <= tier_mid):   one warp per vertex, 1024-slot shared table;
-//   big   (deg <= 10000):      one warp per vertex, table in global memory;
-//   huge  (deg > 10000):       one warp per chunk of 1000 neighbours (the
+// vertices becomes five degree tiers, each a different kernel:
+//   lane  (deg <= tier_lane):  one lane per vertex, labels sorted in
+//          registers (no table at all);
+//   small (deg <= tier_small): one warp per vertex, shared table of up to
+//          128 slots;
+//   mid   (deg <= tier_mid):   one warp per vertex, shared table of up to
+//          1024 slots (both warp tiers fill and scan only the least power of
+//          two >= table_slack * degree slots, at least 32);
+//   big   (deg <= 10000):      one block per vertex, shared table of 8192 or
+//          16384 slots;
+//   huge  (deg > 10000):       one block per chunk of 1000 neighbours (the
 //          compressed format's independently decodable chunks) aggregates in
 //          a shared table and flushes into the vertex's global table with
 //          atomics (the paper's "hash tables as flush buffers" against
-//          contention); one block per vertex then scans that table.
+//          contention); blocks then scan that table in segments and one
+//          block per vertex combines the segments' results.
 // The tier only decides where the sums are formed; integer sums commute and
 // the argmax uses a total order, so the result is tier-independent.
 //
@@ -48,6 +53,7 @@ struct RateCtx {
   uint64_t rk;
   const uint64_t *rk_dev;  // if set, the round key is read here (replayed round graphs)
   int32_t S, s;
+  int32_t slack;  // warp tiers: table slots per neighbour (power of two)
   // M_LP outputs
   int32_t *mv_u, *mv_t, *mv_o;
   int64_t *mv_g;
@@ -158,6 +164,17 @@ __device__ __forceinline__ TieKey tie_key(const RateCtx &c, int64_t u) {
     lb = c.seg.lb[g];
   }
   return TieKey{hstep(hstep(rk_of(c), (uint64_t)(u - vb)), kTagTie), kGamma - (uint64_t)lb};
+}
+// The lane tier decides batched graphs at compile time (SEG), so the one-graph
+// kernels carry no per-graph lookups in their tight register budget.
+template <bool SEG>
+__device__ __forceinline__ int64_t lane_cap(const RateCtx &c, int64_t u) {
+  return SEG ? c.seg.cap[c.seg.gid[u]] : c.cap;
+}
+template <int MODE, bool SEG>
+__device__ __forceinline__ TieKey lane_tie_key(const RateCtx &c, int64_t u) {
+  if (SEG) return tie_key<MODE>(c, u);
+  return TieKey{hstep(hstep(rk_of(c), (uint64_t)u), kTagTie), kGamma};
 }
 
 __device__ __forceinline__ uint32_t slot_of(int32_t x, int logcap) {
@@ -341,6 +358,15 @@ __device__ void rate_vertex_warp(const RateCtx &c, int64_t u, int32_t *keys, int
   finalize_warp<MODE>(c, b, u, cu, mb);
 }
 
+// Warp tiers: the table of a degree-d vertex uses the first 2^lc slots,
+// the least power of two >= slack * d (at least 32, at most 2^maxlog); only
+// those are scanned and cleared.
+__device__ __forceinline__ int table_log(const RateCtx &c, int64_t d, int maxlog) {
+  int lc = 5;
+  while (lc < maxlog && ((int64_t)1 << lc) < c.slack * d) ++lc;
+  return lc;
+}
+
 // Shared memory per warp: table keys + values, then the mover buffer.
 template <int LOG>
 struct WarpSmem {
@@ -372,8 +398,10 @@ __global__ void k_rate_small(RateCtx c) {
     tier_range(c, kb, ke);
     for (int64_t k = kb + gw; k < ke; k += nw) {
       int64_t i, u;
-      if (tier_entry<MODE>(c, k, i, u))
-        rate_vertex_warp<COMP, MODE>(c, u, ws.keys, ws.vals, kSmallLog, true, &mb);
+      if (tier_entry<MODE>(c, k, i, u)) {
+        const int64_t d = COMP ? zip_nbr(c.g, u).deg : c.g.xadj[u + 1] - c.g.xadj[u];
+        rate_vertex_warp<COMP, MODE>(c, u, ws.keys, ws.vals, table_log(c, d, kSmallLog), true, &mb);
+      }
     }
   } else {
     for (int64_t base = gw * 32; base < c.g.n; base += nw * 32) {
@@ -384,7 +412,9 @@ __global__ void k_rate_small(RateCtx c) {
       while (am) {
         int j = __ffs(am) - 1;
         am &= am - 1;
-        rate_vertex_warp<COMP, MODE>(c, base + j, ws.keys, ws.vals, kSmallLog, true, &mb);
+        const int64_t v = base + j;
+        const int64_t d = COMP ? zip_nbr(c.g, v).deg : c.g.xadj[v + 1] - c.g.xadj[v];
+        rate_vertex_warp<COMP, MODE>(c, v, ws.keys, ws.vals, table_log(c, d, kSmallLog), true, &mb);
       }
     }
   }
@@ -593,7 +623,7 @@ __device__ __forceinline__ void emit_lane(const RateCtx &c, bool has, int32_t u,
 // already decoded into the column; CSR: adjacency from xadj[u]) and emits
 // the favourite, or queues the move in the warp's window buffer (nmv
 // records so far, warp-uniform). N >= the largest degree of the batch.
-template <bool COMP, int MODE, bool W, int N>
+template <bool COMP, int MODE, bool W, int N, bool SEG>
 __device__ __forceinline__ void lane_batch(const RateCtx &c, bool has, int32_t u, int deg,
                                            uint32_t *col, uint32_t *wcol, uint8_t *cnt,
                                            LaneMovers &mb, int &nmv) {
@@ -630,8 +660,8 @@ __device__ __forceinline__ void lane_batch(const RateCtx &c, bool has, int32_t u
     const int64_t cu = has ? node_w(c.g, u) : 1;
     LaneCand best{-1, 0xffffffffu, INT32_MAX};
     if (MODE == M_FAV ? rmax > 0 : rmax > rown) {
-      const TieKey hv = tie_key<MODE>(c, u);
-      const int64_t capu = cap_of(c, u);
+      const TieKey hv = lane_tie_key<MODE, SEG>(c, u);
+      const int64_t capu = lane_cap<SEG>(c, u);
       // the best candidate overall is tied at the top rating
       LaneCand b1{-1, 0xffffffffu, INT32_MAX};
       for (int k = 0; k < ncand; ++k) {
@@ -696,8 +726,8 @@ __device__ __forceinline__ void lane_batch(const RateCtx &c, bool has, int32_t u
     const int64_t cu = has ? node_w(c.g, u) : 1;
     LaneCand best{-1, 0xffffffffu, INT32_MAX};
     if (MODE == M_FAV ? rmax > 0 : rmax > rown) {
-      const TieKey hv = tie_key<MODE>(c, u);
-      const int64_t capu = cap_of(c, u);
+      const TieKey hv = lane_tie_key<MODE, SEG>(c, u);
+      const int64_t capu = lane_cap<SEG>(c, u);
       // the best candidate overall is tied at the top rating
       LaneCand b1{-1, 0xffffffffu, INT32_MAX};
       for (int k = 0; k < ncand; ++k) {
@@ -755,14 +785,14 @@ __device__ __forceinline__ void lane_batch(const RateCtx &c, bool has, int32_t u
     bool have_hv = false;
     LaneCand b1{rmax, 0u, x1};
     if (go && ntop >= 2) {
-      hv = tie_key<MODE>(c, u);
+      hv = lane_tie_key<MODE, SEG>(c, u);
       have_hv = true;
       const LaneCand c1{rmax, tie_of(hv, x1), x1}, c2{rmax, tie_of(hv, x2), x2};
       b1 = lane_better(c1, c2) ? c1 : c2;
     }
     const bool many = go && ntop >= 3;
     bool full = false;
-    const int64_t capu = go && MODE != M_FAV ? cap_of(c, u) : 0;
+    const int64_t capu = go && MODE != M_FAV ? lane_cap<SEG>(c, u) : 0;
     if (go && MODE != M_FAV) full = c.lw[b1.x] + cu > capu;
     // rare: three or more labels tied at the top, or the winner is full;
     // the sorted labels go to this lane's column and the runs are walked
@@ -770,7 +800,7 @@ __device__ __forceinline__ void lane_batch(const RateCtx &c, bool has, int32_t u
 #pragma unroll
       for (int i = 0; i < N; ++i) ccol[i * 32] = a[i];
       if (many || full) {
-        if (!have_hv) hv = tie_key<MODE>(c, u);
+        if (!have_hv) hv = lane_tie_key<MODE, SEG>(c, u);
         const int own_run = rown + (N - deg);  // the own label's entries, padding included
         LaneCand bb{-1, 0xffffffffu, INT32_MAX};
         for (int i = 0; i < N;) {
@@ -828,7 +858,7 @@ __host__ __device__ constexpr int lane_warps() { return W ? 4 : kLaneWarps; }
 
 // LONG: some compressed records exceed the 80-byte window (skewed graphs);
 // a separate instantiation keeps the common kernel free of that path.
-template <bool COMP, int MODE, bool W, bool LONG = false>
+template <bool COMP, int MODE, bool W, bool LONG = false, bool SEG = false>
 __global__ void __launch_bounds__(lane_warps<W>() * 32, W ? 1 : kLaneBlocksPerSM)
     k_rate_lane(RateCtx c) {
   static_assert(!(COMP && W), "weighted levels are CSR");
@@ -910,8 +940,8 @@ __global__ void __launch_bounds__(lane_warps<W>() * 32, W ? 1 : kLaneBlocksPerSM
         }
       }
       const unsigned maxdeg = __reduce_max_sync(kFull, (unsigned)deg);
-      if (maxdeg <= 16) lane_batch<COMP, MODE, W, 16>(c, has, u, deg, col, wcol, cnt, mb, nmv);
-      else lane_batch<COMP, MODE, W, kLaneMaxDeg>(c, has, u, deg, col, wcol, cnt, mb, nmv);
+      if (maxdeg <= 16) lane_batch<COMP, MODE, W, 16, SEG>(c, has, u, deg, col, wcol, cnt, mb, nmv);
+      else lane_batch<COMP, MODE, W, kLaneMaxDeg, SEG>(c, has, u, deg, col, wcol, cnt, mb, nmv);
     }
     __syncwarp();
     if (nmv) {  // the window's movers, coalesced
@@ -961,12 +991,8 @@ __global__ void k_rate_list(RateCtx c) {
       int64_t off = c.tbase + c.toff[i];
       rate_vertex_warp<COMP, MODE>(c, u, c.tkeys + off, c.tvals + off, c.tcap[i], false, &mb);
     } else {
-      // use (and afterwards scan and clear) only the first power of two >= 2 deg
-      // slots of the warp's table
       const int64_t d = COMP ? zip_nbr(c.g, u).deg : c.g.xadj[u + 1] - c.g.xadj[u];
-      int lc = kSmallLog;
-      while (lc < kMidLog && ((int64_t)1 << lc) < 2 * d) ++lc;
-      rate_vertex_warp<COMP, MODE>(c, u, wsp->keys, wsp->vals, lc, false, &mb);
+      rate_vertex_warp<COMP, MODE>(c, u, wsp->keys, wsp->vals, table_log(c, d, kMidLog), false, &mb);
     }
   }
   if (MODE == M_LP) flush_movers(c, mb);
@@ -1639,6 +1665,11 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
   TierCache &T = g->tiers;
   c.g = view(g);
   c.tier = T.tier.get();
+  {  // table slots per neighbour: a power of two in 1..8
+    const int32_t sl = std::max(1, std::min(8, p.table_slack));
+    c.slack = 1;
+    while (c.slack < sl) c.slack <<= 1;
+  }
   c.tkeys = T.tkeys.get();
   c.tvals = T.tvals.get();
   c.tlist = T.tlist.get();
@@ -1666,14 +1697,17 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
     if (g->unit_ew) {
       unsigned blocks = (unsigned)std::min<int64_t>(
           (g->n + 256 * kLaneWarps - 1) / (256 * kLaneWarps), (int64_t)sms * kLaneBlocksPerSM);
+      // batched graphs are CSR unions
       if (comp && T.lane_long) launch(k_rate_lane<true, LM, false, true>, blocks, 32 * kLaneWarps, 0, s, c);
       else if (comp) launch(k_rate_lane<true, LM, false>, blocks, 32 * kLaneWarps, 0, s, c);
+      else if (c.seg.gid) launch(k_rate_lane<false, LM, false, false, true>, blocks, 32 * kLaneWarps, 0, s, c);
       else launch(k_rate_lane<false, LM, false>, blocks, 32 * kLaneWarps, 0, s, c);
     } else {  // weighted levels are CSR
       constexpr int WW = lane_warps<true>();
       unsigned blocks =
           (unsigned)std::min<int64_t>((g->n + 256 * WW - 1) / (256 * WW), (int64_t)sms * 16);
-      launch(k_rate_lane<false, LM, true>, blocks, 32 * WW, 0, s, c);
+      if (c.seg.gid) launch(k_rate_lane<false, LM, true, false, true>, blocks, 32 * WW, 0, s, c);
+      else launch(k_rate_lane<false, LM, true>, blocks, 32 * WW, 0, s, c);
     }
     TP_LAUNCH_CHECK();
     if (prof) prof_end(PF_RATE_LANE, s, per_launch * tier_round_bytes(g, n_lane, T.edges[TIER_LANE]));

@@ -63,10 +63,9 @@ def test_batch_rejects_bad_arguments(small_batch):
 def test_autotune_picks_a_result_preserving_setting(small_batch):
     recipe, _, graphs = small_batch
     ks = [s["k"] for s in recipe]
-    p, conc, table = autotune.autotune(graphs[:12], ks[:12], sample=6, repeats=1,
-                                       concurrency=(2, 4))
-    assert conc in (2, 4) and len(table) == 2 + len(list(autotune.candidates()))
-    tuned = tp.partition_batch(graphs[:12], ks[:12], 0.03, p, concurrency=conc)
+    p, table = autotune.autotune(graphs[:12], ks[:12], sample=6, repeats=1)
+    assert 1 <= len(table) <= 1 + len(list(autotune.candidates()))
+    tuned = tp.partition_batch(graphs[:12], ks[:12], 0.03, p)
     plain = tp.partition_batch(graphs[:12], ks[:12], 0.03, tp.default_params(), concurrency=1)
     for (a, _), (b, _) in zip(tuned, plain):
         assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())

@@ -82,9 +82,12 @@ def test_autotune_candidates_and_sample():
 
     cands = list(autotune.candidates())
     keys = {tuple(sorted(c.items())) for c in cands}
-    assert len(keys) == len(cands) == (len(autotune.TIER_LANE) * len(autotune.TIER_SMALL) *
-                                       len(autotune.TIER_MID) * len(autotune.WARPS_PER_BLOCK))
-    assert all(c["tier_mid"] <= 512 for c in cands)  # the mid tier's table holds degree <= 512
+    assert len(keys) == len(cands) == sum(len(v) for _, v in autotune.KNOBS)
+    assert all(c.get("tier_mid", 0) <= 512 for c in cands)  # the mid table holds degree <= 512
+    assert {v for c in cands for k, v in c.items() if k == "table_slack"} <= {1, 2, 4, 8}
+    import paper_2410_19119_gb300 as tp
+    fields = {f for f, _ in tp._lib.Params._fields_}
+    assert all(k in fields for c in cands for k in c)  # every knob is a tp_params field
 
     class G:
         def __init__(self, n, m2):
