@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <unordered_map>
 #include <mutex>
 #include <new>
 
@@ -30,9 +31,43 @@ int64_t mem_mark() {
 }
 int64_t mem_peak_since(int64_t mark) { return t_peak - mark; }
 
+// Opt-in (environment TP_MEM_TRACE=1): the sizes of the buffers live at this
+// thread's high-water mark, printed by mem_trace_dump (a diagnostic of what a
+// call's peak consists of).
+static bool mem_trace_on() {
+  static const bool on = getenv("TP_MEM_TRACE") != nullptr;
+  return on;
+}
+thread_local std::unordered_map<void *, int64_t> *t_live_bufs = nullptr;
+thread_local std::vector<int64_t> *t_peak_bufs = nullptr;
+
 static void mem_add(int64_t b) {
   t_live += b;
-  if (t_live > t_peak) t_peak = t_live;
+  if (t_live > t_peak) {
+    t_peak = t_live;
+    if (mem_trace_on() && t_live_bufs) {
+      if (!t_peak_bufs) t_peak_bufs = new std::vector<int64_t>();
+      t_peak_bufs->clear();
+      for (const auto &kv : *t_live_bufs) t_peak_bufs->push_back(kv.second);
+    }
+  }
+}
+
+static void mem_track(void *p, int64_t b) {
+  if (!mem_trace_on()) return;
+  if (!t_live_bufs) t_live_bufs = new std::unordered_map<void *, int64_t>();
+  if (b > 0) (*t_live_bufs)[p] = b;
+  else t_live_bufs->erase(p);
+}
+
+void mem_trace_dump(const char *what) {
+  if (!mem_trace_on() || !t_peak_bufs) return;
+  std::vector<int64_t> v = *t_peak_bufs;
+  std::sort(v.begin(), v.end(), std::greater<int64_t>());
+  fprintf(stderr, "terapart mem: %s peak %.3f GB in %zu buffers; largest (GB):", what,
+          (double)t_peak / 1e9, v.size());
+  for (size_t i = 0; i < v.size() && i < 16; ++i) fprintf(stderr, " %.3f", (double)v[i] / 1e9);
+  fprintf(stderr, "\n");
 }
 
 void *dev_alloc(size_t bytes, cudaStream_t s, const AllocHook **from) {
@@ -49,6 +84,7 @@ void *dev_alloc(size_t bytes, cudaStream_t s, const AllocHook **from) {
       throw Error{e == cudaErrorMemoryAllocation ? TP_ERR_OOM : TP_ERR_CUDA};
     }
   }
+  mem_track(p, (int64_t)bytes);
   mem_add((int64_t)bytes);
   *from = h;
   return p;
@@ -57,6 +93,7 @@ void *dev_alloc(size_t bytes, cudaStream_t s, const AllocHook **from) {
 void dev_free(void *p, size_t bytes, cudaStream_t s, const AllocHook *from) {
   if (!p) return;
   t_live -= (int64_t)bytes;
+  mem_track(p, 0);
   if (from && from->free) {
     from->free(p, bytes, (void *)s, from->ctx);
     return;
@@ -430,17 +467,33 @@ void build_tiers(tp_graph *g, const tp_params &p, cudaStream_t s) {
     T.n_huge_segs = read_scalar(T.huge_seg_start.get() + T.n_huge, s);
     T.huge_seg_best.alloc((size_t)T.n_huge_segs * kSegBestBytes, s);
   }
-  int64_t total = T.huge_slots;
-  if (total) {
-    T.tkeys.alloc(total, s);
-    T.tvals.alloc(total, s);
-    T.tlist.alloc(total / 2 + 1, s);
+  if (T.huge_slots) {
     T.tcount.alloc(std::max<int64_t>(T.n_huge, 1), s);
     TP_CUDA(cudaMemsetAsync(T.tcount.get(), 0, sizeof(int32_t) * std::max<int64_t>(T.n_huge, 1), s));
-    launch(k_fill_table, grid_for(total, 256), 256, 0, s, T.tkeys.get(), T.tvals.get(), total);
-    TP_LAUNCH_CHECK();
   }
   T.built = true;
+}
+
+// The hubs' global rating tables (2 to 4 slots of 14 bytes per hub
+// neighbour) exist only while a rating call needs them: allocated empty on
+// first use, left empty by every rating launch, freed when the call ends.
+void ensure_hub_tables(tp_graph *g, cudaStream_t s) {
+  TierCache &T = g->tiers;
+  const int64_t total = T.huge_slots;
+  if (!total || T.tkeys.get()) return;
+  T.tkeys.alloc(total, s);
+  T.tvals.alloc(total, s);
+  T.tlist.alloc(total / 2 + 1, s);
+  launch(k_fill_table, grid_for(total, 256), 256, 0, s, T.tkeys.get(), T.tvals.get(), total);
+  TP_LAUNCH_CHECK();
+}
+
+void release_hub_tables(tp_graph *g, cudaStream_t s) {
+  TierCache &T = g->tiers;
+  T.tkeys.s = T.tvals.s = T.tlist.s = s;
+  T.tkeys.release();
+  T.tvals.release();
+  T.tlist.release();
 }
 
 // ---------------------------------------------------------------- compression

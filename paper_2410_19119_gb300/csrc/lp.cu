@@ -1662,6 +1662,7 @@ double tier_round_bytes(const tp_graph *g, int64_t n_t, int64_t e_t) {
 template <int MODE>
 void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
   build_tiers(g, p, s);
+  ensure_hub_tables(g, s);
   TierCache &T = g->tiers;
   c.g = view(g);
   c.tier = T.tier.get();
@@ -2260,6 +2261,7 @@ bool lp_rounds_graph(tp_graph *g, const LpState &st, LpWork &w, uint64_t seed, u
                      cudaStream_t stream) {
   configure_kernels();
   build_tiers(g, p, stream);  // synchronises; must not run while capturing
+  ensure_hub_tables(g, stream);  // nor may the tables be allocated inside the capture
   const int64_t nblocks = (g->n + kBucketSpan - 1) / kBucketSpan;
   if (S > 32 || S * nblocks > 2048) return false;
   if (!w.bucket.get()) w.bucket.alloc(std::max<int64_t>(w.n, 1), stream);
@@ -2476,6 +2478,7 @@ void lp_cluster(tp_graph *g, int64_t U, const tp_params &p, int32_t level, int32
   if (ev_end) TP_CUDA(cudaEventRecord(ev_end, s));
   prof_scope(false);
   if (p.two_hop) two_hop(g, d_cluster, Wc.get(), U, p.seed, level, p, s, seg ? &st.seg : nullptr);
+  release_hub_tables(g, s);
 }
 
 void lp_refine(tp_graph *g, int32_t k, int64_t l_max, const tp_params &p, int32_t level,
@@ -2486,6 +2489,7 @@ void lp_refine(tp_graph *g, int32_t k, int64_t l_max, const tp_params &p, int32_
   LpState st{d_part, d_B, k, l_max};
   if (seg) st.seg = *seg;
   lp_rounds(g, st, w, p.seed, kTagRefine, (uint64_t)level, 0, p.refine_rounds, p.sub_rounds, p, s);
+  release_hub_tables(g, s);
 }
 
 // ---------------------------------------------------------------- rebalancing

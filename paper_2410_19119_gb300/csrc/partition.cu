@@ -185,6 +185,7 @@ void partition(tp_graph *g0, int32_t k, int64_t eps_ppm, const tp_params &p, int
       }
       levels.push_back(cg);
       maps.push_back(std::move(map));
+      mem_trace_dump(level == 0 ? "after contracting level 0" : "after contracting a level");
       S.level_n[levels.size() - 1] = cg->n;
       S.level_m2[levels.size() - 1] = cg->m2;
     }
@@ -203,6 +204,7 @@ void partition(tp_graph *g0, int32_t k, int64_t eps_ppm, const tp_params &p, int
   ip_csr.reset();
   t_phase.stop();
   S.ms_initial = t_phase.ms();
+  mem_trace_dump("after initial partitioning");
   t_phase.start();
   for (int32_t l = L; l >= 0; --l) {
     tp_graph *g = levels[l];
@@ -234,6 +236,7 @@ void partition(tp_graph *g0, int32_t k, int64_t eps_ppm, const tp_params &p, int
   int64_t perfect = (W + k - 1) / k;
   S.imbalance = perfect > 0 ? (double)mx / (double)perfect - 1.0 : 0.0;
   S.peak_bytes = mem_peak_since(mark);
+  mem_trace_dump("tp_partition");
   int32_t e = read_scalar(g0->err.get(), s);
   TP_REQUIRE(e == 0, (tp_status)e);
 }

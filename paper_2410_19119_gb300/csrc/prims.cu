@@ -229,7 +229,8 @@ int bits_for(uint64_t v) {
   return b;
 }
 
-void radix_sort_pairs(uint64_t *keys, uint64_t *vals, int64_t n, int bits, cudaStream_t s) {
+void radix_sort_pairs(uint64_t *keys, uint64_t *vals, int64_t n, int bits, cudaStream_t s,
+                      int lo) {
   if (n <= 1 || bits <= 0) return;
   int passes = (bits + 7) / 8;
   int64_t nwarps = (n + kSortWarpTile - 1) / kSortWarpTile;
@@ -240,7 +241,7 @@ void radix_sort_pairs(uint64_t *keys, uint64_t *vals, int64_t n, int bits, cudaS
   Buf<int64_t> offs(256 * nwarps + 1, s);
   uint64_t *ka = keys, *kb = tk.get(), *va = vals, *vb = vals ? tv.get() : nullptr;
   for (int p = 0; p < passes; ++p) {
-    int shift = 8 * p;
+    int shift = lo + 8 * p;
     launch(k_sort_hist, blocks, kSortWarps * 32, 0, s, ka, n, shift, nwarps, counts.get());
     TP_LAUNCH_CHECK();
     scan<uint32_t, int64_t, SumOp>(counts.get(), offs.get(), 256 * nwarps, true,

@@ -63,6 +63,8 @@ void dev_free(void *p, size_t bytes, cudaStream_t s, const AllocHook *from);
 // returns the current holding; mem_peak_since(mark) is the rise since then.
 int64_t mem_mark();
 int64_t mem_peak_since(int64_t mark);
+// With TP_MEM_TRACE set: prints the buffers live at this thread's peak.
+void mem_trace_dump(const char *what);
 
 // Owning, stream-ordered device buffer.
 template <class T>
@@ -337,7 +339,9 @@ void exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, cudaS
 void inclusive_max_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
 // Stable LSD radix sort of (key, value) pairs by the low `bits` key bits.
 // vals may be null. Buffers are sorted in place (temporary storage internal).
-void radix_sort_pairs(uint64_t *keys, uint64_t *vals, int64_t n, int bits, cudaStream_t s);
+// lo: the sort key is bits lo .. lo + bits - 1 (lower bits ride along).
+void radix_sort_pairs(uint64_t *keys, uint64_t *vals, int64_t n, int bits, cudaStream_t s,
+                      int lo = 0);
 // Reads one device value synchronously.
 template <class T>
 T read_scalar(const T *d, cudaStream_t s) {
@@ -353,6 +357,9 @@ int64_t max_i64(const int64_t *d, int64_t n, cudaStream_t s);  // 0 for n == 0; 
 tp_graph *new_graph();
 void compute_degrees(const tp_graph *g, int64_t *d_deg, cudaStream_t s);  // n entries
 void build_tiers(tp_graph *g, const tp_params &p, cudaStream_t s);
+// Hub rating tables: allocated (empty) for a rating call, released after it.
+void ensure_hub_tables(tp_graph *g, cudaStream_t s);
+void release_hub_tables(tp_graph *g, cudaStream_t s);
 
 // ---------------------------------------------------------------- LP (lp.cu)
 // Batched graphs: one union graph holds many graphs side by side (each a
