@@ -45,6 +45,10 @@ WORKLOADS = {
     "rmat26": dict(gen="rmat", scale=26, ef=16, k=256, seed=1,
                    desc="R-MAT scale 26 edge factor 16 (0.57,0.19,0.19,0.05), symmetrised, "
                         "deduplicated, k=256, eps=0.03, seed 1; compressed with chunking and CSR"),
+    "rmat22": dict(gen="rmat", scale=22, ef=16, k=256, seed=1,
+                   desc="R-MAT scale 22 (profiling case of the skewed tiers), edge factor 16 "
+                        "(0.57,0.19,0.19,0.05), symmetrised, deduplicated, k=256, eps=0.03, "
+                        "seed 1; compressed with chunking"),
     "serve": dict(gen="serve", count=128, seed=1, log2_lo=10.0, log2_hi=22.0, resident_log2=23,
                   resident_deg=32.0, budget=150e9, workers=16, load=0.7,
                   desc="serving: 128 requests, n log-uniform in [2^10, 2^22], G(n,m) deg 8 / "
@@ -387,6 +391,31 @@ def run_batch(args, w):
         "sum_cut": sum(st["cut"] for _, st in out),
     }
     print(json.dumps(line), flush=True)
+
+
+def run_batch_once(args, w):
+    """One warm-up and one timed batched partition with default knobs (for
+    profiler captures)."""
+    import torch
+
+    import paper_2410_19119_gb300 as tp
+    import synth
+
+    recipe = synth.batch_recipe(w["count"], seed=w["seed"])
+    graphs = [tp.graph_from_csr(*synth.batch_graph(s)) for s in recipe]
+    ks = [s["k"] for s in recipe]
+    p = tp.default_params(seed=w["seed"])
+    tp.partition_batch(graphs, ks, EPS, p)
+    torch.cuda.synchronize()
+    l0 = tp.launch_count()
+    t0 = time.perf_counter()
+    out = tp.partition_batch(graphs, ks, EPS, p)
+    torch.cuda.synchronize()
+    st = out[0][1]
+    print(json.dumps({"batch_once": w["desc"], "ms": (time.perf_counter() - t0) * 1e3,
+                      "launches": tp.launch_count() - l0, "ms_coarsen": st["ms_coarsen"],
+                      "ms_initial": st["ms_initial"], "ms_uncoarsen": st["ms_uncoarsen"],
+                      "peak_bytes": st["peak_bytes"]}), flush=True)
 
 
 def serve_recipe(w):
@@ -806,6 +835,8 @@ def main():
     elif w["gen"] == "batch":
         if args.impl == "reference":
             run_batch_reference(args, w)
+        elif args.partition_only:
+            run_batch_once(args, w)
         else:
             run_batch(args, w)
     elif args.lp_only:
