@@ -318,19 +318,31 @@ typedef struct {
   double queued_ms;        /* submit -> start */
   double run_ms;           /* start -> done */
   double total_ms;         /* submit -> done (the request's latency) */
-  int64_t footprint_bytes; /* budget the request held (tp_footprint_bytes) */
+  int64_t footprint_bytes; /* budget the request held (tp_footprint_bytes, or the
+                              whole budget when it ran again alone) */
   int64_t peak_bytes;      /* device memory it actually held at its peak */
+  int32_t retries;         /* 1 if it outgrew its footprint and ran again alone */
 } tp_request_info;
 
-/* Upper bound on the device memory one request holds: the partitioner's
- * working set (and, with upload != 0, the uploaded CSR and, with compress,
- * the compressed copy) for a graph of n vertices, m2 adjacency entries and
- * k blocks. Returns -1 for invalid sizes. */
+/* Device memory one request may hold: the partitioner's working set (and,
+ * with upload != 0, the uploaded CSR and, with compress, the compressed
+ * copy) for a graph of n vertices, m2 adjacency entries and k blocks, summed
+ * phase by phase from the library's allocations with the default params.
+ * It bounds every graph whose coarse levels together hold at most n
+ * vertices and 2 m2 entries and whose coarsest graph has at most
+ * min(n, 4 c_lim k) vertices (any level may consist of hubs entirely); the
+ * server enforces it per request (see tp_server_create). Returns -1 for
+ * invalid sizes. */
 int64_t tp_footprint_bytes(int64_t n, int64_t m2, int32_t k, int32_t upload, int32_t compress);
 
 /* Starts a server with budget_bytes of device memory for requests and
  * `workers` worker threads (1..256) on the calling thread's device. p may be
- * NULL (defaults); it applies to every request. */
+ * NULL (defaults); it applies to every request. A request is admitted by its
+ * footprint and its thread may allocate at most that much: one that would
+ * need more fails before allocating and runs again alone, holding the whole
+ * budget, so requests never hold more than budget_bytes of device memory in
+ * total. (Diagnostics: the environment variable TP_FOOTPRINT_SCALE, read
+ * here, scales every footprint, which lets a test provoke such reruns.) */
 tp_status tp_server_create(int64_t budget_bytes, int32_t workers, const tp_params *p,
                            tp_server **out);
 

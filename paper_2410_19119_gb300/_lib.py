@@ -46,7 +46,8 @@ class Request(ctypes.Structure):
 
 class RequestInfo(ctypes.Structure):
     _fields_ = [("queued_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
-                ("total_ms", ctypes.c_double), ("footprint_bytes", i64), ("peak_bytes", i64)]
+                ("total_ms", ctypes.c_double), ("footprint_bytes", i64), ("peak_bytes", i64),
+                ("retries", i32)]
 
 
 class ProfileEntry(ctypes.Structure):

@@ -22,8 +22,14 @@ std::atomic<int> g_sms{0};
 }  // namespace
 
 // Device bytes this host thread holds and its high-water mark (a call runs
-// on one thread, so the peak of its working set is the mark's rise).
-thread_local int64_t t_live = 0, t_peak = 0;
+// on one thread, so the peak of its working set is the mark's rise), and the
+// most it may hold (mem_cap; an allocation beyond it fails with TP_ERR_BUDGET
+// before anything is allocated).
+thread_local int64_t t_live = 0, t_peak = 0, t_cap = INT64_MAX;
+
+void mem_cap(int64_t bytes_above_now) {
+  t_cap = bytes_above_now < 0 ? INT64_MAX : t_live + bytes_above_now;
+}
 
 int64_t mem_mark() {
   t_peak = t_live;
@@ -72,6 +78,7 @@ void mem_trace_dump(const char *what) {
 
 void *dev_alloc(size_t bytes, cudaStream_t s, const AllocHook **from) {
   if (bytes == 0) return nullptr;
+  if (t_live + (int64_t)bytes > t_cap) throw Error{TP_ERR_BUDGET};
   void *p = nullptr;
   const AllocHook *h = g_hook.load();
   if (h->alloc) {

@@ -7,10 +7,17 @@
 // the budget, and, for a request on a resident graph, no other request is
 // using that graph (a graph caches per-level state while it is partitioned).
 // Admitted requests run concurrently on the device; each one's memory is
-// returned to the budget when it finishes, which admits the next. Every
+// returned to the budget when it finishes, which admits the next. A
+// request's thread may allocate at most its footprint: one that would need
+// more fails before allocating and goes back to the head of the queue with
+// the whole budget as its footprint, so it runs again alone. The device
+// therefore never holds more than the budget for requests. Every
 // request runs the unchanged single-graph path (upload, optional
 // compression, tp_partition, copy back), so its result does not depend on
 // what else is in flight.
+#include <stdlib.h>
+
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -40,6 +47,8 @@ namespace {
 
 struct Request {
   tp_request r;
+  uint64_t ticket = 0;
+  int32_t retries = 0;
   int64_t need = 0;  // admitted footprint (bytes)
   int state = 0;     // 0 queued, 1 running, 2 done
   bool waited = false;  // a waiter holds this request (a ticket is waited once)
@@ -57,6 +66,7 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 
 struct tp_server {
   int64_t budget = 0, in_use = 0, peak_in_use = 0;
+  double footprint_scale = 1.0;  // diagnostics: TP_FOOTPRINT_SCALE scales every footprint
   int32_t max_running = 0, running = 0;
   tp_params params{};
   int device = 0;
@@ -81,6 +91,7 @@ struct tp_server {
   void run(Request *q, cudaStream_t s) {
     const tp_request &r = q->r;
     const int64_t mark = mem_mark();
+    mem_cap(q->need);  // the admitted footprint, enforced
     q->status = guard([&] {
       std::unique_ptr<tp_graph> up, zp;
       const tp_graph *g = r.graph;
@@ -101,6 +112,8 @@ struct tp_server {
                                 cudaMemcpyDeviceToHost, s));
       TP_CUDA(cudaStreamSynchronize(s));
     });
+    if (q->status != TP_OK) cudaStreamSynchronize(s);  // its buffers were freed on s
+    mem_cap(-1);
     q->peak = mem_peak_since(mark);
   }
 
@@ -125,10 +138,19 @@ struct tp_server {
       if (ok) run(q, s);
       else q->status = TP_ERR_CUDA;
       lk.lock();
-      q->t_done = Clock::now();
       in_use -= q->need;
       --running;
       if (q->r.graph) busy.erase(q->r.graph);
+      if (q->status == TP_ERR_BUDGET && q->need < budget && q->retries == 0) {
+        // outgrew its footprint: again, alone, with the whole budget
+        q->need = budget;
+        q->retries = 1;
+        q->state = 0;
+        queue.push_front(q->ticket);
+        cv_work.notify_all();
+        continue;
+      }
+      q->t_done = Clock::now();
       q->state = 2;
       cv_done.notify_all();
       cv_work.notify_all();
@@ -140,12 +162,51 @@ struct tp_server {
 
 extern "C" {
 
+// Device bytes of one request, phase by phase from the library's
+// allocations (bytes per vertex n / adjacency entry m / block k), for any graph whose hierarchy stays inside this
+// envelope: the coarse levels together hold at most n vertices and 2 m
+// adjacency entries (each level has fewer entries than the one below; R-MAT
+// scale 26 coarse levels hold 0.05 n and 1.5 m, random geometric graphs
+// about 0.1 n and 0.3 m), any level may be made of hubs entirely, and the
+// coarsest graph has at most min(n, 4 c_lim k) vertices.
+//   upload   CSR 8n + 4m; with compression the stream (<= 10n + 5m + the
+//            chunk tables), its offsets and the encoder's scratch 16n
+//   part     4n (the request's result)
+//   levels   coarse CSR 16n + 12m per level; per level a map 4n and a tier
+//            cache 5n + 0.05m  -> within the envelope 30n + 24m
+//   cluster  C, map, cluster weights 16n; LP workspace 62n, 8n more for the
+//            records of a compressed level; two-hop packing 88n; hub rating
+//            tables 14 bytes per slot, fewer than 4 slots per hub neighbour: 56m
+//   contract flags, ranks, offsets 24n + coarse weights 8n; keys and their
+//            radix buffer 16m (weights unpackable into keys: 32m); coarse
+//            CSR 12m while the keys live
+//   initial  T attempts x 53 bytes per coarsest vertex + 40 + its CSR 12m
+//   refine   two partition arrays 8n, LP workspace 50n, hub tables 56m;
+//            block weights and per-block approval state 36k (counted apart)
+// The server admits a request by this figure and caps what its thread may
+// allocate at it; a request that would exceed it fails before allocating
+// and runs again alone with the whole budget.
+static int64_t footprint_model(int64_t n, int64_t m, int32_t k, bool upload, bool compress,
+                               int32_t c_lim, int32_t T) {
+  const double N = (double)n, M = (double)m, K = (double)k;
+  double in = 0;
+  if (upload) in = 8 * (N + 1) + 4 * (M + 4) + 64 + (compress ? (10 * N + 5.004 * M) + 16 * N : 0);
+  const double levels = 30 * N + 24 * M;
+  const double cluster = 174 * N + 56 * M;
+  const double contract = 32 * N + std::max(32 * M, 16 * M + 12 * M + 8 * N);
+  const double nc = std::min(N, 4.0 * c_lim * K);
+  const double initial = (53.0 * T + 40) * nc + 12 * std::min(M, nc * nc) + 12 * nc;
+  const double refine = 58 * N + 56 * M;
+  const double work = std::max(std::max(cluster, contract), std::max(initial, refine));
+  const double total = in + 4 * N + levels + work + 36 * K + (double)((int64_t)64 << 20);
+  return total >= 9.0e18 ? INT64_MAX : (int64_t)total;
+}
+
 int64_t tp_footprint_bytes(int64_t n, int64_t m2, int32_t k, int32_t upload, int32_t compress) {
   if (n < 0 || m2 < 0 || k < 1) return -1;
-  const int64_t csr = 8 * (n + 1) + 4 * m2 + 64;
-  int64_t b = 16 * csr + 256 * (int64_t)k + ((int64_t)8 << 20);
-  if (upload) b += csr + (compress ? 2 * csr : 0);
-  return b;
+  tp_params d;
+  tp_params_default(&d);
+  return footprint_model(n, m2, k, upload != 0, compress != 0, d.c_lim, d.ip_attempts);
 }
 
 tp_status tp_server_create(int64_t budget_bytes, int32_t workers, const tp_params *p,
@@ -161,6 +222,10 @@ tp_status tp_server_create(int64_t budget_bytes, int32_t workers, const tp_param
   auto *sv = new tp_server();
   sv->budget = budget_bytes;
   sv->max_running = workers;
+  if (const char *f = getenv("TP_FOOTPRINT_SCALE")) {
+    const double v = atof(f);
+    if (v > 0) sv->footprint_scale = v;
+  }
   sv->params = q;
   if (cudaGetDevice(&sv->device) != cudaSuccess) {
     delete sv;
@@ -191,12 +256,15 @@ tp_status tp_server_submit(tp_server *sv, const tp_request *req, uint64_t *ticke
     return TP_ERR_OOM;
   }
   q->r = r;
-  q->need = tp_footprint_bytes(n, m2, r.k, r.graph ? 0 : 1, r.graph ? 0 : r.compress);
+  q->need = (int64_t)(sv->footprint_scale *
+                      (double)footprint_model(n, m2, r.k, !r.graph, !r.graph && r.compress,
+                                              sv->params.c_lim, std::max(1, sv->params.ip_attempts)));
   if (q->need > sv->budget) return TP_ERR_BUDGET;
   q->t_submit = Clock::now();
   std::lock_guard<std::mutex> lk(sv->mu);
   if (sv->stopping) return TP_ERR_INVALID;
   const uint64_t t = sv->next_ticket;
+  q->ticket = t;
   try {
     sv->reqs.emplace(t, std::move(q));
     try {
@@ -230,6 +298,7 @@ tp_status tp_server_wait(tp_server *sv, uint64_t ticket, tp_stats *stats, tp_req
     info->total_ms = ms_between(q->t_submit, q->t_done);
     info->footprint_bytes = q->need;
     info->peak_bytes = q->peak;
+    info->retries = q->retries;
   }
   tp_status st = q->status;
   sv->reqs.erase(it);

@@ -63,6 +63,9 @@ void dev_free(void *p, size_t bytes, cudaStream_t s, const AllocHook *from);
 // returns the current holding; mem_peak_since(mark) is the rise since then.
 int64_t mem_mark();
 int64_t mem_peak_since(int64_t mark);
+// Caps what this thread may hold at its current holding plus bytes (< 0: no
+// cap); allocations beyond it throw TP_ERR_BUDGET.
+void mem_cap(int64_t bytes_above_now);
 // With TP_MEM_TRACE set: prints the buffers live at this thread's peak.
 void mem_trace_dump(const char *what);
 
