@@ -49,12 +49,17 @@ WORKLOADS = {
                    desc="R-MAT scale 22 (profiling case of the skewed tiers), edge factor 16 "
                         "(0.57,0.19,0.19,0.05), symmetrised, deduplicated, k=256, eps=0.03, "
                         "seed 1; compressed with chunking"),
-    "serve": dict(gen="serve", count=128, seed=1, log2_lo=10.0, log2_hi=22.0, resident_log2=23,
+    "serve": dict(gen="serve", count=64, seed=1, log2_lo=10.0, log2_hi=26.0, resident_log2=26,
                   resident_deg=32.0, budget=150e9, workers=16, load=0.7,
-                  desc="serving: 128 requests, n log-uniform in [2^10, 2^22], G(n,m) deg 8 / "
+                  desc="serving: 64 requests, n log-uniform in [2^10, 2^26], G(n,m) deg 8 / "
                        "RGG-2D deg 12 / RHG deg 16 gamma 2.8 in turn, k log-uniform in [2, 1024], "
-                       "every 8th request on a resident compressed RHG n=2^23 deg 32 gamma 2.8; "
+                       "every 8th request on a resident compressed RHG n=2^26 deg 32 gamma 2.8; "
                        "Poisson arrivals at 70% of the measured capacity; 150 GB budget; eps=0.03"),
+    "serve22": dict(gen="serve", count=128, seed=1, log2_lo=10.0, log2_hi=22.0, resident_log2=23,
+                    resident_deg=32.0, budget=150e9, workers=16, load=0.7,
+                    desc="serving (small): 128 requests, n log-uniform in [2^10, 2^22], the same "
+                         "generators and k, every 8th request on a resident compressed RHG n=2^23 "
+                         "deg 32 gamma 2.8; Poisson arrivals at 70% of capacity; 150 GB budget"),
     "batch4096": dict(gen="batch", count=4096, seed=1,
                       desc="batched: 4096 independent graphs, n log-uniform in [2^8, 2^16], "
                            "G(n,m) deg 8 / RGG-2D deg 12 / RHG deg 16 gamma 2.8 in turn, k in "
@@ -513,6 +518,9 @@ def run_serve(args, w):
         "capacity_rps": len(reqs) / cap_s, "plain_single_graph_rps": len(reqs) / plain_s,
         "speedup_vs_plain": plain_s / cap_s, "identical_to_plain": same,
         "edges_per_s_capacity": edges / cap_s, "peak_budget_in_use_bytes": cap_peak,
+        "peak_request_bytes": max(r[2]["peak_bytes"] for r in cap_res),
+        "reruns_alone": sum(r[2]["retries"] for r in cap_res),
+        "largest_request_n": max(len(host[i][0]) - 1 for i in host),
         "poisson": {"rate_rps": rate, **best, "runs": len(runs)},
         "generate_s": gen_s,
     }
@@ -828,7 +836,7 @@ def main():
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable":
                               "the serving workload's reference arm would be the oracle on "
-                              "requests of up to 2^22 vertices and a 2^23-vertex resident graph; "
+                              "requests of up to 2^26 vertices and a 2^26-vertex resident graph; "
                               "it is timed on the batch and single-graph workloads instead"}))
         else:
             run_serve(args, w)

@@ -346,9 +346,10 @@ int64_t tp_footprint_bytes(int64_t n, int64_t m2, int32_t k, int32_t upload, int
 tp_status tp_server_create(int64_t budget_bytes, int32_t workers, const tp_params *p,
                            tp_server **out);
 
-/* Queues a request and returns its ticket. TP_ERR_BUDGET if its footprint
- * exceeds the whole budget; TP_ERR_INVALID for bad arguments. Never blocks
- * on the device. */
+/* Queues a request and returns its ticket; TP_ERR_INVALID for bad
+ * arguments. A request whose footprint exceeds the whole budget is queued to
+ * run alone with the budget as its cap (tp_server_wait then returns
+ * TP_ERR_BUDGET if it would really need more). Never blocks on the device. */
 tp_status tp_server_submit(tp_server *sv, const tp_request *req, uint64_t *ticket);
 
 /* Blocks until the request is done, fills stats and info (both nullable)

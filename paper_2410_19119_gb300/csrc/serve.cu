@@ -10,8 +10,10 @@
 // returned to the budget when it finishes, which admits the next. A
 // request's thread may allocate at most its footprint: one that would need
 // more fails before allocating and goes back to the head of the queue with
-// the whole budget as its footprint, so it runs again alone. The device
-// therefore never holds more than the budget for requests. Every
+// the whole budget as its footprint, so it runs again alone (a request whose
+// footprint exceeds the budget is admitted that way from the start; it fails
+// only if it would really need more than the budget). The device therefore
+// never holds more than the budget for requests. Every
 // request runs the unchanged single-graph path (upload, optional
 // compression, tp_partition, copy back), so its result does not depend on
 // what else is in flight.
@@ -259,7 +261,8 @@ tp_status tp_server_submit(tp_server *sv, const tp_request *req, uint64_t *ticke
   q->need = (int64_t)(sv->footprint_scale *
                       (double)footprint_model(n, m2, r.k, !r.graph, !r.graph && r.compress,
                                               sv->params.c_lim, std::max(1, sv->params.ip_attempts)));
-  if (q->need > sv->budget) return TP_ERR_BUDGET;
+  // a footprint beyond the budget: the request runs alone, capped at the budget
+  if (q->need > sv->budget) q->need = sv->budget;
   q->t_submit = Clock::now();
   std::lock_guard<std::mutex> lk(sv->mu);
   if (sv->stopping) return TP_ERR_INVALID;

@@ -63,9 +63,14 @@ def test_budget_admission(mix):
         ts = [sv.submit(k, 0.03, xadj=x, adj=a) for (x, a), k in zip(host, ks)]
         infos = [sv.wait(t)[2] for t in ts]
         assert sv.peak_in_use() <= budget
-        with pytest.raises(tp.TpError):  # larger than the whole budget
-            x, a = host[int(np.argmax(fps))]
-            sv.submit(ks[int(np.argmax(fps))], 0.03, xadj=x, adj=a, compress=True)
+        # a footprint beyond the whole budget: admitted alone, capped at the budget
+        big = int(np.argmax(fps))
+        x, a = host[big]
+        part, _, info = sv.wait(sv.submit(ks[big], 0.03, xadj=x, adj=a, compress=True))
+        assert info["footprint_bytes"] == budget and info["peak_bytes"] <= budget
+        alone, _ = tp.partition(tp.graph_from_csr(x, a), ks[big], 0.03, tp.default_params())
+        assert np.array_equal(part, alone.cpu().numpy())
+        assert sv.peak_in_use() <= budget
     assert all(i["peak_bytes"] <= i["footprint_bytes"] for i in infos)
 
 
