@@ -40,6 +40,7 @@ namespace {
 enum Mode { M_LP = 0, M_FAV = 1, M_REBAL = 2 };
 
 constexpr int kSmallLog = 7;   // 128 slots
+constexpr int kMidSmallLog = 9;  // 512 slots: mid tier, degree <= kMidSplit = 256
 constexpr int kMidLog = 10;    // 1024 slots: mid tier, degree <= 512
 constexpr int kHugeLog = 11;   // 2048 slots: one 1000-neighbour chunk of a hub
 constexpr int kMidWarps = 4;
@@ -181,9 +182,11 @@ __device__ __forceinline__ uint32_t slot_of(int32_t x, int logcap) {
   return ((uint32_t)x * 0x9E3779B1u) >> (32 - logcap);
 }
 
-// Adds w to the rating of label x (open addressing, linear probing).
-__device__ __forceinline__ void tbl_add(int32_t *keys, int64_t *vals, int logcap, int32_t x,
-                                        int64_t w, int32_t *err) {
+// Adds w to the rating of label x (open addressing, linear probing); V is
+// int64_t, or uint32_t where ratings are counts (unit weights).
+template <class V>
+__device__ __forceinline__ void tbl_add(int32_t *keys, V *vals, int logcap, int32_t x, int64_t w,
+                                        int32_t *err) {
   uint32_t mask = (1u << logcap) - 1u, h = slot_of(x, logcap);
   for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
     int32_t k = *(volatile int32_t *)&keys[h];
@@ -192,7 +195,8 @@ __device__ __forceinline__ void tbl_add(int32_t *keys, int64_t *vals, int logcap
       k = prev == -1 ? x : prev;
     }
     if (k == x) {
-      atomicAdd((unsigned long long *)&vals[h], (unsigned long long)w);
+      if constexpr (sizeof(V) == 8) atomicAdd((unsigned long long *)&vals[h], (unsigned long long)w);
+      else atomicAdd((unsigned int *)&vals[h], (unsigned int)w);
       return;
     }
   }
@@ -306,52 +310,64 @@ __device__ __forceinline__ void finalize_warp(const RateCtx &c, const Best &b, i
   }
 }
 
-// Rates vertex u with one warp; the table (shared or global) must be empty
-// on entry and is empty again on exit.
-template <bool COMP, int MODE>
-__device__ void rate_vertex_warp(const RateCtx &c, int64_t u, int32_t *keys, int64_t *vals,
-                                 int logcap, bool allow_fast, MoverBuf *mb) {
+// Rates vertex u with one warp; the table must be empty on entry and is
+// empty again on exit. The scan takes two passes: the top rating among the
+// other labels (and the own rating), then the tie order among the labels at
+// that rating only, so tie hashes are formed for tied candidates alone; in
+// LP mode a vertex whose top rating does not beat its own cannot move and
+// skips the second pass.
+template <bool COMP, int MODE, class V>
+__device__ void rate_vertex_warp(const RateCtx &c, int64_t u, int32_t *keys, V *vals, int logcap,
+                                 MoverBuf *mb) {
   const int lane = lane_id();
   const int32_t own = c.label[u];
   const int64_t cu = node_w(c.g, u), capu = cap_of(c, u);
-  const TieKey hv = tie_key<MODE>(c, u);
-  Best b;
-  b.init();
   // every lane adds its neighbour's label to the table (shared-memory
   // atomics are far cheaper than grouping equal labels across lanes first)
   warp_neighbours<COMP>(c.g, u, -1, [&](bool has, int32_t v, int64_t w, int64_t) {
-    if (has) tbl_add(keys, vals, logcap, c.label[v], w, c.g.err);
+    if (has) tbl_add<V>(keys, vals, logcap, c.label[v], w, c.g.err);
   });
   __syncwarp();
   __threadfence_block();
   const int cap = 1 << logcap;
-  // the best label ignoring the cap, and the own rating
+  int64_t rmax = -1, rown = 0;
   for (int i = lane; i < cap; i += 32) {
     const int32_t x = keys[i];
     if (x < 0) continue;
-    if (x == own) {
-      b.rown = vals[i];
-      continue;
-    }
-    const uint32_t t = MODE == M_REBAL ? 0u : tie_of(hv, x);
-    if (better(vals[i], t, x, b.r, b.t, b.x)) b.r = vals[i], b.t = t, b.x = x;
+    const int64_t R = (int64_t)vals[i];
+    if (x == own) rown = R;
+    else rmax = R > rmax ? R : rmax;
   }
-  warp_reduce_best(b);
-  // the winner is full: the best admissible label instead (for a move it
-  // must also improve on the own rating)
-  if (MODE != M_FAV && b.x != INT32_MAX && c.lw[b.x] + cu > capu) {
-    const int64_t rown = b.rown;
-    b.init();
+  rmax = warp_max(rmax);
+  rown = warp_max(rown);
+  Best b;
+  b.init();
+  b.rown = rown;
+  if (rmax >= 0 && (MODE != M_LP || rmax > rown)) {
+    const TieKey hv = tie_key<MODE>(c, u);
+    // the best label ignoring the cap: the top-rated one first in tie order
     for (int i = lane; i < cap; i += 32) {
       const int32_t x = keys[i];
-      if (x < 0 || x == own) continue;
-      const int64_t R = vals[i];
-      if (MODE == M_LP && R <= rown) continue;
+      if (x < 0 || x == own || (int64_t)vals[i] != rmax) continue;
       const uint32_t t = MODE == M_REBAL ? 0u : tie_of(hv, x);
-      if (better(R, t, x, b.r, b.t, b.x) && c.lw[x] + cu <= capu) b.r = R, b.t = t, b.x = x;
+      if (better(rmax, t, x, b.r, b.t, b.x)) b.r = rmax, b.t = t, b.x = x;
     }
-    warp_reduce_best(b);
-    b.rown = rown;
+    warp_best(b.r, b.t, b.x);
+    // the winner is full: the best admissible label instead (for a move it
+    // must also improve on the own rating)
+    if (MODE != M_FAV && b.x != INT32_MAX && c.lw[b.x] + cu > capu) {
+      b.init();
+      for (int i = lane; i < cap; i += 32) {
+        const int32_t x = keys[i];
+        if (x < 0 || x == own) continue;
+        const int64_t R = (int64_t)vals[i];
+        if (MODE == M_LP && R <= rown) continue;
+        const uint32_t t = MODE == M_REBAL ? 0u : tie_of(hv, x);
+        if (better(R, t, x, b.r, b.t, b.x) && c.lw[x] + cu <= capu) b.r = R, b.t = t, b.x = x;
+      }
+      warp_best(b.r, b.t, b.x);
+      b.rown = rown;
+    }
   }
   for (int i = lane; i < cap; i += 32) keys[i] = -1, vals[i] = 0;
   __syncwarp();
@@ -368,16 +384,16 @@ __device__ __forceinline__ int table_log(const RateCtx &c, int64_t d, int maxlog
 }
 
 // Shared memory per warp: table keys + values, then the mover buffer.
-template <int LOG>
+template <int LOG, class V = int64_t>
 struct WarpSmem {
   int32_t keys[1 << LOG];
-  int64_t vals[1 << LOG];
+  V vals[1 << LOG];
   int32_t mu[32], mt[32], mo[32];
   int64_t mg[32];
 };
 
-template <int LOG>
-__device__ __forceinline__ void init_table(WarpSmem<LOG> &w) {
+template <int LOG, class V>
+__device__ __forceinline__ void init_table(WarpSmem<LOG, V> &w) {
   for (int i = lane_id(); i < (1 << LOG); i += 32) w.keys[i] = -1, w.vals[i] = 0;
   __syncwarp();
 }
@@ -400,7 +416,7 @@ __global__ void k_rate_small(RateCtx c) {
       int64_t i, u;
       if (tier_entry<MODE>(c, k, i, u)) {
         const int64_t d = COMP ? zip_nbr(c.g, u).deg : c.g.xadj[u + 1] - c.g.xadj[u];
-        rate_vertex_warp<COMP, MODE>(c, u, ws.keys, ws.vals, table_log(c, d, kSmallLog), true, &mb);
+        rate_vertex_warp<COMP, MODE>(c, u, ws.keys, ws.vals, table_log(c, d, kSmallLog), &mb);
       }
     }
   } else {
@@ -414,7 +430,7 @@ __global__ void k_rate_small(RateCtx c) {
         am &= am - 1;
         const int64_t v = base + j;
         const int64_t d = COMP ? zip_nbr(c.g, v).deg : c.g.xadj[v + 1] - c.g.xadj[v];
-        rate_vertex_warp<COMP, MODE>(c, v, ws.keys, ws.vals, table_log(c, d, kSmallLog), true, &mb);
+        rate_vertex_warp<COMP, MODE>(c, v, ws.keys, ws.vals, table_log(c, d, kSmallLog), &mb);
       }
     }
   }
@@ -967,18 +983,17 @@ __global__ void __launch_bounds__(lane_warps<W>() * 32, W ? 1 : kLaneBlocksPerSM
   }
 }
 
-// Mid tier (shared table) and big tier (global table): one warp per listed vertex.
-template <bool COMP, int MODE, bool GLOBAL>
+// Mid tier: one warp per listed vertex, its table of up to 2^LOG slots in
+// shared memory (V: uint32_t counts at unit weights, int64_t sums otherwise;
+// the smaller tables leave room for more warps per SM).
+template <bool COMP, int MODE, int LOG, class V>
 __global__ void k_rate_list(RateCtx c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  WarpSmem<kMidLog> *wsp = nullptr;
   __shared__ int32_t mu[kMidWarps][32], mt[kMidWarps][32], mo[kMidWarps][32];
   __shared__ int64_t mg[kMidWarps][32];
-  int w = threadIdx.x >> 5;
-  if (!GLOBAL) {
-    wsp = &reinterpret_cast<WarpSmem<kMidLog> *>(smem_raw)[w];
-    init_table(*wsp);
-  }
+  const int w = threadIdx.x >> 5;
+  WarpSmem<LOG, V> &ws = reinterpret_cast<WarpSmem<LOG, V> *>(smem_raw)[w];
+  init_table(ws);
   MoverBuf mb{mu[w], mt[w], mo[w], mg[w], 0};
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -987,13 +1002,8 @@ __global__ void k_rate_list(RateCtx c) {
   for (int64_t k = kb + gw; k < ke; k += nw) {
     int64_t i, u;
     if (!tier_entry<MODE>(c, k, i, u)) continue;
-    if (GLOBAL) {
-      int64_t off = c.tbase + c.toff[i];
-      rate_vertex_warp<COMP, MODE>(c, u, c.tkeys + off, c.tvals + off, c.tcap[i], false, &mb);
-    } else {
-      const int64_t d = COMP ? zip_nbr(c.g, u).deg : c.g.xadj[u + 1] - c.g.xadj[u];
-      rate_vertex_warp<COMP, MODE>(c, u, wsp->keys, wsp->vals, table_log(c, d, kMidLog), false, &mb);
-    }
+    const int64_t d = COMP ? zip_nbr(c.g, u).deg : c.g.xadj[u + 1] - c.g.xadj[u];
+    rate_vertex_warp<COMP, MODE, V>(c, u, ws.keys, ws.vals, table_log(c, d, LOG), &mb);
   }
   if (MODE == M_LP) flush_movers(c, mb);
 }
@@ -1149,6 +1159,21 @@ __device__ __forceinline__ void blk_add(int32_t *keys, V *vals, int logc, int32_
   latch_error(err, TP_ERR_CORRUPT);
 }
 
+// Block-wide maxima of two values; the results are in every thread.
+__device__ __forceinline__ void block_max2(int64_t &a, int64_t &b, int64_t *red) {
+  a = warp_max(a);
+  b = warp_max(b);
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  __shared__ int64_t rb[kBlockThreads / 32];
+  if (lane == 0) red[w] = a, rb[w] = b;
+  __syncthreads();
+  int64_t x = lane < kBlockThreads / 32 ? red[lane] : INT64_MIN;
+  int64_t y = lane < kBlockThreads / 32 ? rb[lane] : INT64_MIN;
+  a = warp_max(x);
+  b = warp_max(y);
+  __syncthreads();
+}
+
 // Block-wide best (rating order) and own rating; the result is in every thread.
 __device__ __forceinline__ void block_reduce_best(Best &b, Best *wb) {
   warp_reduce_best(b);
@@ -1200,27 +1225,36 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_block(RateCtx c, int max
       }
     }
     __syncthreads();
-    // best label ignoring the cap, and the own rating
+    // the top rating among the other labels and the own rating, then the tie
+    // order among the top-rated labels only (as in the warp tiers)
     const int32_t own = c.label[u];
     const int64_t cu = node_w(c.g, u), capu = cap_of(c, u);
-    const TieKey hv = tie_key<MODE>(c, u);
-    Best b;
-    b.init();
+    int64_t rmax = -1, rown = 0;
     for (int k = tid; k < cap; k += kBlockThreads) {
       const int32_t x = keys[k];
       if (x < 0) continue;
       const int64_t R = (int64_t)vals[k];
-      if (x == own) {
-        b.rown = R;
-        continue;
-      }
-      const uint32_t t = MODE == M_REBAL ? 0u : tie_of(hv, x);
-      if (better(R, t, x, b.r, b.t, b.x)) b.r = R, b.t = t, b.x = x;
+      if (x == own) rown = R;
+      else rmax = R > rmax ? R : rmax;
     }
-    block_reduce_best(b, wb);
+    block_max2(rmax, rown, red);
+    Best b;
+    b.init();
+    b.rown = rown;
+    const bool rate = rmax >= 0 && (MODE != M_LP || rmax > rown);  // uniform over the block
+    const TieKey hv = rate ? tie_key<MODE>(c, u) : TieKey{0, 0};
+    if (rate) {
+      for (int k = tid; k < cap; k += kBlockThreads) {
+        const int32_t x = keys[k];
+        if (x < 0 || x == own || (int64_t)vals[k] != rmax) continue;
+        const uint32_t t = MODE == M_REBAL ? 0u : tie_of(hv, x);
+        if (better(rmax, t, x, b.r, b.t, b.x)) b.r = rmax, b.t = t, b.x = x;
+      }
+      block_reduce_best(b, wb);
+    }
     // the winner is full: the best admissible label instead (it must improve
     // on the own rating to matter)
-    if (MODE != M_FAV && b.x != INT32_MAX && c.lw[b.x] + cu > capu) {
+    if (rate && MODE != M_FAV && b.x != INT32_MAX && c.lw[b.x] + cu > capu) {
       const int64_t rown = b.rown;
       b.init();
       for (int k = tid; k < cap; k += kBlockThreads) {
@@ -1736,18 +1770,37 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
     TP_LAUNCH_CHECK();
     if (prof) prof_end(PF_RATE_SMALL, s, per_launch * tier_round_bytes(g, T.count[TIER_SMALL], T.edges[TIER_SMALL]));
   }
-  if (T.n_mid > 0) {
+  if (T.n_mid + T.n_mid2 > 0) {
     if (prof) prof_begin(PF_RATE_MID, s);
-    RateCtx m = c;
-    m.list = T.mid.get();
-    m.list_n = T.n_mid;
-    bucketed(m, 1);
-    size_t sm = sizeof(WarpSmem<kMidLog>) * kMidWarps;
-    unsigned blocks = (unsigned)std::min<int64_t>((T.n_mid + kMidWarps - 1) / kMidWarps, (int64_t)sms * 8);
-    if (comp) launch(k_rate_list<true, MODE, false>, blocks, 32 * kMidWarps, sm, s, m);
-    else launch(k_rate_list<false, MODE, false>, blocks, 32 * kMidWarps, sm, s, m);
-    TP_LAUNCH_CHECK();
-    if (prof) prof_end(PF_RATE_MID, s, per_launch * tier_round_bytes(g, T.n_mid, T.edges[TIER_MID]));
+    // counts in 32 bits at unit weights (compressed levels have unit weights)
+    const bool unit = g->unit_ew != 0;
+    auto run = [&](const int32_t *list, int64_t cnt, int t, bool big_tables) {
+      if (!cnt) return;
+      RateCtx m = c;
+      m.list = list;
+      m.list_n = cnt;
+      bucketed(m, t);
+      const unsigned blocks =
+          (unsigned)std::min<int64_t>((cnt + kMidWarps - 1) / kMidWarps, (int64_t)sms * 16);
+#define TP_MID(LG, V)                                                                         \
+  do {                                                                                        \
+    const size_t sm = sizeof(WarpSmem<LG, V>) * kMidWarps;                                    \
+    if (comp) launch(k_rate_list<true, MODE, LG, V>, blocks, 32 * kMidWarps, sm, s, m);      \
+    else launch(k_rate_list<false, MODE, LG, V>, blocks, 32 * kMidWarps, sm, s, m);          \
+  } while (0)
+      if (big_tables) {
+        if (unit) TP_MID(kMidLog, uint32_t);
+        else TP_MID(kMidLog, int64_t);
+      } else {
+        if (unit) TP_MID(kMidSmallLog, uint32_t);
+        else TP_MID(kMidSmallLog, int64_t);
+      }
+#undef TP_MID
+      TP_LAUNCH_CHECK();
+    };
+    run(T.mid.get(), T.n_mid, 1, false);
+    run(T.mid2.get(), T.n_mid2, 2, true);
+    if (prof) prof_end(PF_RATE_MID, s, per_launch * tier_round_bytes(g, T.n_mid + T.n_mid2, T.edges[TIER_MID]));
   }
   if (T.n_big0 + T.n_big + T.n_big2 > 0) {
     if (prof) prof_begin(PF_RATE_BIG, s);
@@ -1771,9 +1824,9 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
 #undef TP_BLK
       TP_LAUNCH_CHECK();
     };
-    run(T.big0.get(), T.n_big0, kBlockTinyLog, 2);
-    run(T.big.get(), T.n_big, kBlockSmallLog, 3);
-    run(T.big2.get(), T.n_big2, kBlockBigLog, 4);
+    run(T.big0.get(), T.n_big0, kBlockTinyLog, 3);
+    run(T.big.get(), T.n_big, kBlockSmallLog, 4);
+    run(T.big2.get(), T.n_big2, kBlockBigLog, 5);
     if (prof) prof_end(PF_RATE_BIG, s, per_launch * tier_round_bytes(g, T.n_big0 + T.n_big + T.n_big2, T.edges[TIER_BIG]));
   }
   if (T.n_huge > 0) {
@@ -1781,7 +1834,7 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
     RateCtx m = c;
     m.list = T.huge.get();
     m.list_n = T.n_huge;
-    bucketed(m, 5);
+    bucketed(m, 6);
     m.toff = T.huge_toff.get();
     m.tcap = T.huge_tcap.get();
     m.tbase = 0;
@@ -1811,17 +1864,22 @@ void set_smem_limits(K kernel, size_t bytes) {
 
 void configure_kernels_once() {
   size_t small16 = sizeof(WarpSmem<kSmallLog>) * 16;
-  size_t mid = sizeof(WarpSmem<kMidLog>) * kMidWarps;
+#define TP_CFG_MID(M, LG, V)                                                       \
+  set_smem_limits(k_rate_list<true, M, LG, V>, sizeof(WarpSmem<LG, V>) * kMidWarps); \
+  set_smem_limits(k_rate_list<false, M, LG, V>, sizeof(WarpSmem<LG, V>) * kMidWarps);
 #define TP_CFG_MODE(M)                                              \
   set_smem_limits(k_rate_small<true, M>, small16);                  \
   set_smem_limits(k_rate_small<false, M>, small16);                 \
-  set_smem_limits(k_rate_list<true, M, false>, mid);                \
-  set_smem_limits(k_rate_list<false, M, false>, mid);               \
+  TP_CFG_MID(M, kMidSmallLog, uint32_t)                             \
+  TP_CFG_MID(M, kMidSmallLog, int64_t)                              \
+  TP_CFG_MID(M, kMidLog, uint32_t)                                  \
+  TP_CFG_MID(M, kMidLog, int64_t)
 
   TP_CFG_MODE(M_LP)
   TP_CFG_MODE(M_FAV)
   TP_CFG_MODE(M_REBAL)
 #undef TP_CFG_MODE
+#undef TP_CFG_MID
   // the largest dynamic shared memory: weighted CSR with 16384 slots, or
   // compressed with 16384 slots and the record staging
   const size_t blk = std::max(((size_t)1 << kBlockBigLog) * (sizeof(int32_t) + 8),
@@ -2038,11 +2096,10 @@ __global__ void k_huge_items(const int32_t *bpos, int64_t nh, const int64_t *pre
 // Buckets the warp and block tiers' lists of this round by sub-round.
 static void tier_buckets(tp_graph *g, LpWork &w, int32_t S, cudaStream_t stream) {
   TierCache &T = g->tiers;
-  const int32_t *lists[LpWork::kTiers] = {T.small.get(), T.mid.get(), T.big0.get(), T.big.get(),
-                                          T.big2.get(),
-                                          T.huge.get()};
-  const int64_t lens[LpWork::kTiers] = {T.n_small, T.n_mid, T.n_big0, T.n_big, T.n_big2,
-                                        T.n_huge};
+  const int32_t *lists[LpWork::kTiers] = {T.small.get(), T.mid.get(),  T.mid2.get(), T.big0.get(),
+                                          T.big.get(),   T.big2.get(), T.huge.get()};
+  const int64_t lens[LpWork::kTiers] = {T.n_small, T.n_mid,  T.n_mid2, T.n_big0,
+                                        T.n_big,   T.n_big2, T.n_huge};
   int64_t total = 0;
   for (int t = 0; t < LpWork::kTiers; ++t) w.tb_base[t] = total, total += lens[t];
   w.tb_valid = false;
@@ -2076,7 +2133,7 @@ static void tier_buckets(tp_graph *g, LpWork &w, int32_t S, cudaStream_t stream)
       w.hc_item.alloc(std::max<int64_t>(T.n_huge_chunks, 1), stream);
     if ((int64_t)w.hs_item.n < std::max<int64_t>(T.n_huge_segs, 1))
       w.hs_item.alloc(std::max<int64_t>(T.n_huge_segs, 1), stream);
-    const int32_t *hp = w.tb_pos.get() + w.tb_base[5];
+    const int32_t *hp = w.tb_pos.get() + w.tb_base[6];
     launch(k_huge_counts, grid_for(nh, 256), 256, 0, stream, hp, nh, T.huge_chunk_start.get(),
            T.huge_seg_start.get(), w.hc_pre.get(), w.hs_pre.get());
     exclusive_scan_i64(w.hc_pre.get(), w.hc_pre.get(), nh, stream);
