@@ -203,27 +203,6 @@ __device__ __forceinline__ void tbl_add(int32_t *keys, V *vals, int logcap, int3
   latch_error(err, TP_ERR_CORRUPT);  // more distinct labels than the degree allows
 }
 
-// tbl_add that returns the slot it filled (-1 if x was there already).
-__device__ __forceinline__ int32_t tbl_add_claim(int32_t *keys, int64_t *vals, int logcap, int32_t x,
-                                                 int64_t w, int32_t *err) {
-  uint32_t mask = (1u << logcap) - 1u, h = slot_of(x, logcap);
-  for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
-    int32_t k = *(volatile int32_t *)&keys[h];
-    int32_t filled = -1;
-    if (k == -1) {
-      const int32_t prev = atomicCAS(&keys[h], -1, x);
-      if (prev == -1) filled = (int32_t)h;
-      k = prev == -1 ? x : prev;
-    }
-    if (k == x) {
-      atomicAdd((unsigned long long *)&vals[h], (unsigned long long)w);
-      return filled;
-    }
-  }
-  latch_error(err, TP_ERR_CORRUPT);
-  return -1;
-}
-
 struct Best {
   int64_t r;
   uint32_t t;
@@ -1070,7 +1049,7 @@ __device__ __forceinline__ uint32_t block_excl_sum32(uint32_t v, int64_t *red, u
 // ending in its slice to vbuf (count entries), each assembled without
 // branches from its last byte and up to four preceding continuation bytes,
 // (3) a block scan over the values turns them into neighbour ids, and (4)
-// f is called for every id.
+// f(count) is called by every thread once the ids are in vbuf.
 template <class F>
 __device__ __forceinline__ void block_decode_range(const GView &g, int64_t u, uint64_t cb,
                                                    uint64_t ce, int64_t count, uint8_t *stage,
@@ -1136,7 +1115,7 @@ __device__ __forceinline__ void block_decode_range(const GView &g, int64_t u, ui
     vbuf[i] = (uint32_t)min(max(id0 + (int64_t)run, (int64_t)0), nmax);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < cnt; i += kBlockThreads) f((int32_t)vbuf[i]);
+  f(cnt);  // the ids are in vbuf[0 .. cnt)
   __syncthreads();  // stage and vbuf are reused
 }
 
@@ -1213,8 +1192,9 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_block(RateCtx c, int max
     __syncthreads();
     if (COMP) {
       const ZipNbr z = zip_nbr(c.g, u);  // one chunk: the big tier is below the chunking threshold
-      block_decode_range(c.g, u, z.data, z.end, z.deg, stage, vbuf, red, [&](int32_t v) {
-        blk_add<V>(keys, vals, logc, c.label[v], (V)1, c.g.err);
+      block_decode_range(c.g, u, z.data, z.end, z.deg, stage, vbuf, red, [&](int cnt) {
+        for (int e = tid; e < cnt; e += kBlockThreads)
+          blk_add<V>(keys, vals, logc, c.label[vbuf[e]], (V)1, c.g.err);
       });
     } else {
       const int64_t b = c.g.xadj[u];
@@ -1327,8 +1307,9 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_huge_chunks(RateCtx c) {
       uint64_t cb, ce;
       int64_t cnt;
       zip_chunk(c.g, z, j, cb, ce, cnt);
-      block_decode_range(c.g, u, cb, ce, cnt, stage, vbuf, red, [&](int32_t v) {
-        blk_add<unsigned long long>(keys, vals, kHugeLog, c.label[v], 1ull, c.g.err);
+      block_decode_range(c.g, u, cb, ce, cnt, stage, vbuf, red, [&](int n) {
+        for (int e = tid; e < n; e += kBlockThreads)
+          blk_add<unsigned long long>(keys, vals, kHugeLog, c.label[vbuf[e]], 1ull, c.g.err);
       });
     } else {
       const int64_t b = c.g.xadj[u] + j * kChunkSize;
@@ -1346,13 +1327,54 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_huge_chunks(RateCtx c) {
     const int lc = c.tcap[i];
     if (tid == 0) s_nclaim = 0;
     __syncthreads();
-    for (int k = tid; k < (1 << kHugeLog); k += kBlockThreads) {
-      const int32_t x = keys[k];
-      if (x < 0) continue;
-      const int32_t h = tbl_add_claim(tk, tv, lc, x, (int64_t)vals[k], c.g.err);
-      if (h >= 0) claimed[atomicAdd(&s_nclaim, 1)] = h;
-      keys[k] = -1;
-      vals[k] = 0;
+    // every thread inserts its kFlush shared slots together: each probe
+    // step issues all pending key loads, then all claims (atomicCAS), so a
+    // thread waits for one round trip per step instead of one per label
+    constexpr int kFlush = (1 << kHugeLog) / kBlockThreads;
+    {
+      const uint32_t mask = (1u << lc) - 1u;
+      int32_t lab[kFlush];
+      int64_t w[kFlush];
+      uint32_t h[kFlush], probes[kFlush];
+      bool pend[kFlush];
+#pragma unroll
+      for (int q = 0; q < kFlush; ++q) {
+        const int k = tid + q * kBlockThreads;
+        lab[q] = keys[k];
+        w[q] = (int64_t)vals[k];
+        keys[k] = -1;
+        vals[k] = 0;
+        pend[q] = lab[q] >= 0;
+        h[q] = pend[q] ? slot_of(lab[q], lc) : 0;
+        probes[q] = 0;
+      }
+      for (;;) {
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < kFlush; ++q) any |= pend[q];
+        if (!any) break;
+        int32_t cur[kFlush], prev[kFlush];
+#pragma unroll
+        for (int q = 0; q < kFlush; ++q) cur[q] = pend[q] ? *(volatile int32_t *)&tk[h[q]] : 0;
+#pragma unroll
+        for (int q = 0; q < kFlush; ++q)
+          prev[q] = pend[q] && cur[q] == -1 ? atomicCAS(&tk[h[q]], -1, lab[q]) : 0;
+#pragma unroll
+        for (int q = 0; q < kFlush; ++q) {
+          if (!pend[q]) continue;
+          const int32_t kk = cur[q] == -1 ? (prev[q] == -1 ? lab[q] : prev[q]) : cur[q];
+          if (kk == lab[q]) {
+            atomicAdd((unsigned long long *)&tv[h[q]], (unsigned long long)w[q]);
+            if (cur[q] == -1 && prev[q] == -1) claimed[atomicAdd(&s_nclaim, 1)] = (int32_t)h[q];
+            pend[q] = false;
+          } else if (++probes[q] > mask) {
+            latch_error(c.g.err, TP_ERR_CORRUPT);  // more distinct labels than the table holds
+            pend[q] = false;
+          } else {
+            h[q] = (h[q] + 1) & mask;
+          }
+        }
+      }
     }
     __syncthreads();
     // the slots this chunk filled join the hub's list with one counter update
@@ -1417,21 +1439,39 @@ __global__ void __launch_bounds__(kBlockThreads) k_rate_huge_scan(RateCtx c, Bes
     Best b, a;
     b.init();
     a.init();
-    for (int64_t j = (dense ? 2 * s0 : s0) + threadIdx.x; j < s1; j += kBlockThreads) {
-      const int32_t sl = dense ? (int32_t)j : tl[j];
-      const int32_t x = tk[sl];
-      if (x < 0) continue;
-      const int64_t R = tv[sl];
-      tk[sl] = -1;
-      tv[sl] = 0;
-      if (x == own) {
-        b.rown = R;
-        continue;
+    // kScanBatch slots per thread and step, every load of a step issued
+    // before the first is used (list entries, then keys, then values), so a
+    // thread waits for one round trip per step instead of one per slot
+    constexpr int kScanBatch = 8;
+    for (int64_t j0 = (dense ? 2 * s0 : s0) + threadIdx.x; j0 < s1;
+         j0 += (int64_t)kBlockThreads * kScanBatch) {
+      int32_t sl[kScanBatch], xs[kScanBatch];
+      int64_t Rs[kScanBatch];
+#pragma unroll
+      for (int q = 0; q < kScanBatch; ++q) {
+        const int64_t j = j0 + (int64_t)q * kBlockThreads;
+        sl[q] = j < s1 ? (dense ? (int32_t)j : tl[j]) : -1;
       }
-      const uint32_t t = MODE == M_REBAL ? 0u : tie_of(hv, x);
-      if (better(R, t, x, b.r, b.t, b.x)) b.r = R, b.t = t, b.x = x;
-      if (MODE != M_FAV && better(R, t, x, a.r, a.t, a.x) && c.lw[x] + cu <= capu)
-        a.r = R, a.t = t, a.x = x;
+#pragma unroll
+      for (int q = 0; q < kScanBatch; ++q) xs[q] = sl[q] >= 0 ? tk[sl[q]] : -1;
+#pragma unroll
+      for (int q = 0; q < kScanBatch; ++q) Rs[q] = xs[q] >= 0 ? tv[sl[q]] : 0;
+#pragma unroll
+      for (int q = 0; q < kScanBatch; ++q) {
+        const int32_t x = xs[q];
+        if (x < 0) continue;
+        const int64_t R = Rs[q];
+        tk[sl[q]] = -1;
+        tv[sl[q]] = 0;
+        if (x == own) {
+          b.rown = R;
+          continue;
+        }
+        const uint32_t t = MODE == M_REBAL ? 0u : tie_of(hv, x);
+        if (better(R, t, x, b.r, b.t, b.x)) b.r = R, b.t = t, b.x = x;
+        if (MODE != M_FAV && better(R, t, x, a.r, a.t, a.x) && c.lw[x] + cu <= capu)
+          a.r = R, a.t = t, a.x = x;
+      }
     }
     block_reduce_best(b, wb);
     if (MODE != M_FAV) block_reduce_best(a, wb);
