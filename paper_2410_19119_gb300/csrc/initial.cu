@@ -27,7 +27,7 @@ namespace tp {
 namespace {
 
 // Threads per attempt: 1024 for large nodes or few attempts in flight,
-// 256 or 128 when many small nodes share the GPU (several CTAs per SM).
+// 512, 256 or 128 when many smaller nodes share the GPU (several CTAs per SM).
 constexpr int kIPThreads = 1024;
 
 struct IPCtx {
@@ -609,6 +609,7 @@ void initial_partition_roots(const tp_graph *g, const std::vector<IPRoot> &roots
     const bool many = ctas >= 4LL * num_sms();
     if (many && max_ns <= 512) launch(k_bisect<128>, (unsigned)ctas, 128, 0, s, c);
     else if (many && max_ns <= 4096) launch(k_bisect<256>, (unsigned)ctas, 256, 0, s, c);
+    else if (many && max_ns <= 16384) launch(k_bisect<512>, (unsigned)ctas, 512, 0, s, c);
     else launch(k_bisect<kIPThreads>, (unsigned)ctas, kIPThreads, 0, s, c);
     TP_LAUNCH_CHECK();
     launch(k_fill_i32, grid_for(n, 256), 256, 0, s, next_node.get(), n, -1);
