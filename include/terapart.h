@@ -146,6 +146,37 @@ tp_status tp_graph_from_compressed(int64_t n, uint64_t nbytes, const uint8_t *by
                                    const uint64_t *off, int host_ptrs, void *stream,
                                    tp_graph **out);
 
+/* The interval + edge-weight format (Section "Compression Scheme": runs of
+ * >= 3 consecutive neighbour ids stored as intervals, edge weights VarInt-
+ * coded and interleaved with the codes they belong to). Headers, chunking
+ * and the terminal header are those of tp_graph_compress. A chunk with
+ * intervals (intervals != 0) starts with VarInt(number of maximal runs of >= 3
+ * consecutive ids); each run, smallest first, is VarInt(start code: the
+ * first run 2|x-u| + [x<u], a later one x - previous end - 2), VarInt(length
+ * - 3) and, with weights, its members' weights; the remaining ids follow as
+ * in the plain format. With weights (weights != 0; a unit-weight graph writes
+ * ones) every id or gap code is followed by VarInt(2|w - w'| + [w < w']), w'
+ * the chunk's previous weight in storage order (0 first). Without either it
+ * is the plain stream of tp_graph_compress.
+ * tp_encode_ex encodes the CSR graph g: d_off (n + 1 u64, device, caller-
+ * owned) receives every vertex's byte offset (off[n]: the terminal header),
+ * *nbytes the stream's length, and, when d_bytes (device, at least *nbytes
+ * bytes) is not NULL, the stream itself. TP_ERR_INVALID for a compressed g.
+ * Synchronises. */
+tp_status tp_encode_ex(const tp_graph *g, int32_t intervals, int32_t weights, uint64_t *d_off,
+                       uint8_t *d_bytes, uint64_t *nbytes, void *stream);
+
+/* Decodes such a stream (device pointers, caller-owned) into a new CSR graph
+ * (with its edge weights when weighted != 0, unit weights otherwise). A
+ * malformed stream (bad header or chunk table, truncated VarInt, id out of
+ * range, unsorted ids, a residual inside a run, a weight below 1) gives
+ * TP_ERR_CORRUPT; a decoded graph that is not a valid symmetric graph gives
+ * TP_ERR_INVALID. The rating kernels read the plain format only, so such a
+ * graph is partitioned as CSR. Synchronises. */
+tp_status tp_graph_from_stream_ex(int64_t n, uint64_t nbytes, const uint8_t *d_bytes,
+                                  const uint64_t *d_off, int32_t intervals, int32_t weighted,
+                                  void *stream, tp_graph **out);
+
 /* Decodes a compressed graph back to CSR (round-trip check); corrupt streams
  * give TP_ERR_CORRUPT. Synchronises. */
 tp_status tp_graph_decompress(const tp_graph *g, void *stream, tp_graph **out_csr);

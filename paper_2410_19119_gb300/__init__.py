@@ -18,7 +18,8 @@ __all__ = ["Graph", "Params", "Stats", "TpError", "default_params", "graph_from_
            "graph_from_compressed", "partition", "lp_cluster", "lp_subround", "contract",
            "initial_partition", "lp_refine", "rebalance", "metrics", "launch_count",
            "profile_enable", "profile_read", "PROFILE_FAMILIES", "partition_batch", "Server",
-           "footprint_bytes", "use_torch_allocator", "use_default_allocator", "set_allocator"]
+           "footprint_bytes", "use_torch_allocator", "use_default_allocator", "set_allocator",
+           "graph_from_stream_ex"]
 
 PROFILE_FAMILIES = ("rate_small", "rate_mid", "rate_big", "rate_huge", "approve", "rate_lane")
 
@@ -165,6 +166,20 @@ class Graph:
         check(lib().tp_graph_export_compressed(self._h, _ptr(data), _ptr(off), _stream(stream)),
               "tp_graph_export_compressed")
         return data[:nbytes], off
+
+    def encode_ex(self, intervals=True, weights=False, stream=None):
+        """(bytes uint8 CUDA tensor, offsets int64 CUDA tensor holding u64) of
+        this CSR graph in the interval + edge-weight format (tp_encode_ex)."""
+        torch = _torch()
+        n = self.n
+        off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        nb = ctypes.c_uint64()
+        check(lib().tp_encode_ex(self._h, int(intervals), int(weights), _ptr(off), None,
+                                 ctypes.byref(nb), _stream(stream)), "tp_encode_ex")
+        data = torch.empty(max(nb.value, 1), dtype=torch.uint8, device="cuda")
+        check(lib().tp_encode_ex(self._h, int(intervals), int(weights), _ptr(off), _ptr(data),
+                                 ctypes.byref(nb), _stream(stream)), "tp_encode_ex")
+        return data[: nb.value], off
 
     def check(self, stream=None):
         check(lib().tp_graph_check(self._h, _stream(stream)), "tp_graph_check")
@@ -315,6 +330,16 @@ def partition_batch(graphs, ks, eps=0.03, params=None, concurrency=1, outs=None)
     check(lib().tp_partition_batch(cnt, handles, karr, eps, ctypes.byref(p), parr, st, status,
                                    concurrency), "tp_partition_batch")
     return [(parts[i][: graphs[i].n], stats_dict(st[i])) for i in range(cnt)]
+
+
+def graph_from_stream_ex(n, data, off, intervals=True, weighted=False, stream=None) -> Graph:
+    """CSR graph decoded from an interval + edge-weight stream (device tensors;
+    tp_graph_from_stream_ex)."""
+    out = ctypes.c_void_p()
+    check(lib().tp_graph_from_stream_ex(int(n), int(data.numel()), _ptr(data), _ptr(off),
+                                        int(intervals), int(weighted), _stream(stream),
+                                        ctypes.byref(out)), "tp_graph_from_stream_ex")
+    return Graph(out)
 
 
 def footprint_bytes(n, m2, k, upload=True, compress=False) -> int:

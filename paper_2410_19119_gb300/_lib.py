@@ -62,6 +62,8 @@ SIGNATURES = {
     "tp_graph_compress": (ctypes.c_int, [vp, vp, P(vp)]),
     "tp_graph_from_compressed": (ctypes.c_int, [i64, u64, vp, vp, ctypes.c_int, vp, P(vp)]),
     "tp_graph_decompress": (ctypes.c_int, [vp, vp, P(vp)]),
+    "tp_encode_ex": (ctypes.c_int, [vp, i32, i32, vp, vp, P(u64), vp]),
+    "tp_graph_from_stream_ex": (ctypes.c_int, [i64, u64, vp, vp, i32, i32, vp, P(vp)]),
     "tp_graph_info": (ctypes.c_int, [vp, P(i64), P(i64), P(ctypes.c_int), P(sz), P(sz)]),
     "tp_graph_export_csr": (ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
     "tp_graph_export_compressed": (ctypes.c_int, [vp, vp, vp, vp]),

@@ -23,6 +23,10 @@ void export_csr(const tp_graph *g, int64_t *xadj, int32_t *adj, int64_t *vw, int
 void export_compressed(const tp_graph *g, uint8_t *bytes, uint64_t *off, cudaStream_t s);
 void partition(tp_graph *g0, int32_t k, int64_t eps_ppm, const tp_params &p, int32_t *d_part,
                tp_stats *st, cudaStream_t s);
+uint64_t encode_ex(const tp_graph *g, bool intervals, bool weights, uint64_t *d_off,
+                   uint8_t *d_bytes, cudaStream_t s);
+tp_graph *decode_ex(int64_t n, uint64_t nbytes, const uint8_t *d_bytes, const uint64_t *d_off,
+                    bool intervals, bool weighted, cudaStream_t s);
 void partition_union(const std::vector<const tp_graph *> &gs, const std::vector<int32_t> &idx,
                      const int32_t *k, int64_t eps_ppm, const tp_params &p,
                      int32_t *const *d_part, tp_stats *stats, cudaStream_t s);
@@ -124,6 +128,26 @@ tp_status tp_graph_from_compressed(int64_t n, uint64_t nbytes, const uint8_t *by
   return guard([&] {
     pool_setup();
     *out = from_compressed(n, nbytes, bytes, off, host_ptrs, (cudaStream_t)stream);
+  });
+}
+
+tp_status tp_encode_ex(const tp_graph *g, int32_t intervals, int32_t weights, uint64_t *d_off,
+                       uint8_t *d_bytes, uint64_t *nbytes, void *stream) {
+  if (!g || !d_off || !nbytes) return TP_ERR_INVALID;
+  return guard([&] {
+    *nbytes = encode_ex(g, intervals != 0, weights != 0, d_off, d_bytes, (cudaStream_t)stream);
+  });
+}
+
+tp_status tp_graph_from_stream_ex(int64_t n, uint64_t nbytes, const uint8_t *d_bytes,
+                                  const uint64_t *d_off, int32_t intervals, int32_t weighted,
+                                  void *stream, tp_graph **out) {
+  if (!out) return TP_ERR_INVALID;
+  *out = nullptr;
+  return guard([&] {
+    pool_setup();
+    *out = decode_ex(n, nbytes, d_bytes, d_off, intervals != 0, weighted != 0,
+                     (cudaStream_t)stream);
   });
 }
 
