@@ -299,7 +299,7 @@ tp_graph *contract(const tp_graph *g, const int32_t *C, int32_t *d_map, cudaStre
     Buf<int64_t> off(n + 1, s);
     unsigned wb = grid_for(n * 32, 256);
     unsigned tb = grid_for(n, 256);
-    const bool warp_work = T.n_mid + T.n_mid2 + T.n_big0 + T.n_big + T.n_big2 > 0;
+    const bool warp_work = T.n_mid + T.n_mid2 + T.n_big0 + T.n_big1 + T.n_big + T.n_big2 > 0;
     if (comp) launch(k_count_thread<true>, tb, 256, 0, s, v, T.tier.get(), map, off.get());
     else launch(k_count_thread<false>, tb, 256, 0, s, v, T.tier.get(), map, off.get());
     if (warp_work || T.n_huge) {  // the warp kernel also zeroes the hub entries

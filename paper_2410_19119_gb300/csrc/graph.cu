@@ -312,7 +312,7 @@ __global__ void k_classify(const int64_t *deg, int64_t n, int32_t lane_max, int3
                            int32_t mid_max, const uint32_t *off32, const uint64_t *off64,
                            bool long_records, uint8_t *tier, int32_t *flag_small,
                            int32_t *flag_mid, int32_t *flag_mid2, int32_t *flag_big0,
-                           int32_t *flag_big,
+                           int32_t *flag_big1, int32_t *flag_big,
                            int32_t *flag_big2, int32_t *flag_huge, unsigned long long *stats) {
   int64_t e[5] = {0, 0, 0, 0, 0}, c[5] = {0, 0, 0, 0, 0};
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
@@ -333,7 +333,8 @@ __global__ void k_classify(const int64_t *deg, int64_t n, int32_t lane_max, int3
     flag_mid[u] = t == TIER_MID && d <= kMidSplit;
     flag_mid2[u] = t == TIER_MID && d > kMidSplit;
     flag_big0[u] = t == TIER_BIG && d <= kBigTinySplit;
-    flag_big[u] = t == TIER_BIG && d > kBigTinySplit && d <= kBigSplit;
+    flag_big1[u] = t == TIER_BIG && d > kBigTinySplit && d <= kBigMidSplit;
+    flag_big[u] = t == TIER_BIG && d > kBigMidSplit && d <= kBigSplit;
     flag_big2[u] = t == TIER_BIG && d > kBigSplit;
     flag_huge[u] = t == TIER_HUGE;
     e[t] += d;
@@ -406,7 +407,7 @@ void build_tiers(tp_graph *g, const tp_params &p, cudaStream_t s) {
   }
   Buf<int64_t> deg(n, s);
   compute_degrees(g, deg.get(), s);
-  Buf<int32_t> fs(n, s), fm(n, s), fm2(n, s), fb0(n, s), fb(n, s), fb2(n, s), fh(n, s);
+  Buf<int32_t> fs(n, s), fm(n, s), fm2(n, s), fb0(n, s), fb1(n, s), fb(n, s), fb2(n, s), fh(n, s);
   Buf<unsigned long long> te(10, s);
   TP_CUDA(cudaMemsetAsync(te.get(), 0, 10 * sizeof(unsigned long long), s));
   const uint32_t *o32 = g->compressed && !g->off_is64 ? g->off32.get() : nullptr;
@@ -422,8 +423,8 @@ void build_tiers(tp_graph *g, const tp_params &p, cudaStream_t s) {
     TP_CUDA(cudaMemsetAsync(te.get(), 0, 2 * sizeof(unsigned long long), s));
   }
   launch(k_classify, grid_for(n, 256), 256, 0, s, deg.get(), n, lane_max, small_max, mid_max,
-         o32, o64, long_records, T.tier.get(), fs.get(), fm.get(), fm2.get(), fb0.get(), fb.get(),
-         fb2.get(), fh.get(), te.get());
+         o32, o64, long_records, T.tier.get(), fs.get(), fm.get(), fm2.get(), fb0.get(), fb1.get(),
+         fb.get(), fb2.get(), fh.get(), te.get());
   TP_LAUNCH_CHECK();
   unsigned long long hte[10];
   TP_CUDA(cudaMemcpyAsync(hte, te.get(), sizeof(hte), cudaMemcpyDeviceToHost, s));
@@ -443,6 +444,7 @@ void build_tiers(tp_graph *g, const tp_params &p, cudaStream_t s) {
   make_list(fm, T.mid, T.n_mid);
   make_list(fm2, T.mid2, T.n_mid2);
   make_list(fb0, T.big0, T.n_big0);
+  make_list(fb1, T.big1, T.n_big1);
   make_list(fb, T.big, T.n_big);
   make_list(fb2, T.big2, T.n_big2);
   make_list(fh, T.huge, T.n_huge);

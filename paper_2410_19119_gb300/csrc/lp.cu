@@ -998,6 +998,7 @@ __global__ void k_rate_list(RateCtx c) {
 // each value its index and the sum of the gaps before it.
 constexpr int kBlockThreads = 256;
 constexpr int kBlockTinyLog = 11;   // 2048 slots: degrees up to kBigTinySplit = 1024
+constexpr int kBlockMidLog = 12;    // 4096 slots: degrees up to kBigMidSplit = 2048
 constexpr int kBlockSmallLog = 13;  // 8192 slots: degrees up to kBigSplit = 4096
 constexpr int kBlockBigLog = 14;    // 16384 slots: degrees up to 10000
 // Record staging and decoded values for a compressed vertex of degree <= dmax:
@@ -1007,7 +1008,10 @@ __host__ __device__ constexpr size_t block_stage_bytes(int64_t dmax) {
 }
 __host__ __device__ constexpr size_t block_vbuf_bytes(int64_t dmax) { return (size_t)4 * dmax; }
 __host__ __device__ constexpr int64_t block_max_deg(int lg) {
-  return lg == kBlockTinyLog ? kBigTinySplit : lg == kBlockSmallLog ? kBigSplit : kChunkThreshold;
+  return lg == kBlockTinyLog    ? kBigTinySplit
+         : lg == kBlockMidLog   ? kBigMidSplit
+         : lg == kBlockSmallLog ? kBigSplit
+                                : kChunkThreshold;
 }
 
 // Block-wide exclusive sum of one int64 per thread; returns this thread's
@@ -1842,7 +1846,7 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
     run(T.mid2.get(), T.n_mid2, 2, true);
     if (prof) prof_end(PF_RATE_MID, s, per_launch * tier_round_bytes(g, T.n_mid + T.n_mid2, T.edges[TIER_MID]));
   }
-  if (T.n_big0 + T.n_big + T.n_big2 > 0) {
+  if (T.n_big0 + T.n_big1 + T.n_big + T.n_big2 > 0) {
     if (prof) prof_begin(PF_RATE_BIG, s);
     const bool wt = !g->unit_ew;
     auto run = [&](const int32_t *list, int64_t cnt, int maxlog, int t) {
@@ -1865,16 +1869,17 @@ void rate_tiers(tp_graph *g, RateCtx c, const tp_params &p, cudaStream_t s) {
       TP_LAUNCH_CHECK();
     };
     run(T.big0.get(), T.n_big0, kBlockTinyLog, 3);
-    run(T.big.get(), T.n_big, kBlockSmallLog, 4);
-    run(T.big2.get(), T.n_big2, kBlockBigLog, 5);
-    if (prof) prof_end(PF_RATE_BIG, s, per_launch * tier_round_bytes(g, T.n_big0 + T.n_big + T.n_big2, T.edges[TIER_BIG]));
+    run(T.big1.get(), T.n_big1, kBlockMidLog, 4);
+    run(T.big.get(), T.n_big, kBlockSmallLog, 5);
+    run(T.big2.get(), T.n_big2, kBlockBigLog, 6);
+    if (prof) prof_end(PF_RATE_BIG, s, per_launch * tier_round_bytes(g, T.n_big0 + T.n_big1 + T.n_big + T.n_big2, T.edges[TIER_BIG]));
   }
   if (T.n_huge > 0) {
     if (prof) prof_begin(PF_RATE_HUGE, s);
     RateCtx m = c;
     m.list = T.huge.get();
     m.list_n = T.n_huge;
-    bucketed(m, 6);
+    bucketed(m, 7);
     m.toff = T.huge_toff.get();
     m.tcap = T.huge_tcap.get();
     m.tbase = 0;
@@ -2136,10 +2141,11 @@ __global__ void k_huge_items(const int32_t *bpos, int64_t nh, const int64_t *pre
 // Buckets the warp and block tiers' lists of this round by sub-round.
 static void tier_buckets(tp_graph *g, LpWork &w, int32_t S, cudaStream_t stream) {
   TierCache &T = g->tiers;
-  const int32_t *lists[LpWork::kTiers] = {T.small.get(), T.mid.get(),  T.mid2.get(), T.big0.get(),
-                                          T.big.get(),   T.big2.get(), T.huge.get()};
-  const int64_t lens[LpWork::kTiers] = {T.n_small, T.n_mid,  T.n_mid2, T.n_big0,
-                                        T.n_big,   T.n_big2, T.n_huge};
+  const int32_t *lists[LpWork::kTiers] = {T.small.get(), T.mid.get(),  T.mid2.get(),
+                                          T.big0.get(),  T.big1.get(), T.big.get(),
+                                          T.big2.get(),  T.huge.get()};
+  const int64_t lens[LpWork::kTiers] = {T.n_small, T.n_mid, T.n_mid2, T.n_big0,
+                                        T.n_big1,  T.n_big, T.n_big2, T.n_huge};
   int64_t total = 0;
   for (int t = 0; t < LpWork::kTiers; ++t) w.tb_base[t] = total, total += lens[t];
   w.tb_valid = false;
@@ -2173,7 +2179,7 @@ static void tier_buckets(tp_graph *g, LpWork &w, int32_t S, cudaStream_t stream)
       w.hc_item.alloc(std::max<int64_t>(T.n_huge_chunks, 1), stream);
     if ((int64_t)w.hs_item.n < std::max<int64_t>(T.n_huge_segs, 1))
       w.hs_item.alloc(std::max<int64_t>(T.n_huge_segs, 1), stream);
-    const int32_t *hp = w.tb_pos.get() + w.tb_base[6];
+    const int32_t *hp = w.tb_pos.get() + w.tb_base[7];
     launch(k_huge_counts, grid_for(nh, 256), 256, 0, stream, hp, nh, T.huge_chunk_start.get(),
            T.huge_seg_start.get(), w.hc_pre.get(), w.hs_pre.get());
     exclusive_scan_i64(w.hc_pre.get(), w.hc_pre.get(), nh, stream);

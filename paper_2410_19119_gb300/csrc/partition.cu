@@ -109,7 +109,7 @@ int64_t edge_cut(const tp_graph *g, const int32_t *part, cudaStream_t s) {
     unsigned tb = grid_for(g->n, 256);
     if (g->compressed) launch(k_cut_thread<true>, tb, 256, 0, s, view(g), tier, part, acc.get());
     else launch(k_cut_thread<false>, tb, 256, 0, s, view(g), tier, part, acc.get());
-    if (T.n_mid + T.n_mid2 + T.n_big0 + T.n_big + T.n_big2 + T.n_huge > 0) {
+    if (T.n_mid + T.n_mid2 + T.n_big0 + T.n_big1 + T.n_big + T.n_big2 + T.n_huge > 0) {
       unsigned b = grid_for(g->n * 32, 256);
       if (g->compressed) launch(k_cut<true>, b, 256, 0, s, view(g), tier, part, acc.get());
       else launch(k_cut<false>, b, 256, 0, s, view(g), tier, part, acc.get());

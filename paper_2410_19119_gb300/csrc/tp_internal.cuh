@@ -114,6 +114,7 @@ constexpr int kSegLog = 12;                 // huge tables are scanned 4096 slot
 constexpr int kSegBestBytes = 48;           // one segment's best label and best admissible label
 constexpr int64_t kMidSplit = 256;          // mid tier: degrees up to here use 512-slot tables
 constexpr int64_t kBigTinySplit = 1024;     // big tier: degrees up to here use 2048-slot tables
+constexpr int64_t kBigMidSplit = 2048;      // big tier: degrees up to here use 4096-slot tables
 constexpr int64_t kBigSplit = 4096;         // big tier: degrees up to here use 8192-slot tables
 
 struct TierCache {
@@ -124,10 +125,12 @@ struct TierCache {
   Buf<uint8_t> tier;         // n
   // vertex lists per tier (ascending); the mid tier is listed in two parts,
   // degree <= kMidSplit (warp tables of 512 slots) and above (1024), the big
-  // tier in three, degree <= kBigTinySplit (block tables of 2048 slots, many
-  // blocks per SM), <= kBigSplit (8192) and above (16384)
-  Buf<int32_t> small, mid, mid2, big0, big, big2, huge;
-  int64_t n_small = 0, n_mid = 0, n_mid2 = 0, n_big0 = 0, n_big = 0, n_big2 = 0, n_huge = 0;
+  // tier in four, degree <= kBigTinySplit (block tables of 2048 slots, many
+  // blocks per SM), <= kBigMidSplit (4096), <= kBigSplit (8192) and above
+  // (16384)
+  Buf<int32_t> small, mid, mid2, big0, big1, big, big2, huge;
+  int64_t n_small = 0, n_mid = 0, n_mid2 = 0, n_big0 = 0, n_big1 = 0, n_big = 0, n_big2 = 0,
+          n_huge = 0;
   Buf<int64_t> huge_toff;  // global table offsets (slots), size n_huge + 1
   Buf<int32_t> huge_tcap;  // log2 of the table capacity per vertex
   int64_t huge_slots = 0;
@@ -147,7 +150,7 @@ struct TierCache {
   // Later frees go to stream s (the cache may have been built on a stream
   // that no longer exists; see tp_graph::rehome).
   void rehome(cudaStream_t s) {
-    tier.s = small.s = mid.s = mid2.s = big0.s = big.s = big2.s = huge.s = s;
+    tier.s = small.s = mid.s = mid2.s = big0.s = big1.s = big.s = big2.s = huge.s = s;
     huge_toff.s = huge_tcap.s = s;
     huge_chunk_start.s = tkeys.s = tvals.s = tlist.s = tcount.s = s;
     huge_seg_start.s = huge_seg_best.s = s;
@@ -411,14 +414,14 @@ struct LpWork {
   Buf<int64_t> bucket_off;   // S * nblocks + 1 offsets (sub-round major)
   int64_t bucket_nblocks = 0;
   int32_t bucket_S = 0;      // S of the current buckets (0: none)
-  // the other tiers' lists (small, mid, mid2, big0, big, big2, huge) grouped by sub-round:
+  // the other tiers' lists (small, mid, mid2, big0, big1, big, big2, huge) grouped by sub-round:
   // tb_pos holds list positions, tb_off[t * (S + 1) + s] where sub-round s of
   // tier t starts in tb_pos (tier t's entries begin at tb_base[t])
-  static constexpr int kTiers = 7;
+  static constexpr int kTiers = 8;
   Buf<int32_t> tb_pos;       // sum of the tier list lengths
   Buf<int64_t> tb_off;       // kTiers * (S + 1)
   Buf<int64_t> tb_cur;       // kTiers * S cursors
-  int64_t tb_base[kTiers] = {0, 0, 0, 0, 0, 0, 0};
+  int64_t tb_base[kTiers] = {0, 0, 0, 0, 0, 0, 0, 0};
   bool tb_valid = false;
   // huge tier, in bucket order of its hubs: prefix of chunk and segment
   // counts (n_huge + 1) and the items themselves (hub position << 32 | index)
