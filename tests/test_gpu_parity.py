@@ -315,7 +315,8 @@ def _degree_boundaries(leaves=30000, seed=12):
     # hubs whose degrees sit on both sides of every tier boundary and of the
     # chunking threshold (10 000 / 10 001 neighbours, chunks of 1 000), over
     # leaves joined by a path and random edges
-    degs = [1, 31, 32, 33, 63, 64, 65, 511, 512, 513, 1000, 9999, 10000, 10001, 10999, 11000]
+    degs = [1, 31, 32, 33, 63, 64, 65, 255, 256, 257, 511, 512, 513, 1000, 1024, 1025, 2048,
+            2049, 4096, 4097, 9999, 10000, 10001, 10999, 11000]
     h = len(degs)
     rng = np.random.default_rng(seed)
     edges = set()
