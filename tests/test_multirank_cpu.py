@@ -102,3 +102,42 @@ def test_autotune_candidates_and_sample():
     sizes = sorted(gs[i].n for i in idx)
     assert sizes[0] == 5 and sizes[-1] >= 2000  # spread from the smallest upwards
     assert sorted(autotune.sample_indices(gs, 99)) == list(range(len(gs)))
+
+
+def test_autotune_coordinate_descent_picks_the_fastest_knobs(monkeypatch):
+    """With a stubbed batch call whose cost depends on the knobs and a fake
+    clock, the tuner improves one knob at a time from the defaults and keeps
+    every improvement."""
+    import types
+
+    import torch
+
+    from paper_2410_19119_gb300 import autotune
+
+    clock = {"t": 0.0}
+    best = {"tier_lane": 16, "tier_small": 64, "tier_mid": 256, "warps_per_block": 4,
+            "table_slack": 1}
+
+    def cost(p):
+        return 1.0 + sum(0.1 for k, v in best.items() if getattr(p, k) != v)
+
+    def fake_batch(gs, kk, eps, p, concurrency=1):
+        clock["t"] += cost(p)
+
+    monkeypatch.setattr(autotune, "partition_batch", fake_batch)
+    monkeypatch.setattr(autotune, "time", types.SimpleNamespace(perf_counter=lambda: clock["t"]))
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+
+    class G:
+        def __init__(self, n):
+            self.n = n
+
+        def info(self):
+            return {"m2": 8 * self.n}
+
+    gs = [G(100 * (i + 1)) for i in range(20)]
+    p, table = autotune.autotune(gs, [2] * 20, sample=5, repeats=1)
+    assert {k: getattr(p, k) for k in best} == best
+    assert abs(min(t for _, t in table) - 1.0) < 1e-9
+    # the defaults first, then each knob's values with the others held
+    assert len(table) <= 1 + sum(len(v) for _, v in autotune.KNOBS)
